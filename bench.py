@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the SDRT residual on GB300: DOF-updates/s of classical RK4 steps.
+
+Workload (default): compressible Euler (5 variables, gamma = 1.4) on the
+periodic cube [-5, 5]^3 split into 24^3 x 6 = 82,944 tetrahedra, SDRT degree
+p = 3 (20 solution points per element), Rusanov common flux, isentropic vortex
+(Ma 0.5, S = 13.5, R = 1.5) times (1 + 1e-3 U(-1, 1)) with NumPy PCG64 seed
+20210518, RK4 with dt = 1e-3.  One step = one RK4 step = 4 residual
+evaluations, each fused with its stage update.  DOF-updates/s =
+nsol * nvar * nelem * 4 / step time (paper App. C's PM metric inverted).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py --impl reference      # the FP64 CPU oracle on the same workload
+
+Multi-GPU (torchrun): every rank steps its own replica of the workload
+(independent problems, no data-path collective); value = all ranks' DOF
+updates / max over ranks of the timed region.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SDRT residual DOF-updates/s on 1 GB300 (FP32/batched vs FP64 at stated L2 err), % roofline"
+UNIT = "DOF-updates/s"
+WORKLOAD = "euler3d_tet_p3_82944_rk4"
+SEED = 20210518
+DT = 1e-3
+NCELL = 24
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sdrt", choices=["sdrt", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_mesh(ncell=NCELL):
+    from inputs import meshes
+    return meshes.box_mesh("tet", (ncell,) * 3, [-5.0] * 3, [5.0] * 3)
+
+
+def initial_field(X, seed):
+    from inputs import fields
+    u = fields.isentropic_vortex(X, gamma=1.4, mach=0.5)
+    return u * (1 + fields.uniform_noise(u.shape, seed, 1e-3))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(nsol, nfe, nvar, nfaces, nd, s, nelem):
+    """Algorithmic bytes of one RK4 step, per kernel launch kind.
+
+    interp_ext : read U (nsol V s), write own face states (nfe V s)
+    residual   : read stage input (nsol V s), read partner face states (nfe V s),
+                 metric ((1 + nd^2 + nfaces (nd+1)) s), face map (nfe * 4 B),
+                 stage update averaged over the 4 RK4 stages: 3 state volumes
+                 (read u0 / read+write accumulator / write next stage), i.e.
+                 stage 1: 2 writes; stages 2-3: 2 reads + 2 writes; stage 4:
+                 1 read + 1 write -> (2 + 4 + 4 + 2) / 4 = 3
+    """
+    interp = (nsol + nfe) * nvar * s
+    metric = (1 + nd * nd + nfaces * (nd + 1)) * s
+    resid = (nsol + nfe) * nvar * s + metric + nfe * 4 + 3 * nsol * nvar * s
+    return interp * nelem, resid * nelem
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ncu_traffic(kernels_src):
+    """dram bytes per launch of the residual kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_residual_tet_p3_euler_fp32.txt")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(kernels_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernels_cu_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(ncell=16):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    the same element type, degree, physics and initial field on a periodic
+    ncell^3 x 6 tetrahedron box, one RK4 step (4 residual evaluations)."""
+    from oracle import mesh as omesh
+    from oracle import physics as ophx
+    from oracle import residual as ores
+    mesh = workload_mesh(ncell)
+    geom = omesh.build(mesh, 3)
+    phys = ophx.Physics("euler", 3, "rusanov", gamma=1.4)
+    U = []
+    for g in geom.blocks:
+        X = g.xsol.reshape(-1, 3)
+        v = initial_field(X, SEED).reshape(g.nelem, g.ops.n_sol, 5)
+        U.append(np.ascontiguousarray(np.transpose(v, (1, 2, 0))))
+    t0 = time.perf_counter()
+    ores.rk4_step(geom, phys, U, DT)
+    t = time.perf_counter() - t0
+    ndof = sum(g.ops.n_sol * 5 * g.nelem for g in geom.blocks)
+    return {"value": ndof * 4 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one RK4 step (4 residuals) of the same tet p=3 Euler workload on a {ncell}^3 x 6 = "
+                      f"{6 * ncell ** 3}-element periodic box; NumPy FP64, single-threaded einsum; "
+                      f"{t:.2f} s; host affinity {len(os.sched_getaffinity(0))} cores"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(ncell=4)
+        if i >= args.warmup:
+            steps.append(cb["value"])
+    v = float(np.mean(steps))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "4^3 x 6 = 384 tetrahedra per step (bounded CPU sample)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one RK4 step on a 4^3 x 6 tetrahedron periodic box per bench step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2105_08632_gb300 import sdrt
+    if not os.path.exists(sdrt.LIB_PATH):
+        from paper_2105_08632_gb300 import build
+        build.build()
+
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    ctx = sdrt.Context(local, stream.cuda_stream)
+    mesh = workload_mesh()
+    phys = sdrt.make_physics("euler", 3, "rusanov", args.precision, gamma=1.4)
+    M = sdrt.Mesh(ctx, mesh, 3, phys)
+    lay = M.layouts[0]
+    nelem, nsol, nvar = lay["nelem"], lay["nsol"], lay["nvar"]
+    ndof = M.info["ndof"]
+    X = M.sol_points()[0].reshape(-1, 3)
+    U0 = initial_field(X, SEED + rank).reshape(nelem, nsol, nvar).transpose(1, 2, 0)
+    host = M.pack([U0])
+    tdtype = torch.float32 if args.precision == "fp32" else torch.float64
+    U = torch.from_numpy(host).to(f"cuda:{local}")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        M.rk4_step(U, DT, 1)
+    M.sync()
+    sdrt.sdrt_profile_enable(ctx.ptr, True)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = sdrt.sdrt_launch_count(ctx.ptr)
+    prof = {k: [0.0, 0] for k in sdrt.KERNEL_KINDS}
+    step_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # evict L2 (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M.rk4_step(U, DT, 1)
+        e1.record(stream)
+        for k, (ms, n) in sdrt.sdrt_profile_collect(ctx.ptr).items():   # synchronises
+            prof[k][0] += ms
+            prof[k][1] += n
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = sdrt.sdrt_launch_count(ctx.ptr) - launches0
+    clocks = sampler.stop()
+    sdrt.sdrt_profile_enable(ctx.ptr, False)
+    M.sync()
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * ndof * 4 / (ms_per_step / 1e3)
+
+    # Roofline of the dominant kernel (the residual / divergence kernel).
+    s = 4 if args.precision == "fp32" else 8
+    info = sdrt.sdrt_get_etype_info(ctx.ptr, M.etypes[0])
+    b_interp, b_resid = algorithmic_bytes(nsol, info["nfe"], nvar, info["nfaces"], 3, s, nelem)
+    ms_r, n_r = prof["residual"]
+    ms_i, n_i = prof["interp_ext"]
+    avg_r = ms_r / max(n_r, 1)
+    avg_i = ms_i / max(n_i, 1)
+    peak, peak_kind = peaks()
+    achieved = b_resid / (avg_r / 1e3) / 1e9 if n_r else None
+    traffic = ncu_traffic(os.path.join(ROOT, "paper_2105_08632_gb300", "csrc", "kernels.cu"))
+    roofline = {"bound": "hbm", "kernel": "k_residual", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "algorithmic_bytes_per_launch": b_resid, "avg_launch_ms": avg_r,
+                "interp_ext": {"algorithmic_bytes_per_launch": b_interp, "avg_launch_ms": avg_i,
+                               "achieved_gbs": b_interp / (avg_i / 1e3) / 1e9 if n_i else None},
+                "step_share": {"k_residual": ms_r / max(total_ms, 1e-9) if not dist else None,
+                               "k_interp_ext": ms_i / max(total_ms, 1e-9) if not dist else None}}
+
+    # End to end through the host-buffer entry point (pinned memory).
+    pin_in = torch.from_numpy(host).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    e2e_t = []
+    for i in range(args.e2e_steps + 1):
+        t0 = time.perf_counter()
+        M.rk4_step_host(pin_in, pin_out, DT, 1)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_t.append(t1 - t0)
+    nbytes = host.nbytes
+    e2e = {"value": world * ndof * 4 / float(np.mean(e2e_t)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "api": "sdrt_rk4_step_host (pinned host buffers, 1 step per call)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "elements": nelem, "degree": 3, "nsol": nsol, "nvar": nvar,
+                           "ndof": ndof, "residuals_per_step": 4, "precision": args.precision,
+                           "l2": "flushed between timed steps (256 MiB write, untimed)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * sdrt.h -- C ABI of the GB300 (sm_103a) Spectral Difference Raviart-Thomas
+ * residual library (arXiv 2105.08632).
+ *
+ * The library evaluates the SDRT semi-discrete residual dU/dt = R(U) (paper
+ * Sec. 2.1, Eqs. "interpolate_sol_to_flux" .. "divergence_sdrt" and the
+ * semi-discrete form after it; matrix form App. B, Eq. "residual_sdrt_matrices")
+ * for meshes of triangles, quadrilaterals, tetrahedra, prisms and hexahedra,
+ * classical RK4 steps of it, and its Jacobian-vector / vector-Jacobian products.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: SDRT_OK (0) or a negative sdrt_status.  The message of the
+ *    last failure of a context is available from sdrt_last_error().
+ *  - Device calls are asynchronous and ordered on the context's CUDA stream.
+ *    Argument / state errors are reported immediately; kernel launch errors
+ *    are returned by the call that launched; the non-finite flag raised by a
+ *    kernel is reported by sdrt_sync().
+ *  - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *    host pointers owned by the caller.  The library never frees caller memory.
+ *  - State layout: the state of a mesh is one array holding its blocks one
+ *    after the other.  Block b starts at element offset `offset` (see
+ *    sdrt_block_layout) and stores value (rho, v, e) -- solution point rho,
+ *    variable v, element e -- at offset + (rho * nvar + v) * ld + e, where
+ *    ld >= nelem is a multiple of 32 (the paper's state matrix, App. B Eq.
+ *    "state_matrices", with the element index fastest).  Padding entries
+ *    (nelem <= e < ld) are never read as data and never written.
+ *    The element type is double (SDRT_FP64) or float (SDRT_FP32).
+ *  - Ordering of solution / flux points and local faces: see sdrt_point_order
+ *    in the package documentation; it is the same convention as the mesh
+ *    faces' local numbering documented at sdrt_face.
+ */
+#ifndef SDRT_H
+#define SDRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdrt_ctx sdrt_ctx;
+
+typedef enum {
+    SDRT_OK = 0,
+    SDRT_ERR_ARG = -1,          /* invalid argument (null pointer, bad id, size mismatch) */
+    SDRT_ERR_UNSUPPORTED = -2,  /* valid request outside the implemented set */
+    SDRT_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    SDRT_ERR_STATE = -4,        /* call out of order (e.g. mesh used before setup) */
+    SDRT_ERR_NONFINITE = -5,    /* a kernel produced NaN / Inf (reported by sdrt_sync) */
+    SDRT_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    SDRT_ERR_MESH = -7          /* faces do not match / inverted or non-affine element */
+} sdrt_status;
+
+typedef enum { SDRT_TRI = 0, SDRT_QUAD = 1, SDRT_TET = 2, SDRT_PRI = 3, SDRT_HEX = 4 } sdrt_shape;
+typedef enum { SDRT_ADVECTION = 0, SDRT_ADVDIFF = 1, SDRT_EULER = 2, SDRT_NAVIER_STOKES = 3 } sdrt_system;
+typedef enum { SDRT_UPWIND = 0, SDRT_RUSANOV = 1, SDRT_ROE = 2 } sdrt_riemann;
+typedef enum { SDRT_FP64 = 0, SDRT_FP32 = 1 } sdrt_precision;
+
+/* Element type: reference element and degree p (paper App. A). */
+typedef struct {
+    int32_t shape;   /* sdrt_shape */
+    int32_t degree;  /* p >= 1; p <= 4 validated (simplices are unstable for p >= 5, Sec. 3.1.1) */
+} sdrt_etype_desc;
+
+/* Counts of one element type (paper App. A, Tables "nsolpts_nfpts", "nfpts_extra"). */
+typedef struct {
+    int32_t ndim, nsol, nfe, nfi, nfiu, nfaces;
+} sdrt_etype_info;
+
+/* Physics of a mesh.  Fluxes (Sec. 2.1, 3, 5): advection f = a u; advection-
+ * diffusion f = a u - mu grad u; Euler; Navier-Stokes with dynamic viscosity
+ * mu, Prandtl number, ratio of specific heats gamma.  Common fluxes: upwind
+ * (Eq. "flux_advection"), Rusanov (wave speed max(|v.n|+c) per side), Roe;
+ * viscous terms use the LDG common value / flux with parameters beta, eta
+ * (Eq. "common_var_for_grad" and the common viscous flux of Sec. 2.1). */
+typedef struct {
+    int32_t system;      /* sdrt_system */
+    int32_t riemann;     /* sdrt_riemann */
+    int32_t precision;   /* sdrt_precision of the state arrays */
+    int32_t ndim;        /* 2 or 3, must match every block's element type */
+    double a[3];         /* advection velocity */
+    double mu, gamma, prandtl, beta, eta;
+} sdrt_physics;
+
+/* One block of elements of a single type.  verts: host, FP64,
+ * nelem x nvert x ndim, vertices in the reference order of the type:
+ *   tri (-1,-1),(1,-1),(-1,1); quad (-1,-1),(1,-1),(1,1),(-1,1);
+ *   tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1);
+ *   pri tri x {-1} then tri x {+1}; hex quad x {-1} then quad x {+1}.
+ * Elements must be affine images of the reference element (curved elements
+ * are not supported: SDRT_ERR_UNSUPPORTED). Copied at setup. */
+typedef struct {
+    int32_t etype;
+    int32_t nelem;
+    const double* verts;
+} sdrt_block;
+
+/* A glued pair of faces.  Local face numbering (vertex subsets):
+ *   tri  e0 (0,1) e1 (1,2) e2 (2,0)      quad e0 (0,1) e1 (1,2) e2 (3,2) e3 (0,3)
+ *   tet  f0 (0,1,2) f1 (0,1,3) f2 (1,2,3) f3 (0,2,3)
+ *   pri  f0 (0,1,2) f1 (0,1,4,3) f2 (1,2,5,4) f3 (0,2,5,3) f4 (3,4,5)
+ *   hex  f0 (0,1,2,3) f1 (0,1,5,4) f2 (1,2,6,5) f3 (3,2,6,7) f4 (0,3,7,4) f5 (4,5,6,7)
+ * The first element is the face's L side: the common value and common flux
+ * of the face are evaluated once with (u_L, u_R, n_L).  shift: x_L = x_R + shift
+ * for coincident points (periodic faces). */
+typedef struct {
+    int32_t blk_l, elem_l, face_l;
+    int32_t blk_r, elem_r, face_r;
+    double shift[3];
+} sdrt_face;
+
+typedef struct {
+    int32_t nvar, nblocks, ndim, precision;
+    int64_t state_len;   /* length of a state array in elements (with padding) */
+    int64_t ndof;        /* sum over blocks of nsol * nvar * nelem */
+    int64_t nfe_total;   /* number of external flux points of the mesh */
+} sdrt_mesh_info;
+
+typedef struct {
+    int32_t etype, nsol, nvar, nelem, ld, nfe;
+    int64_t offset;      /* element offset of the block in a state array */
+} sdrt_block_layout;
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The stream is borrowed:
+ * it must outlive the context.  device = -1 creates a host-only context:
+ * element types and meshes are built on the host (operators, metrics, face
+ * maps can be queried) but every device computation returns SDRT_ERR_STATE. */
+int sdrt_create(sdrt_ctx** ctx, int device, void* cuda_stream);
+/* Destroy a context and every device buffer it owns. NULL is ignored. */
+void sdrt_destroy(sdrt_ctx* ctx);
+/* Message of the last failure of ctx (static storage of the context). */
+const char* sdrt_last_error(const sdrt_ctx* ctx);
+/* Replace the stream of later calls (borrowed). */
+int sdrt_set_stream(sdrt_ctx* ctx, void* cuda_stream);
+
+/* Build one element type: point sets, Vandermonde inverses and the matrix
+ * operators M0, M12, M13, M14, M15, M16 in FP64 on the host (paper Sec. 2.1
+ * Vandermonde equations, App. A bases, App. B operators), then upload them.
+ * Identical descriptors return the existing id. */
+int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* desc, int* etype_id);
+int sdrt_get_etype_info(sdrt_ctx* ctx, int etype_id, sdrt_etype_info* out);
+
+/* Export an FP64 operator of an element type to host memory, row-major.
+ * which: 0 = M0 (nfe x nsol), 1 = M12 (nfiu x nsol), 2 = M13 (nsol x nfi),
+ *        3 = M14 (nsol x nfe), 4 = M15 (ndim*nsol x nfi), 5 = M16 (ndim*nsol x nfe),
+ *        6 = solution points (nsol x ndim), 7 = external flux points (nfe x ndim).
+ * n must equal the operator's size. */
+int sdrt_get_operator(sdrt_ctx* ctx, int etype_id, int which, double* host_out, int64_t n);
+
+/* Build a mesh: affine metrics per element (Eqs. "mapping_jacobian",
+ * "inverse_mapping_jacobian"), physical unit normals and det J |J^{-T} n~| at
+ * external flux points, and the int32 map pairing every external flux point
+ * with the coincident point of the glued face (matched by physical
+ * coordinates after the periodic shift).  Every external face must be glued
+ * exactly once (periodic / closed meshes).  Host inputs are copied. */
+int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                    int64_t nfaces, const sdrt_face* faces, int* mesh_id);
+int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out);
+int sdrt_get_block_layout(sdrt_ctx* ctx, int mesh_id, int block, sdrt_block_layout* out);
+
+/* Physical coordinates of the solution points, host FP64, blocks in order,
+ * each block nelem x nsol x ndim (no padding). n = total length. */
+int sdrt_get_sol_points(sdrt_ctx* ctx, int mesh_id, double* host_out, int64_t n);
+
+/* Face map in canonical numbering g = base[b] + e * nfe[b] + sigma (no padding;
+ * base = running sum of nelem * nfe): partner_out[g] = canonical index of the
+ * paired point, is_left_out[g] = 1 on the L side of the face.  n = nfe_total.
+ * Bit-exact contract of the mesh setup. */
+int sdrt_get_face_map(sdrt_ctx* ctx, int mesh_id, int32_t* partner_out, uint8_t* is_left_out, int64_t n);
+
+/* R = dU/dt for the whole mesh.  U_dev, R_dev: device state arrays (layout
+ * above, precision of the mesh); may not alias. */
+int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev);
+
+/* nsteps classical RK4 steps of size dt, in place on U_dev (device).  Each
+ * stage is one residual evaluation fused with its stage update (paper Sec. 2.1
+ * explicit RK; RK4 stability polynomial Eq. "rk_exponential"). */
+int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U_dev, double dt, int nsteps);
+
+/* Same as sdrt_rk4_step with host buffers: copies U_in_host to the device,
+ * steps, copies the result to U_out_host and synchronises the stream.
+ * U_in_host / U_out_host: state_len values (may be the same buffer; pinned
+ * memory gives the fastest copies). */
+int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* U_in_host, void* U_out_host,
+                       double dt, int nsteps);
+
+/* Jacobian-vector product JV = (dR/dU)(U) . V (device arrays, state layout).
+ * At ties of |.| and max() the derivative of the first / non-negative branch
+ * is taken. */
+int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* V_dev, void* JV_dev);
+
+/* Vector-Jacobian product JTW = (dR/dU)(U)^T . W (device arrays).  Inviscid
+ * systems only (SDRT_ERR_UNSUPPORTED for advection-diffusion / Navier-Stokes). */
+int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* W_dev, void* JTW_dev);
+
+/* Synchronise the context's stream; returns SDRT_ERR_NONFINITE (and clears the
+ * flag) if a kernel wrote NaN / Inf into a residual since the last sync. */
+int sdrt_sync(sdrt_ctx* ctx);
+
+/* Number of kernel launches issued by the context since creation (for
+ * accounting). */
+int64_t sdrt_launch_count(const sdrt_ctx* ctx);
+
+/* Per-launch device timing with CUDA events recorded on the context's stream
+ * around every kernel the context launches, including inside the captured
+ * RK4 graphs (enabling or disabling drops captured graphs, which are then
+ * re-captured).  Costs two event records per launch. */
+int sdrt_profile_enable(sdrt_ctx* ctx, int enable);
+
+/* Synchronise the stream, then ADD to ms_out[kind] the device milliseconds and
+ * to count_out[kind] the number of launches recorded since the last collect.
+ * kind: 0 = interpolation to external points, 1 = residual / divergence
+ * kernel, 2 = its JVP variant, 3 = reserved.  Arrays of 4 entries, caller
+ * owned.  A graph replayed several times between two collects keeps only its
+ * last replay's timings: collect after every sdrt_rk4_step call. */
+int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDRT_H */

@@ -1,0 +1,912 @@
+// C ABI of the SDRT library: contexts, element types, meshes and the residual,
+// RK4, JVP / VJP entry points (declared in include/sdrt.h).
+#include "sdrt.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "kargs.hpp"
+#include "launch.hpp"
+#include "refel.hpp"
+
+using namespace sdrt;
+
+namespace {
+
+// Owned device allocation.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t alloc(size_t n) {
+        release();
+        bytes = n;
+        if (n == 0) return cudaSuccess;
+        return cudaMalloc(&p, n);
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& h) {
+    cudaError_t e = b.alloc(h.size() * sizeof(T));
+    if (e != cudaSuccess || h.empty()) return e;
+    return cudaMemcpy(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+struct EType {
+    sdrt_etype_desc desc{};
+    RefElement R;
+    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0;
+    DevBuf Ai[2], Ad[2];          // [0] double, [1] float
+    DevBuf fe_face, fi_tab;
+};
+
+struct MBlock {
+    int etype = 0, nelem = 0, ld = 0;
+    int64_t u_off = 0, fe_base = 0, canon_base = 0;
+    DevBuf metric, map;
+    int tile = 32;                // elements per CTA tile
+    int tile_dual = 32;
+};
+
+struct Mesh {
+    sdrt_physics phys{};
+    int nvar = 0, nd = 0;
+    std::vector<std::unique_ptr<MBlock>> blocks;
+    int64_t state_len = 0, Ftot = 0, ndof = 0, nfe_total = 0;
+    std::vector<int32_t> partner;     // canonical face map
+    std::vector<uint8_t> is_left;
+    std::vector<double> sol_xyz;
+    DevBuf ufe, dufe, ustage, uacc, uhost_dev;
+    // RK4 graph cache
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_u = nullptr;
+    double graph_dt = 0;
+    std::vector<int> graph_slots;     // timing slots recorded inside the graph
+    bool warmed = false;
+    ~Mesh() {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
+};
+
+}  // namespace
+
+struct sdrt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 1;
+    bool host_only = false;       // device == -1: host-side setup only, no compute
+    std::string err;
+    std::vector<std::unique_ptr<EType>> etypes;
+    std::vector<std::unique_ptr<Mesh>> meshes;
+    DevBuf flag;
+    int64_t launches = 0;
+    // Per-launch timing: slot s owns events ev[2s], ev[2s+1] and a kernel kind.
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> slot_kind;
+    std::vector<int> eager_slots;        // reusable slots for launches outside graphs
+    int eager_next = 0;
+    std::vector<int>* capture_slots = nullptr;   // slots of the graph being captured
+    std::vector<int> pending;            // slots recorded since the last collect
+    ~sdrt_ctx() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+enum { KIND_INTERP = 0, KIND_RESIDUAL = 1, KIND_JVP = 2, KIND_COUNT = 4 };
+
+int new_slot(sdrt_ctx* ctx, int kind) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1;
+    }
+    ctx->ev.push_back(a);
+    ctx->ev.push_back(b);
+    ctx->slot_kind.push_back(kind);
+    return (int)ctx->slot_kind.size() - 1;
+}
+
+// Start timing one launch: returns the slot (or -1 when profiling is off).
+int prof_begin(sdrt_ctx* ctx, int kind) {
+    if (!ctx->prof) return -1;
+    int s;
+    if (ctx->capture_slots) {
+        s = new_slot(ctx, kind);
+        if (s < 0) return -1;
+        ctx->capture_slots->push_back(s);
+    } else {
+        if (ctx->eager_next == (int)ctx->eager_slots.size()) {
+            int n = new_slot(ctx, kind);
+            if (n < 0) return -1;
+            ctx->eager_slots.push_back(n);
+        }
+        s = ctx->eager_slots[ctx->eager_next++];
+        ctx->slot_kind[s] = kind;
+        ctx->pending.push_back(s);
+    }
+    cudaEventRecord(ctx->ev[2 * s], ctx->stream);
+    return s;
+}
+
+void prof_end(sdrt_ctx* ctx, int s) {
+    if (s >= 0) cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream);
+}
+
+int fail(sdrt_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define SDRT_CUDA(call)                                                                            \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, SDRT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Affine map of one element: x = x0 + J (x~ - x~0); J columns from vertex edges.
+bool element_jacobian(int shape, const double* X, int nd, double* J) {
+    int cols[3];
+    switch (shape) {
+        case TRI: cols[0] = 1; cols[1] = 2; break;
+        case QUAD: cols[0] = 1; cols[1] = 3; break;
+        case TET: cols[0] = 1; cols[1] = 2; cols[2] = 3; break;
+        case PRI: cols[0] = 1; cols[1] = 2; cols[2] = 3; break;
+        default: cols[0] = 1; cols[1] = 3; cols[2] = 4; break;
+    }
+    for (int d = 0; d < nd; ++d)
+        for (int i = 0; i < nd; ++i) J[i * nd + d] = 0.5 * (X[cols[d] * nd + i] - X[i]);
+    // affinity check on every vertex
+    const auto& ref = ref_vertices(shape);
+    const int nv = shape_nverts(shape);
+    double scale = 0;
+    for (int k = 0; k < nd * nd; ++k) scale = std::max(scale, std::fabs(J[k]));
+    for (int v = 0; v < nv; ++v)
+        for (int i = 0; i < nd; ++i) {
+            double x = X[i];
+            for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (ref[v * nd + d] - ref[d]);
+            if (std::fabs(x - X[v * nd + i]) > 1e-10 * (scale + std::fabs(X[v * nd + i]))) return false;
+        }
+    return true;
+}
+
+double det_inv(const double* J, int nd, double* Ji) {
+    if (nd == 2) {
+        double d = J[0] * J[3] - J[1] * J[2];
+        Ji[0] = J[3] / d;
+        Ji[1] = -J[1] / d;
+        Ji[2] = -J[2] / d;
+        Ji[3] = J[0] / d;
+        return d;
+    }
+    double d = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+               J[2] * (J[3] * J[7] - J[4] * J[6]);
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / d;
+    Ji[1] = (J[2] * J[7] - J[1] * J[8]) / d;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / d;
+    Ji[3] = (J[5] * J[6] - J[3] * J[8]) / d;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / d;
+    Ji[5] = (J[2] * J[3] - J[0] * J[5]) / d;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / d;
+    Ji[7] = (J[1] * J[6] - J[0] * J[7]) / d;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / d;
+    return d;
+}
+
+template <typename T>
+KBlock<T> make_kblock(const EType& et, const MBlock& b) {
+    const int pi = std::is_same<T, float>::value ? 1 : 0;
+    KBlock<T> K{};
+    K.nsol = et.R.nsol;
+    K.nfe = et.R.nfe;
+    K.nfi = et.R.nfi;
+    K.nfiu = et.R.nfiu;
+    K.nfaces = et.R.nfaces;
+    K.nelem = b.nelem;
+    K.ld = b.ld;
+    K.u_off = b.u_off;
+    K.fe_base = b.fe_base;
+    K.Ai = et.Ai[pi].as<T>();
+    K.Mi = et.Mi;
+    K.Mi_pad = et.Mi_pad;
+    K.Ad = et.Ad[pi].as<T>();
+    K.Md_pad = et.Md_pad;
+    K.Ag = nullptr;
+    K.Agf = nullptr;
+    K.Mg_pad = et.Mg_pad;
+    K.fe_face = et.fe_face.as<int>();
+    K.fi_tab = et.fi_tab.as<int>();
+    K.metric = b.metric.as<T>();
+    K.map = b.map.as<int>();
+    return K;
+}
+
+template <typename T>
+KPhys<T> make_phys(const sdrt_physics& p) {
+    KPhys<T> P{};
+    for (int d = 0; d < 3; ++d) P.a[d] = (T)p.a[d];
+    P.gamma = (T)p.gamma;
+    P.mu = (T)p.mu;
+    P.prandtl = (T)p.prandtl;
+    P.beta = (T)p.beta;
+    P.eta = (T)p.eta;
+    return P;
+}
+
+int grid_for(const sdrt_ctx* ctx, const MBlock& b, int TE, int per_sm) {
+    const int ntiles = (b.nelem + TE - 1) / TE;
+    return std::max(1, std::min(ntiles, ctx->nsm * per_sm));
+}
+
+// Residual-type evaluation of the whole mesh: interpolation of every block,
+// then the residual kernel of every block with epilogue E.
+template <typename T>
+int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>& E) {
+    const KPhys<T> P = make_phys<T>(m.phys);
+    T* ufe = m.ufe.as<T>();
+    T* dufe = m.dufe.as<T>();
+    for (auto& bp : m.blocks) {
+        const EType& et = *ctx->etypes[bp->etype];
+        KBlock<T> K = make_kblock<T>(et, *bp);
+        int s = prof_begin(ctx, KIND_INTERP);
+        launch_interp_ext<T>(K, m.nvar, U, ufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
+        prof_end(ctx, s);
+        ++ctx->launches;
+        if (dU) {
+            s = prof_begin(ctx, KIND_INTERP);
+            launch_interp_ext<T>(K, m.nvar, dU, dufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
+            prof_end(ctx, s);
+            ++ctx->launches;
+        }
+    }
+    for (auto& bp : m.blocks) {
+        const EType& et = *ctx->etypes[bp->etype];
+        KBlock<T> K = make_kblock<T>(et, *bp);
+        const int TE = dU ? bp->tile_dual : bp->tile;
+        if (TE == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
+        const int s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
+        int r = launch_residual<T>(K, m.phys.system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER, m.phys.riemann,
+                                   m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, E, TE,
+                                   grid_for(ctx, *bp, TE, 2), ctx->stream);
+        prof_end(ctx, s);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
+        ++ctx->launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+template <typename T>
+int rk4_stages(sdrt_ctx* ctx, Mesh& m, T* U, double dt) {
+    KEpi<T> E{};
+    E.flag = ctx->flag.as<int>();
+    T* us = m.ustage.as<T>();
+    T* ua = m.uacc.as<T>();
+    const T c6 = (T)(dt / 6.0), c3 = (T)(dt / 3.0), c2 = (T)(dt / 2.0), c1 = (T)dt;
+    E.u0 = U;
+    E.uacc = ua;
+    E.unext = us;
+    E.mode = EPI_RK_FIRST;
+    E.cacc = c6;
+    E.cnext = c2;
+    int r = run_residual<T>(ctx, m, U, nullptr, E);
+    if (r) return r;
+    E.mode = EPI_RK_MID;
+    E.cacc = c3;
+    E.cnext = c2;
+    if ((r = run_residual<T>(ctx, m, us, nullptr, E))) return r;
+    E.cnext = c1;
+    if ((r = run_residual<T>(ctx, m, us, nullptr, E))) return r;
+    E.mode = EPI_RK_LAST;
+    E.cacc = c6;
+    E.out = U;
+    return run_residual<T>(ctx, m, us, nullptr, E);
+}
+
+int check_mesh(sdrt_ctx* ctx, int mesh_id) {
+    if (!ctx) return SDRT_ERR_ARG;
+    if (mesh_id < 0 || mesh_id >= (int)ctx->meshes.size() || !ctx->meshes[mesh_id])
+        return fail(ctx, SDRT_ERR_ARG, "invalid mesh id");
+    return SDRT_OK;
+}
+
+int check_compute(sdrt_ctx* ctx, int mesh_id) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    if (ctx->host_only) return fail(ctx, SDRT_ERR_STATE, "host-only context: no device computation");
+    return SDRT_OK;
+}
+
+int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
+    const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
+    if (!m.ufe.p) SDRT_CUDA(m.ufe.alloc((size_t)m.nvar * m.Ftot * es));
+    if (need_dual && !m.dufe.p) SDRT_CUDA(m.dufe.alloc((size_t)m.nvar * m.Ftot * es));
+    if (need_rk && !m.ustage.p) {
+        SDRT_CUDA(m.ustage.alloc((size_t)m.state_len * es));
+        SDRT_CUDA(m.uacc.alloc((size_t)m.state_len * es));
+        SDRT_CUDA(cudaMemset(m.ustage.p, 0, m.ustage.bytes));
+        SDRT_CUDA(cudaMemset(m.uacc.p, 0, m.uacc.bytes));
+    }
+    return SDRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdrt_create(sdrt_ctx** out, int device, void* stream) {
+    if (!out) return SDRT_ERR_ARG;
+    *out = nullptr;
+    auto ctx = std::make_unique<sdrt_ctx>();
+    if (device == -1) {
+        ctx->host_only = true;
+        *out = ctx.release();
+        return SDRT_OK;
+    }
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return SDRT_ERR_CUDA;
+    if (device < 0 || device >= n) return SDRT_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SDRT_ERR_CUDA;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SDRT_ERR_CUDA;
+    ctx->nsm = prop.multiProcessorCount;
+    if (ctx->flag.alloc(sizeof(int)) != cudaSuccess) return SDRT_ERR_CUDA;
+    if (cudaMemset(ctx->flag.p, 0, sizeof(int)) != cudaSuccess) return SDRT_ERR_CUDA;
+    *out = ctx.release();
+    return SDRT_OK;
+}
+
+void sdrt_destroy(sdrt_ctx* ctx) {
+    if (!ctx) return;
+    if (!ctx->host_only) cudaSetDevice(ctx->device);
+    delete ctx;
+}
+
+const char* sdrt_last_error(const sdrt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int sdrt_set_stream(sdrt_ctx* ctx, void* stream) {
+    if (!ctx) return SDRT_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    for (auto& m : ctx->meshes)
+        if (m && m->graph) {
+            cudaGraphExecDestroy(m->graph);
+            m->graph = nullptr;
+        }
+    return SDRT_OK;
+}
+
+int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_id) {
+    if (!ctx || !d || !etype_id) return fail(ctx, SDRT_ERR_ARG, "null argument");
+    if (d->shape < 0 || d->shape > 4) return fail(ctx, SDRT_ERR_ARG, "unknown shape");
+    if (d->degree < 1 || d->degree > 6) return fail(ctx, SDRT_ERR_UNSUPPORTED, "degree must be in 1..6");
+    for (size_t i = 0; i < ctx->etypes.size(); ++i)
+        if (ctx->etypes[i]->desc.shape == d->shape && ctx->etypes[i]->desc.degree == d->degree) {
+            *etype_id = (int)i;
+            return SDRT_OK;
+        }
+    auto et = std::make_unique<EType>();
+    et->desc = *d;
+    try {
+        et->R = build_ref_element(d->shape, d->degree);
+    } catch (const std::exception& ex) {
+        return fail(ctx, SDRT_ERR_UNSUPPORTED, ex.what());
+    }
+    const RefElement& R = et->R;
+    et->Mi = R.nfe + R.nfiu;
+    et->Mi_pad = round_up(et->Mi, 8);
+    et->Md_pad = round_up(R.nsol, 8);
+    et->Mg_pad = round_up(R.nd * R.nsol, 8);
+    std::vector<double> Ai((size_t)R.nsol * et->Mi_pad, 0.0), Ad((size_t)(R.nfe + R.nfi) * et->Md_pad, 0.0);
+    for (int r = 0; r < R.nsol; ++r) {
+        for (int j = 0; j < R.nfe; ++j) Ai[(size_t)r * et->Mi_pad + j] = R.M0[(size_t)j * R.nsol + r];
+        for (int j = 0; j < R.nfiu; ++j) Ai[(size_t)r * et->Mi_pad + R.nfe + j] = R.M12[(size_t)j * R.nsol + r];
+        for (int k = 0; k < R.nfe; ++k) Ad[(size_t)k * et->Md_pad + r] = R.M14[(size_t)r * R.nfe + k];
+        for (int k = 0; k < R.nfi; ++k) Ad[(size_t)(R.nfe + k) * et->Md_pad + r] = R.M13[(size_t)r * R.nfi + k];
+    }
+    std::vector<float> Aif(Ai.begin(), Ai.end()), Adf(Ad.begin(), Ad.end());
+    std::vector<int> tab((size_t)R.nfiu * 4, 0);
+    for (int nu = 0; nu < R.nfi; ++nu) {
+        int k = R.fi_point[nu];
+        int& cnt = tab[(size_t)k * 4];
+        if (cnt >= 3) return fail(ctx, SDRT_ERR_UNSUPPORTED, "more than 3 DOFs at an internal point");
+        tab[(size_t)k * 4 + 1 + cnt] = nu | (R.fi_axis[nu] << 16);
+        ++cnt;
+    }
+    if (!ctx->host_only) {
+        SDRT_CUDA(upload(et->Ai[0], Ai));
+        SDRT_CUDA(upload(et->Ad[0], Ad));
+        SDRT_CUDA(upload(et->Ai[1], Aif));
+        SDRT_CUDA(upload(et->Ad[1], Adf));
+        SDRT_CUDA(upload(et->fe_face, R.fe_face));
+        SDRT_CUDA(upload(et->fi_tab, tab));
+    }
+    ctx->etypes.push_back(std::move(et));
+    *etype_id = (int)ctx->etypes.size() - 1;
+    return SDRT_OK;
+}
+
+int sdrt_get_etype_info(sdrt_ctx* ctx, int id, sdrt_etype_info* out) {
+    if (!ctx || !out) return SDRT_ERR_ARG;
+    if (id < 0 || id >= (int)ctx->etypes.size()) return fail(ctx, SDRT_ERR_ARG, "invalid element type id");
+    const RefElement& R = ctx->etypes[id]->R;
+    *out = {R.nd, R.nsol, R.nfe, R.nfi, R.nfiu, R.nfaces};
+    return SDRT_OK;
+}
+
+int sdrt_get_operator(sdrt_ctx* ctx, int id, int which, double* out, int64_t n) {
+    if (!ctx || !out) return SDRT_ERR_ARG;
+    if (id < 0 || id >= (int)ctx->etypes.size()) return fail(ctx, SDRT_ERR_ARG, "invalid element type id");
+    const RefElement& R = ctx->etypes[id]->R;
+    const std::vector<double>* src = nullptr;
+    switch (which) {
+        case 0: src = &R.M0; break;
+        case 1: src = &R.M12; break;
+        case 2: src = &R.M13; break;
+        case 3: src = &R.M14; break;
+        case 4: src = &R.M15; break;
+        case 5: src = &R.M16; break;
+        case 6: src = &R.xs; break;
+        case 7: src = &R.xfe; break;
+        default: return fail(ctx, SDRT_ERR_ARG, "unknown operator");
+    }
+    if ((int64_t)src->size() != n) return fail(ctx, SDRT_ERR_ARG, "size mismatch");
+    std::memcpy(out, src->data(), src->size() * sizeof(double));
+    return SDRT_OK;
+}
+
+int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks, int64_t nfaces,
+                    const sdrt_face* faces, int* mesh_id) {
+    if (!ctx || !phys || !blocks || !mesh_id || nblocks <= 0 || (nfaces > 0 && !faces))
+        return fail(ctx, SDRT_ERR_ARG, "null or empty argument");
+    if (phys->ndim != 2 && phys->ndim != 3) return fail(ctx, SDRT_ERR_ARG, "ndim must be 2 or 3");
+    if (phys->precision != SDRT_FP32 && phys->precision != SDRT_FP64) return fail(ctx, SDRT_ERR_ARG, "bad precision");
+    if (phys->system != SDRT_ADVECTION && phys->system != SDRT_EULER)
+        return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by this build");
+    if (phys->system == SDRT_ADVECTION && phys->riemann == SDRT_ROE)
+        return fail(ctx, SDRT_ERR_ARG, "Roe flux needs the Euler system");
+    auto m = std::make_unique<Mesh>();
+    m->phys = *phys;
+    const int nd = phys->ndim;
+    m->nd = nd;
+    m->nvar = (phys->system == SDRT_ADVECTION || phys->system == SDRT_ADVDIFF) ? 1 : nd + 2;
+    const bool f32 = phys->precision == SDRT_FP32;
+
+    // Layout.
+    int64_t canon = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        const sdrt_block& B = blocks[b];
+        if (B.etype < 0 || B.etype >= (int)ctx->etypes.size()) return fail(ctx, SDRT_ERR_ARG, "bad etype id");
+        if (B.nelem <= 0 || !B.verts) return fail(ctx, SDRT_ERR_ARG, "empty block");
+        const RefElement& R = ctx->etypes[B.etype]->R;
+        if (R.nd != nd) return fail(ctx, SDRT_ERR_ARG, "element dimension does not match physics");
+        auto mb = std::make_unique<MBlock>();
+        mb->etype = B.etype;
+        mb->nelem = B.nelem;
+        mb->ld = round_up(B.nelem, 32);
+        mb->u_off = m->state_len;
+        mb->fe_base = m->Ftot;
+        mb->canon_base = canon;
+        m->state_len += (int64_t)R.nsol * m->nvar * mb->ld;
+        m->Ftot += (int64_t)R.nfe * mb->ld;
+        m->ndof += (int64_t)R.nsol * m->nvar * B.nelem;
+        canon += (int64_t)R.nfe * B.nelem;
+        m->blocks.push_back(std::move(mb));
+    }
+    m->nfe_total = canon;
+    if (canon >= INT32_MAX || m->Ftot >= INT32_MAX) return fail(ctx, SDRT_ERR_UNSUPPORTED, "mesh too large for int32 maps");
+
+    // Metrics, physical points.
+    struct HostBlk {
+        std::vector<double> J, Ji, det, xfe;   // per element
+        std::vector<double> metric;            // [NM][ld]
+        std::vector<uint8_t> glued;            // per (e, f)
+    };
+    std::vector<HostBlk> hb(nblocks);
+    for (int b = 0; b < nblocks; ++b) {
+        const sdrt_block& B = blocks[b];
+        const RefElement& R = ctx->etypes[B.etype]->R;
+        MBlock& mb = *m->blocks[b];
+        const int nv = shape_nverts(R.shape);
+        const int NM = 1 + nd * nd + R.nfaces * (nd + 1);
+        HostBlk& H = hb[b];
+        H.J.resize((size_t)B.nelem * nd * nd);
+        H.Ji.resize((size_t)B.nelem * nd * nd);
+        H.det.resize(B.nelem);
+        H.xfe.resize((size_t)B.nelem * R.nfe * nd);
+        H.metric.assign((size_t)NM * mb.ld, 0.0);
+        H.glued.assign((size_t)B.nelem * R.nfaces, 0);
+        const auto& ref = ref_vertices(R.shape);
+        for (int e = 0; e < B.nelem; ++e) {
+            const double* X = B.verts + (size_t)e * nv * nd;
+            double* J = &H.J[(size_t)e * nd * nd];
+            double* Ji = &H.Ji[(size_t)e * nd * nd];
+            if (!element_jacobian(R.shape, X, nd, J))
+                return fail(ctx, SDRT_ERR_UNSUPPORTED, "element " + std::to_string(e) + " of block " +
+                                                           std::to_string(b) + " is not affine");
+            double det = det_inv(J, nd, Ji);
+            if (!(det > 0)) return fail(ctx, SDRT_ERR_MESH, "inverted or degenerate element");
+            H.det[e] = det;
+            H.metric[e] = 1.0 / det;
+            for (int d = 0; d < nd; ++d)
+                for (int i = 0; i < nd; ++i) H.metric[(size_t)(1 + d * nd + i) * mb.ld + e] = det * Ji[d * nd + i];
+            for (int s = 0; s < R.nfe; ++s)
+                for (int i = 0; i < nd; ++i) {
+                    double x = X[i];
+                    for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (R.xfe[s * nd + d] - ref[d]);
+                    H.xfe[((size_t)e * R.nfe + s) * nd + i] = x;
+                }
+            for (int s = 0; s < R.nsol; ++s)
+                for (int i = 0; i < nd; ++i) {
+                    double x = X[i];
+                    for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (R.xs[s * nd + d] - ref[d]);
+                    m->sol_xyz.push_back(x);
+                }
+        }
+    }
+
+    // Face pairing.
+    m->partner.assign(m->nfe_total, -1);
+    m->is_left.assign(m->nfe_total, 0);
+    auto face_normal = [&](int b, int e, int f, double* n, double& mag) {
+        const RefElement& R = ctx->etypes[blocks[b].etype]->R;
+        const double* Ji = &hb[b].Ji[(size_t)e * nd * nd];
+        double s = 0;
+        for (int i = 0; i < nd; ++i) {
+            n[i] = 0;
+            for (int d = 0; d < nd; ++d) n[i] += Ji[d * nd + i] * R.face_nrm[f * nd + d];
+            s += n[i] * n[i];
+        }
+        s = std::sqrt(s);
+        for (int i = 0; i < nd; ++i) n[i] /= s;
+        mag = hb[b].det[e] * s;
+    };
+    for (int64_t fi = 0; fi < nfaces; ++fi) {
+        const sdrt_face& F = faces[fi];
+        int bs[2] = {F.blk_l, F.blk_r}, es[2] = {F.elem_l, F.elem_r}, fs[2] = {F.face_l, F.face_r};
+        for (int s = 0; s < 2; ++s) {
+            if (bs[s] < 0 || bs[s] >= nblocks || es[s] < 0 || es[s] >= blocks[bs[s]].nelem)
+                return fail(ctx, SDRT_ERR_ARG, "face references a missing element");
+            const RefElement& R = ctx->etypes[blocks[bs[s]].etype]->R;
+            if (fs[s] < 0 || fs[s] >= R.nfaces) return fail(ctx, SDRT_ERR_ARG, "bad local face index");
+            uint8_t& g = hb[bs[s]].glued[(size_t)es[s] * R.nfaces + fs[s]];
+            if (g) return fail(ctx, SDRT_ERR_MESH, "a face is glued twice");
+            g = 1;
+        }
+        const RefElement& RL = ctx->etypes[blocks[F.blk_l].etype]->R;
+        const RefElement& RR = ctx->etypes[blocks[F.blk_r].etype]->R;
+        std::vector<int> iL, iR;
+        for (int s = 0; s < RL.nfe; ++s)
+            if (RL.fe_face[s] == F.face_l) iL.push_back(s);
+        for (int s = 0; s < RR.nfe; ++s)
+            if (RR.fe_face[s] == F.face_r) iR.push_back(s);
+        if (iL.size() != iR.size()) return fail(ctx, SDRT_ERR_MESH, "glued faces have different point counts");
+        const double* JL = &hb[F.blk_l].J[(size_t)F.elem_l * nd * nd];
+        double h = 0;
+        for (int k = 0; k < nd * nd; ++k) h = std::max(h, std::fabs(JL[k]));
+        const double tol = 1e-8 * h;
+        std::vector<char> used(iR.size(), 0);
+        const MBlock& bl = *m->blocks[F.blk_l];
+        const MBlock& br = *m->blocks[F.blk_r];
+        for (size_t a = 0; a < iL.size(); ++a) {
+            const double* xl = &hb[F.blk_l].xfe[((size_t)F.elem_l * RL.nfe + iL[a]) * nd];
+            int hit = -1;
+            for (size_t c = 0; c < iR.size(); ++c) {
+                if (used[c]) continue;
+                const double* xr = &hb[F.blk_r].xfe[((size_t)F.elem_r * RR.nfe + iR[c]) * nd];
+                double dd = 0;
+                for (int i = 0; i < nd; ++i) dd = std::max(dd, std::fabs(xr[i] + F.shift[i] - xl[i]));
+                if (dd <= tol) {
+                    hit = (int)c;
+                    break;
+                }
+            }
+            if (hit < 0) return fail(ctx, SDRT_ERR_MESH, "face flux points do not coincide (face " + std::to_string(fi) + ")");
+            used[hit] = 1;
+            int64_t gL = bl.canon_base + (int64_t)F.elem_l * RL.nfe + iL[a];
+            int64_t gR = br.canon_base + (int64_t)F.elem_r * RR.nfe + iR[hit];
+            m->partner[gL] = (int32_t)gR;
+            m->partner[gR] = (int32_t)gL;
+            m->is_left[gL] = 1;
+        }
+        // Face metric: the L side's unit normal for both sides; signed scales.
+        double nL[3], nR[3], magL, magR;
+        face_normal(F.blk_l, F.elem_l, F.face_l, nL, magL);
+        face_normal(F.blk_r, F.elem_r, F.face_r, nR, magR);
+        const int NDD = 1 + nd * nd;
+        for (int c = 0; c < nd; ++c) {
+            hb[F.blk_l].metric[(size_t)(NDD + F.face_l * (nd + 1) + c) * bl.ld + F.elem_l] = nL[c];
+            hb[F.blk_r].metric[(size_t)(NDD + F.face_r * (nd + 1) + c) * br.ld + F.elem_r] = nL[c];
+        }
+        hb[F.blk_l].metric[(size_t)(NDD + F.face_l * (nd + 1) + nd) * bl.ld + F.elem_l] = magL;
+        hb[F.blk_r].metric[(size_t)(NDD + F.face_r * (nd + 1) + nd) * br.ld + F.elem_r] = -magR;
+    }
+    for (int b = 0; b < nblocks; ++b)
+        for (uint8_t g : hb[b].glued)
+            if (!g) return fail(ctx, SDRT_ERR_MESH, "mesh has an unglued face (only closed / periodic meshes)");
+
+    // Device copies.
+    for (int b = 0; b < nblocks; ++b) {
+        MBlock& mb = *m->blocks[b];
+        const RefElement& R = ctx->etypes[mb.etype]->R;
+        std::vector<int> dmap((size_t)R.nfe * mb.ld, 0);
+        for (int e = 0; e < mb.nelem; ++e)
+            for (int s = 0; s < R.nfe; ++s) {
+                int64_t g = m->partner[mb.canon_base + (int64_t)e * R.nfe + s];
+                int pb = nblocks - 1;
+                while (m->blocks[pb]->canon_base > g) --pb;
+                const MBlock& q = *m->blocks[pb];
+                const int qnfe = ctx->etypes[q.etype]->R.nfe;
+                const int64_t rel = g - q.canon_base;
+                const int pe = (int)(rel / qnfe), ps = (int)(rel % qnfe);
+                dmap[(size_t)s * mb.ld + e] = (int)(q.fe_base + (int64_t)ps * q.ld + pe);
+            }
+        if (!ctx->host_only) {
+            SDRT_CUDA(upload(mb.map, dmap));
+            if (f32) {
+                std::vector<float> mf(hb[b].metric.begin(), hb[b].metric.end());
+                SDRT_CUDA(upload(mb.metric, mf));
+            } else {
+                SDRT_CUDA(upload(mb.metric, hb[b].metric));
+            }
+        }
+        // Tile widths: keep the residual kernel's shared memory within ~100 KB
+        // (two CTAs per SM), down to 8 elements per tile for large element types.
+        const EType& et = *ctx->etypes[mb.etype];
+        auto smem_of = [&](int TE, bool dual) {
+            int ra = std::max(R.nsol, R.nfi);
+            return (ra + et.Mi) * m->nvar * TE * (f32 ? 4 : 8) * (dual ? 2 : 1);
+        };
+        for (int dual = 0; dual < 2; ++dual) {
+            int TE = 32;
+            while (TE > 4 && smem_of(TE, dual) > 100 * 1024) TE /= 2;
+            if (smem_of(TE, dual) > 220 * 1024) {
+                if (!dual) return fail(ctx, SDRT_ERR_UNSUPPORTED, "element type too large for the shared-memory tile");
+                TE = 0;   // JVP unavailable for this block
+            }
+            (dual ? mb.tile_dual : mb.tile) = TE;
+        }
+    }
+    ctx->meshes.push_back(std::move(m));
+    *mesh_id = (int)ctx->meshes.size() - 1;
+    return SDRT_OK;
+}
+
+int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    if (!out) return fail(ctx, SDRT_ERR_ARG, "null output");
+    const Mesh& m = *ctx->meshes[mesh_id];
+    out->nvar = m.nvar;
+    out->nblocks = (int)m.blocks.size();
+    out->ndim = m.nd;
+    out->precision = m.phys.precision;
+    out->state_len = m.state_len;
+    out->ndof = m.ndof;
+    out->nfe_total = m.nfe_total;
+    return SDRT_OK;
+}
+
+int sdrt_get_block_layout(sdrt_ctx* ctx, int mesh_id, int block, sdrt_block_layout* out) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    const Mesh& m = *ctx->meshes[mesh_id];
+    if (!out || block < 0 || block >= (int)m.blocks.size()) return fail(ctx, SDRT_ERR_ARG, "bad block");
+    const MBlock& b = *m.blocks[block];
+    const RefElement& R = ctx->etypes[b.etype]->R;
+    *out = {b.etype, R.nsol, m.nvar, b.nelem, b.ld, R.nfe, b.u_off};
+    return SDRT_OK;
+}
+
+int sdrt_get_sol_points(sdrt_ctx* ctx, int mesh_id, double* out, int64_t n) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    const Mesh& m = *ctx->meshes[mesh_id];
+    if (!out || n != (int64_t)m.sol_xyz.size()) return fail(ctx, SDRT_ERR_ARG, "size mismatch");
+    std::memcpy(out, m.sol_xyz.data(), m.sol_xyz.size() * sizeof(double));
+    return SDRT_OK;
+}
+
+int sdrt_get_face_map(sdrt_ctx* ctx, int mesh_id, int32_t* partner, uint8_t* is_left, int64_t n) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    const Mesh& m = *ctx->meshes[mesh_id];
+    if (!partner || n != m.nfe_total) return fail(ctx, SDRT_ERR_ARG, "size mismatch");
+    std::memcpy(partner, m.partner.data(), m.partner.size() * sizeof(int32_t));
+    if (is_left) std::memcpy(is_left, m.is_left.data(), m.is_left.size());
+    return SDRT_OK;
+}
+
+int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U, void* R) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (!U || !R || U == R) return fail(ctx, SDRT_ERR_ARG, "U and R must be distinct device arrays");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if (m.phys.precision == SDRT_FP32) {
+        KEpi<float> E{};
+        E.mode = EPI_STORE;
+        E.out = static_cast<float*>(R);
+        E.flag = ctx->flag.as<int>();
+        return run_residual<float>(ctx, m, static_cast<const float*>(U), nullptr, E);
+    }
+    KEpi<double> E{};
+    E.mode = EPI_STORE;
+    E.out = static_cast<double*>(R);
+    E.flag = ctx->flag.as<int>();
+    return run_residual<double>(ctx, m, static_cast<const double*>(U), nullptr, E);
+}
+
+static int rk4_eager(sdrt_ctx* ctx, Mesh& m, void* U, double dt) {
+    if (m.phys.precision == SDRT_FP32) return rk4_stages<float>(ctx, m, static_cast<float*>(U), dt);
+    return rk4_stages<double>(ctx, m, static_cast<double*>(U), dt);
+}
+
+int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (!U || nsteps < 0 || !(std::isfinite(dt))) return fail(ctx, SDRT_ERR_ARG, "bad argument");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if ((r = ensure_workspace(ctx, m, false, true))) return r;
+    int s = 0;
+    if (!m.warmed && nsteps > 0) {
+        // First step runs eagerly (loads the kernels) before any graph capture.
+        if ((r = rk4_eager(ctx, m, U, dt))) return r;
+        m.warmed = true;
+        s = 1;
+    }
+    if (s >= nsteps) return SDRT_OK;
+    if (!m.graph || m.graph_u != U || m.graph_dt != dt) {
+        if (m.graph) {
+            cudaGraphExecDestroy(m.graph);
+            m.graph = nullptr;
+        }
+        if (ctx->stream == nullptr) {
+            // Capture needs a non-default stream: run eagerly.
+            for (; s < nsteps; ++s)
+                if ((r = rk4_eager(ctx, m, U, dt))) return r;
+            return SDRT_OK;
+        }
+        cudaGraph_t g;
+        const int64_t before = ctx->launches;
+        m.graph_slots.clear();
+        SDRT_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        ctx->capture_slots = &m.graph_slots;
+        r = rk4_eager(ctx, m, U, dt);
+        ctx->capture_slots = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        ctx->launches = before;
+        if (r) return r;
+        if (ce != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&m.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        m.graph_u = U;
+        m.graph_dt = dt;
+    }
+    const int per_step = (int)m.blocks.size() * 8;
+    for (; s < nsteps; ++s) {
+        SDRT_CUDA(cudaGraphLaunch(m.graph, ctx->stream));
+        ctx->launches += per_step;
+    }
+    // Events inside the graph hold the timings of its last replay.
+    if (ctx->prof) ctx->pending.insert(ctx->pending.end(), m.graph_slots.begin(), m.graph_slots.end());
+    return SDRT_OK;
+}
+
+int sdrt_profile_enable(sdrt_ctx* ctx, int enable) {
+    if (!ctx) return SDRT_ERR_ARG;
+    if (ctx->host_only) return fail(ctx, SDRT_ERR_STATE, "host-only context");
+    ctx->prof = enable != 0;
+    ctx->pending.clear();
+    ctx->eager_next = 0;
+    for (auto& m : ctx->meshes)
+        if (m && m->graph) {
+            cudaGraphExecDestroy(m->graph);
+            m->graph = nullptr;
+        }
+    return SDRT_OK;
+}
+
+int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out) {
+    if (!ctx || !ms_out || !count_out) return SDRT_ERR_ARG;
+    if (ctx->host_only) return fail(ctx, SDRT_ERR_STATE, "host-only context");
+    SDRT_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int s : ctx->pending) {
+        float t = 0;
+        SDRT_CUDA(cudaEventElapsedTime(&t, ctx->ev[2 * s], ctx->ev[2 * s + 1]));
+        ms_out[ctx->slot_kind[s]] += t;
+        count_out[ctx->slot_kind[s]] += 1;
+    }
+    ctx->pending.clear();
+    ctx->eager_next = 0;
+    return SDRT_OK;
+}
+
+int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* Uin, void* Uout, double dt, int nsteps) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (!Uin || !Uout) return fail(ctx, SDRT_ERR_ARG, "null host buffer");
+    Mesh& m = *ctx->meshes[mesh_id];
+    const size_t bytes = (size_t)m.state_len * (m.phys.precision == SDRT_FP32 ? 4 : 8);
+    if (!m.uhost_dev.p) SDRT_CUDA(m.uhost_dev.alloc(bytes));
+    SDRT_CUDA(cudaMemcpyAsync(m.uhost_dev.p, Uin, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if ((r = sdrt_rk4_step(ctx, mesh_id, m.uhost_dev.p, dt, nsteps))) return r;
+    SDRT_CUDA(cudaMemcpyAsync(Uout, m.uhost_dev.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    SDRT_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SDRT_OK;
+}
+
+int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* V, void* JV) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (!U || !V || !JV || JV == U || JV == V) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if ((r = ensure_workspace(ctx, m, true, false))) return r;
+    if (m.phys.precision == SDRT_FP32) {
+        KEpi<float> E{};
+        E.mode = EPI_STORE;
+        E.out = static_cast<float*>(JV);
+        E.flag = ctx->flag.as<int>();
+        return run_residual<float>(ctx, m, static_cast<const float*>(U), static_cast<const float*>(V), E);
+    }
+    KEpi<double> E{};
+    E.mode = EPI_STORE;
+    E.out = static_cast<double*>(JV);
+    E.flag = ctx->flag.as<int>();
+    return run_residual<double>(ctx, m, static_cast<const double*>(U), static_cast<const double*>(V), E);
+}
+
+int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    (void)U;
+    (void)W;
+    (void)JTW;
+    return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP not available in this build");
+}
+
+int sdrt_sync(sdrt_ctx* ctx) {
+    if (!ctx) return SDRT_ERR_ARG;
+    if (ctx->host_only) return SDRT_OK;
+    SDRT_CUDA(cudaStreamSynchronize(ctx->stream));
+    int h = 0;
+    SDRT_CUDA(cudaMemcpy(&h, ctx->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        SDRT_CUDA(cudaMemset(ctx->flag.p, 0, sizeof(int)));
+        return fail(ctx, SDRT_ERR_NONFINITE, "a kernel produced a non-finite value");
+    }
+    return SDRT_OK;
+}
+
+int64_t sdrt_launch_count(const sdrt_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

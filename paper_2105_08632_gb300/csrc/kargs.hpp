@@ -1,0 +1,64 @@
+// Argument blocks shared by the host launch code and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+
+namespace sdrt {
+
+enum System { SYS_ADVECTION = 0, SYS_ADVDIFF = 1, SYS_EULER = 2, SYS_NS = 3 };
+enum Riemann { RIE_UPWIND = 0, RIE_RUSANOV = 1, RIE_ROE = 2 };
+
+// Per-block device data of one mesh block (element type + its elements).
+//
+// State arrays: value (rho, v, e) of the block at u_off + (rho * V + v) * ld + e.
+// External-point arrays ("face states", UFE): value (sigma, v, e) at
+//   v * F_tot + fe_base + sigma * ld + e   (F_tot = sum of nfe * ld over blocks).
+// Metric rows (k, e) at metric[k * ld + e]:
+//   k = 0                    1 / det J
+//   k = 1 + d * ND + i       S_di = det J * (J^{-1})_di = det J dx~_d / dx_i
+//   k = 1 + ND^2 + f(ND+1)+c unit normal n_L of face f (the face's L side), c < ND
+//   k = 1 + ND^2 + f(ND+1)+ND  signed scale s = +-det J |J^{-T} n~_f| (+ on the L side)
+template <typename T>
+struct KBlock {
+    int nsol, nfe, nfi, nfiu, nfaces;
+    int nelem, ld;
+    int64_t u_off;       // element offset of the block in a state array
+    int64_t fe_base;     // offset of the block's first external point in UFE
+    const T* Ai;         // interpolation operator, transposed: [nsol][Mi_pad], rows [M0; M12]
+    int Mi, Mi_pad;      // Mi = nfe + nfiu
+    const T* Ad;         // divergence operator, transposed: [nfe + nfi][Md_pad], columns [M14 | M13]
+    int Md_pad;
+    const T* Ag;         // viscous: gradient operator on U, transposed: [nsol][Mg_pad], rows (d, rho) of M15 P M12
+    const T* Agf;        // viscous: M16 transposed: [nfe][Mg_pad]
+    int Mg_pad;
+    const int* fe_face;  // [nfe] local face of each external point
+    const int* fi_tab;   // [nfiu][4]: count, then (nu | axis << 16) per internal DOF of the point
+    const T* metric;     // [NM][ld]
+    const int* map;      // [nfe][ld] UFE index (without the v * F_tot term) of the paired point
+};
+
+template <typename T>
+struct KPhys {
+    T a[3];
+    T gamma, mu, prandtl, beta, eta;
+};
+
+// Stage update fused into the divergence epilogue (R = dU/dt of the tile):
+//   EPI_STORE  out = R
+//   EPI_RK_FIRST   uacc = u0 + cacc R ; unext = u0 + cnext R
+//   EPI_RK_MID     uacc = uacc + cacc R ; unext = u0 + cnext R
+//   EPI_RK_LAST    out = uacc + cacc R
+enum EpiMode { EPI_STORE = 0, EPI_RK_FIRST = 1, EPI_RK_MID = 2, EPI_RK_LAST = 3 };
+
+template <typename T>
+struct KEpi {
+    int mode;
+    T* out;
+    const T* u0;
+    T* uacc;
+    T* unext;
+    T cacc, cnext;
+    int* flag;           // set to 1 when a non-finite value is produced
+};
+
+}  // namespace sdrt

@@ -1,0 +1,138 @@
+"""Host-side checks of libsdrt (no GPU needed): the library loads and exports
+every entry point of include/sdrt.h; its FP64 operators (built from a
+Legendre-product basis) equal the oracle's (monomial basis); its face maps
+equal the oracle's bit for bit; bad arguments give error codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from inputs import meshes
+from oracle import mesh as omesh
+from oracle import operators as oops
+
+sdrt = pytest.importorskip("paper_2105_08632_gb300.sdrt")
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "sdrt.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(sdrt.LIB_PATH):
+        from paper_2105_08632_gb300 import build
+        build.build()
+    return sdrt.lib()
+
+
+@pytest.fixture(scope="module")
+def hctx(lib):
+    c = sdrt.sdrt_create(-1)
+    yield c
+    sdrt.sdrt_destroy(c)
+
+
+def test_exports_every_declared_symbol(lib):
+    text = open(HEADER).read()
+    declared = set(re.findall(r"^\s*(?:int|void|int64_t|const char\*)\s+(sdrt_\w+)\s*\(", text, re.M))
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(sdrt.EXPORTED) | declared
+
+
+CASES = [(s, p) for s in ("tri", "quad", "tet", "pri", "hex") for p in (1, 2, 3, 4)]
+
+
+@pytest.mark.parametrize("shape,p", CASES)
+def test_operators_match_oracle(hctx, shape, p):
+    et = sdrt.sdrt_setup_element_type(hctx, shape, p)
+    info = sdrt.sdrt_get_etype_info(hctx, et)
+    ref = oops.get(shape, p)
+    assert (info["nsol"], info["nfe"], info["nfi"], info["nfiu"]) == (ref.n_sol, ref.n_fe, ref.n_fi, ref.n_fiu)
+    np.testing.assert_allclose(sdrt.sdrt_get_operator(hctx, et, "xs"), ref.xs, atol=1e-14)
+    np.testing.assert_allclose(sdrt.sdrt_get_operator(hctx, et, "xfe"), ref.xfe, atol=1e-14)
+    for name in ("M0", "M12", "M13", "M14", "M15", "M16"):
+        got = sdrt.sdrt_get_operator(hctx, et, name)
+        want = getattr(ref, name)
+        tol = 1e-12 * max(1.0, np.abs(want).max()) * max(1.0, ref.cond_flux / 1e3)
+        assert np.abs(got - want).max() < tol, (name, np.abs(got - want).max())
+
+
+MESHES = [("tri", (5, 3), 2), ("quad", (3, 4), 3), ("tet", (3, 2, 2), 3), ("pri", (2, 3, 2), 2),
+          ("hex", (2, 2, 3), 2), ("tet", (2, 2, 2), 4)]
+
+
+def _lib_mesh(ctx, mesh, p, system="euler", precision="fp64"):
+    nd = mesh["blocks"][0]["verts"].shape[2]
+    phys = sdrt.make_physics(system, nd, "rusanov" if system == "euler" else "upwind", precision)
+    blocks = [(sdrt.sdrt_setup_element_type(ctx, b["shape"], p), b["verts"]) for b in mesh["blocks"]]
+    mid = sdrt.sdrt_setup_mesh(ctx, phys, blocks, (mesh["faces"], mesh["shift"]))
+    return mid
+
+
+@pytest.mark.parametrize("kind,n,p", MESHES)
+def test_face_map_bit_exact(hctx, kind, n, p):
+    mesh = meshes.box_mesh(kind, n, [0.0] * len(n), [1.0] * len(n))
+    mid = _lib_mesh(hctx, mesh, p)
+    info = sdrt.sdrt_get_mesh_info(hctx, mid)
+    part, left = sdrt.sdrt_get_face_map(hctx, mid, info["nfe_total"])
+    geom = omesh.build(mesh, p)
+    assert np.array_equal(part.astype(np.int64), geom.partner)
+    assert np.array_equal(left.astype(bool), geom.is_left)
+
+
+def test_mixed_mesh_face_map(hctx):
+    """Tetrahedra glued to z-extruded prisms, prisms (x-extruded) glued to hexahedra."""
+    for kinds, degs in ((["tet", "tet", "pri"], {"tet": 2, "pri": 2}),
+                        (["hex", "pri_x", "pri_x"], {"hex": 2, "pri": 2})):
+        mesh = meshes.box_mesh(kinds, (2, 2, 3), [0, 0, 0], [1, 1, 1])
+        phys = sdrt.make_physics("euler", 3, "rusanov", "fp64")
+        blocks = [(sdrt.sdrt_setup_element_type(hctx, b["shape"], degs[b["shape"]]), b["verts"])
+                  for b in mesh["blocks"]]
+        mid = sdrt.sdrt_setup_mesh(hctx, phys, blocks, (mesh["faces"], mesh["shift"]))
+        info = sdrt.sdrt_get_mesh_info(hctx, mid)
+        part, left = sdrt.sdrt_get_face_map(hctx, mid, info["nfe_total"])
+        geom = omesh.build(mesh, degs)
+        assert np.array_equal(part.astype(np.int64), geom.partner)
+        assert np.array_equal(left.astype(bool), geom.is_left)
+
+
+def test_sol_points_match_oracle(hctx):
+    mesh = meshes.box_mesh("tet", (2, 3, 2), [-1.0, 0.0, 2.0], [1.0, 3.0, 3.0])
+    mid = _lib_mesh(hctx, mesh, 3)
+    info = sdrt.sdrt_get_mesh_info(hctx, mid)
+    lay = sdrt.sdrt_get_block_layout(hctx, mid, 0)
+    n = lay["nelem"] * lay["nsol"] * 3
+    got = sdrt.sdrt_get_sol_points(hctx, mid, n).reshape(lay["nelem"], lay["nsol"], 3)
+    geom = omesh.build(mesh, 3)
+    np.testing.assert_allclose(got, geom.blocks[0].xsol, atol=1e-13)
+    assert lay["ld"] % 32 == 0 and lay["ld"] >= lay["nelem"]
+    assert info["ndof"] == lay["nelem"] * lay["nsol"] * 5
+
+
+def test_error_codes(hctx):
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_element_type(hctx, 7, 2)
+    assert ei.value.code == -1
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_get_mesh_info(hctx, 12345)
+    assert ei.value.code == -1
+    # a mesh with a missing face is rejected
+    mesh = meshes.box_mesh("tet", (2, 2, 2), [0, 0, 0], [1, 1, 1])
+    phys = sdrt.make_physics("euler", 3, "rusanov", "fp64")
+    et = sdrt.sdrt_setup_element_type(hctx, "tet", 2)
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, phys, [(et, mesh["blocks"][0]["verts"])], (mesh["faces"][1:], mesh["shift"][1:]))
+    assert ei.value.code == -7
+    # mismatched faces (wrong local face index) are rejected
+    bad = mesh["faces"].copy()
+    bad[0, 2] = (bad[0, 2] + 1) % 4
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, phys, [(et, mesh["blocks"][0]["verts"])], (bad, mesh["shift"]))
+    assert ei.value.code == -7
+    # device computation is refused on a host-only context
+    mid = sdrt.sdrt_setup_mesh(hctx, phys, [(et, mesh["blocks"][0]["verts"])], (mesh["faces"], mesh["shift"]))
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_residual(hctx, mid, 1, 2)
+    assert ei.value.code == -4
