@@ -289,15 +289,17 @@ def main():
     pin_in = torch.from_numpy(host).pin_memory()
     pin_out = torch.empty_like(pin_in).pin_memory()
     e2e_t = []
-    for i in range(args.e2e_steps + 1):
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         t0 = time.perf_counter()
         M.rk4_step_host(pin_in, pin_out, DT, 1)
         t1 = time.perf_counter()
         if i > 0:
             e2e_t.append(t1 - t0)
     nbytes = host.nbytes
-    e2e = {"value": world * ndof * 4 / float(np.mean(e2e_t)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "api": "sdrt_rk4_step_host (pinned host buffers, 1 step per call)"}
+    e2e = None
+    if e2e_t:
+        e2e = {"value": world * ndof * 4 / float(np.mean(e2e_t)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "api": "sdrt_rk4_step_host (pinned host buffers, 1 step per call)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -148,12 +148,17 @@ int prof_begin(sdrt_ctx* ctx, int kind) {
         ctx->slot_kind[s] = kind;
         ctx->pending.push_back(s);
     }
-    cudaEventRecord(ctx->ev[2 * s], ctx->stream);
+    // Inside a stream capture a plain record is only a dependency marker: an
+    // external record becomes an event-record node that replays record.
+    if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s], ctx->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ctx->ev[2 * s], ctx->stream);
     return s;
 }
 
 void prof_end(sdrt_ctx* ctx, int s) {
-    if (s >= 0) cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream);
+    if (s < 0) return;
+    if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s + 1], ctx->stream, cudaEventRecordExternal);
+    else cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream);
 }
 
 int fail(sdrt_ctx* c, int code, const std::string& msg) {

@@ -1,0 +1,34 @@
+"""Per-launch event timing of the library (used by bench.py's roofline): the
+counts match the launches of an RK4 step, with and without the captured graph."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from tests import gpu_util as gu  # noqa: E402
+
+
+def test_profile_counts_rk4_steps():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_08632_gb300 import build, sdrt
+    build.build()
+    stream = torch.cuda.Stream(0)
+    with torch.cuda.stream(stream):
+        ctx = sdrt.Context(0, stream.cuda_stream)
+        M, geom, oph, _ = gu.build_pair(ctx, "tet", (3, 3, 2), 2, "euler", "rusanov", "fp32")
+        U = torch.from_numpy(M.pack(gu.oracle_state(geom, gu.smooth_gas, 5))).to("cuda")
+        M.rk4_step(U, 1e-3, 1)                 # eager warm-up step
+        sdrt.sdrt_profile_enable(ctx.ptr, True)
+        for _ in range(3):                     # graph captured on the first, replayed after
+            M.rk4_step(U, 1e-3, 1)
+            prof = sdrt.sdrt_profile_collect(ctx.ptr)
+            assert prof["interp_ext"][1] == 4 and prof["residual"][1] == 4
+            assert prof["residual"][0] > 0 and prof["interp_ext"][0] > 0
+        R = torch.zeros_like(U)
+        M.residual(U, R)
+        prof = sdrt.sdrt_profile_collect(ctx.ptr)
+        assert prof["interp_ext"][1] == 1 and prof["residual"][1] == 1
+        sdrt.sdrt_profile_enable(ctx.ptr, False)
+        M.sync()
+        ctx.close()
