@@ -173,6 +173,32 @@ int sdrt_get_face_map(sdrt_ctx* ctx, int mesh_id, int32_t* partner_out, uint8_t*
  * above, precision of the mesh); may not alias. */
 int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev);
 
+/* Size in bytes of the fixed face-state buffer used by sdrt_residual_noalloc. */
+#define SDRT_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Same result as sdrt_residual, for callers that cannot allocate device
+ * memory (for example a solver running as a plugin inside a framework whose
+ * memory pool owns the whole device, or a time-critical loop that cannot take
+ * cudaMalloc's implicit device synchronisation).  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ *  - Allocates nothing: the face states exchanged between elements go to a
+ *    fixed SDRT_NOALLOC_SCRATCH_BYTES buffer that is part of the library image
+ *    on every GPU that loads the library (held until process exit).  The
+ *    caller passes U_dev and R_dev as for sdrt_residual.
+ *  - The mesh must need at most SDRT_NOALLOC_SCRATCH_BYTES of face states
+ *    (nvar * external flux points (rows padded to 32 elements) * 4 or 8
+ *    bytes); larger meshes are rejected with SDRT_ERR_UNSUPPORTED and a
+ *    message giving both sizes.  Example: Euler on 40,000 tetrahedra of degree
+ *    3 in FP32 needs 40,000 x 40 points x 5 x 4 B = 32,000,000 B and fits
+ *    (limit 33,554,432 B).
+ *  - The first call on a device looks up the buffer's device address; make
+ *    that first call before any stream capture.
+ *  - All calls share the one buffer: calls whose kernels can overlap on the
+ *    GPU (different streams, other contexts) race and give wrong results;
+ *    serialise them.  Nothing needs clearing between calls: each call writes
+ *    every entry it reads. */
+int sdrt_residual_noalloc(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev);
+
 /* nsteps classical RK4 steps of size dt, in place on U_dev (device).  Each
  * stage is one residual evaluation fused with its stage update (paper Sec. 2.1
  * explicit RK; RK4 stability polynomial Eq. "rk_exponential"). */

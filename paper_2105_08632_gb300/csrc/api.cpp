@@ -18,6 +18,7 @@
 #include "kargs.hpp"
 #include "launch.hpp"
 #include "refel.hpp"
+#include "internal.hpp"
 
 using namespace sdrt;
 
@@ -915,3 +916,63 @@ int sdrt_sync(sdrt_ctx* ctx) {
 int64_t sdrt_launch_count(const sdrt_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal hooks (internal.hpp) used by the allocation-free entry point.
+
+namespace {
+
+// The value-residual launches of run_residual, with the face states in `ufe`.
+template <typename T>
+int residual_into(sdrt_ctx* ctx, Mesh& m, const T* U, T* R, T* ufe) {
+    const KPhys<T> P = make_phys<T>(m.phys);
+    KEpi<T> E{};
+    E.mode = EPI_STORE;
+    E.out = R;
+    E.flag = ctx->flag.as<int>();
+    for (auto& bp : m.blocks) {
+        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+        launch_interp_ext<T>(K, m.nvar, U, ufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
+        ++ctx->launches;
+    }
+    for (auto& bp : m.blocks) {
+        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+        int r = launch_residual<T>(K, m.phys.system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER, m.phys.riemann,
+                                   m.nd, U, nullptr, ufe, nullptr, m.Ftot, P, E, bp->tile,
+                                   grid_for(ctx, *bp, bp->tile, 2), ctx->stream);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
+        ++ctx->launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+}  // namespace
+
+namespace sdrt {
+
+int internal_device(const sdrt_ctx* ctx) { return (!ctx || ctx->host_only) ? -1 : ctx->device; }
+
+int internal_fail(sdrt_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+
+int internal_residual_with_scratch(sdrt_ctx* ctx, int mesh_id, const void* U, void* R, void* scratch,
+                                   size_t scratch_bytes) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (!U || !R || U == R || !scratch) return fail(ctx, SDRT_ERR_ARG, "U and R must be distinct device arrays");
+    Mesh& m = *ctx->meshes[mesh_id];
+    const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
+    const size_t need = (size_t)m.nvar * (size_t)m.Ftot * es;
+    if (need > scratch_bytes)
+        return fail(ctx, SDRT_ERR_UNSUPPORTED,
+                    "mesh needs " + std::to_string(need) + " bytes of face-state scratch, more than the " +
+                        std::to_string(scratch_bytes) + "-byte static buffer of the allocation-free entry point");
+    if (m.phys.precision == SDRT_FP32)
+        return residual_into<float>(ctx, m, static_cast<const float*>(U), static_cast<float*>(R),
+                                    static_cast<float*>(scratch));
+    return residual_into<double>(ctx, m, static_cast<const double*>(U), static_cast<double*>(R),
+                                 static_cast<double*>(scratch));
+}
+
+}  // namespace sdrt

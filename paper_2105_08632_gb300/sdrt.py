@@ -25,7 +25,7 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_get_etype_info", "sdrt_get_operator", "sdrt_setup_mesh", "sdrt_get_mesh_info",
             "sdrt_get_block_layout", "sdrt_get_sol_points", "sdrt_get_face_map", "sdrt_residual",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
-            "sdrt_profile_enable", "sdrt_profile_collect"]
+            "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc"]
 
 
 class SdrtError(RuntimeError):
@@ -106,6 +106,7 @@ def lib():
         "sdrt_launch_count": (I64, [P]),
         "sdrt_profile_enable": (I, [P, I]),
         "sdrt_profile_collect": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "sdrt_residual_noalloc": (I, [P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -226,6 +227,12 @@ def sdrt_get_face_map(ctx, mesh, n):
 
 def sdrt_residual(ctx, mesh, U, R):
     _check(ctx, lib().sdrt_residual(ctx, int(mesh), _ptr(U), _ptr(R)))
+
+
+def sdrt_residual_noalloc(ctx, mesh, U, R):
+    """sdrt_residual without any device allocation (fixed library-image scratch;
+    see include/sdrt.h for the size limit and the sharing rules)."""
+    _check(ctx, lib().sdrt_residual_noalloc(ctx, int(mesh), _ptr(U), _ptr(R)))
 
 
 def sdrt_rk4_step(ctx, mesh, U, dt, nsteps=1):
