@@ -69,20 +69,23 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def algorithmic_bytes(nsol, nfe, nvar, nfaces, nd, s, nelem):
-    """Algorithmic bytes of one RK4 step, per kernel launch kind.
+def algorithmic_bytes(nsol, nfe, nfiu, nvar, nfaces, nd, s, nelem):
+    """Algorithmic bytes per launch of the two kernels of one RK4 stage
+    (padding of the records excluded).
 
-    interp_ext : read U (nsol V s), write own face states (nfe V s)
-    residual   : read stage input (nsol V s), read partner face states (nfe V s),
-                 metric ((1 + nd^2 + nfaces (nd+1)) s), face map (nfe * 4 B),
-                 stage update averaged over the 4 RK4 stages: 3 state volumes
-                 (read u0 / read+write accumulator / write next stage), i.e.
-                 stage 1: 2 writes; stages 2-3: 2 reads + 2 writes; stage 4:
-                 1 read + 1 write -> (2 + 4 + 4 + 2) / 4 = 3
+    k_interp_rec : read U (nsol V s); write the external-point states (nfe V s)
+                   and the internal-point states (nfiu V s)
+    k_flux_rec   : read own and partner external-point states (2 nfe V s), the
+                   internal-point states (nfiu V s), the metric
+                   ((1 + nd^2 + nfaces (nd+1)) s), the partner permutation
+                   (nfe B) and partner face offsets (nfaces * 4 B); stage update
+                   averaged over the 4 RK4 stages in state volumes (nsol V s):
+                   stage 1 read u0 + 2 writes = 3, stages 2-3 2 reads + 2 writes
+                   = 4, stage 4 read + write = 2 -> 13 / 4 = 3.25
     """
-    interp = (nsol + nfe) * nvar * s
+    interp = (nsol + nfe + nfiu) * nvar * s
     metric = (1 + nd * nd + nfaces * (nd + 1)) * s
-    resid = (nsol + nfe) * nvar * s + metric + nfe * 4 + 3 * nsol * nvar * s
+    resid = (2 * nfe + nfiu) * nvar * s + metric + nfe + 4 * nfaces + 3.25 * nsol * nvar * s
     return interp * nelem, resid * nelem
 
 
@@ -127,20 +130,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def ncu_traffic(kernels_src):
-    """dram bytes per launch of the residual kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def kernel_sources_sha():
+    """Hash of every CUDA source of the library (identifies the kernel build)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_residual_tet_p3_euler_fp32.txt")
+    csrc = os.path.join(ROOT, "paper_2105_08632_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".hpp")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "k_flux_rec_tet_p3_euler_fp32.txt")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(kernels_src, "rb").read()).hexdigest()[:16]
+    sha = kernel_sources_sha()
     vals = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernels_cu_sha256_16") != sha:
+    if vals.get("kernel_sources_sha256_16") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])
@@ -268,22 +281,25 @@ def main():
     # Roofline of the dominant kernel (the residual / divergence kernel).
     s = 4 if args.precision == "fp32" else 8
     info = sdrt.sdrt_get_etype_info(ctx.ptr, M.etypes[0])
-    b_interp, b_resid = algorithmic_bytes(nsol, info["nfe"], nvar, info["nfaces"], 3, s, nelem)
+    b_interp, b_resid = algorithmic_bytes(nsol, info["nfe"], info["nfiu"], nvar, info["nfaces"], 3, s, nelem)
     ms_r, n_r = prof["residual"]
     ms_i, n_i = prof["interp_ext"]
     avg_r = ms_r / max(n_r, 1)
     avg_i = ms_i / max(n_i, 1)
     peak, peak_kind = peaks()
     achieved = b_resid / (avg_r / 1e3) / 1e9 if n_r else None
-    traffic = ncu_traffic(os.path.join(ROOT, "paper_2105_08632_gb300", "csrc", "kernels.cu"))
-    roofline = {"bound": "hbm", "kernel": "k_residual", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    traffic = ncu_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_flux_rec", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                                else "of fallback"),
                 "algorithmic_bytes_per_launch": b_resid, "avg_launch_ms": avg_r,
-                "interp_ext": {"algorithmic_bytes_per_launch": b_interp, "avg_launch_ms": avg_i,
-                               "achieved_gbs": b_interp / (avg_i / 1e3) / 1e9 if n_i else None},
-                "step_share": {"k_residual": ms_r / max(total_ms, 1e-9) if not dist else None,
-                               "k_interp_ext": ms_i / max(total_ms, 1e-9) if not dist else None}}
+                "kernel_sources_sha256_16": kernel_sources_sha(),
+                "k_interp_rec": {"algorithmic_bytes_per_launch": b_interp, "avg_launch_ms": avg_i,
+                                 "achieved_gbs": b_interp / (avg_i / 1e3) / 1e9 if n_i else None},
+                "step_share": {"k_flux_rec": ms_r / max(total_ms, 1e-9) if not dist else None,
+                               "k_interp_rec": ms_i / max(total_ms, 1e-9) if not dist else None},
+                "step_hbm_frac": ((b_resid + b_interp) * 4 / (ms_per_step / 1e3) / 1e9) / peak}
 
     # End to end through the host-buffer entry point (pinned memory).
     pin_in = torch.from_numpy(host).pin_memory()

@@ -56,8 +56,8 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& h) {
 struct EType {
     sdrt_etype_desc desc{};
     RefElement R;
-    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0;
-    DevBuf Ai[2], Ad[2];          // [0] double, [1] float
+    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0, Mir = 0;
+    DevBuf Ai[2], Ad[2], Air[2];  // [0] double, [1] float
     DevBuf fe_face, fi_tab;
 };
 
@@ -67,6 +67,10 @@ struct MBlock {
     DevBuf metric, map;
     int tile = 32;                // elements per CTA tile
     int tile_dual = 32;
+    // Record layout of the register-blocked path (kernels_fast.cu).
+    int ers = 0, frs = 0, frec = 0, nmp = 0, pstride = 0;
+    int64_t rec_base = 0, fiur_base = 0;
+    DevBuf maos, pfr, perm, recoff;
 };
 
 struct Mesh {
@@ -74,10 +78,12 @@ struct Mesh {
     int nvar = 0, nd = 0;
     std::vector<std::unique_ptr<MBlock>> blocks;
     int64_t state_len = 0, Ftot = 0, ndof = 0, nfe_total = 0;
+    bool fast = false;                // every block on the register-blocked record path
+    int64_t rec_total = 0, fiur_total = 0;
     std::vector<int32_t> partner;     // canonical face map
     std::vector<uint8_t> is_left;
     std::vector<double> sol_xyz;
-    DevBuf ufe, dufe, ustage, uacc, uhost_dev;
+    DevBuf ufe, dufe, ustage, uacc, uhost_dev, rec, drec, fiur, dfiur;
     // RK4 graph cache
     cudaGraphExec_t graph = nullptr;
     const void* graph_u = nullptr;
@@ -250,6 +256,19 @@ KBlock<T> make_kblock(const EType& et, const MBlock& b) {
     K.fi_tab = et.fi_tab.as<int>();
     K.metric = b.metric.as<T>();
     K.map = b.map.as<int>();
+    K.Air = et.Air[pi].as<T>();
+    K.Mir = et.Mir;
+    K.ers = b.ers;
+    K.frs = b.frs;
+    K.frec = b.frec;
+    K.nmp = b.nmp;
+    K.pstride = b.pstride;
+    K.rec_base = b.rec_base;
+    K.fiur_base = b.fiur_base;
+    K.maos = b.maos.as<T>();
+    K.pfr = b.pfr.as<int>();
+    K.perm = b.perm.as<unsigned char>();
+    K.recoff = b.recoff.as<int>();
     return K;
 }
 
@@ -277,6 +296,39 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
     const KPhys<T> P = make_phys<T>(m.phys);
     T* ufe = m.ufe.as<T>();
     T* dufe = m.dufe.as<T>();
+    const int sys = m.phys.system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER;
+    if (m.fast) {
+        // Register-blocked record path: interpolation of every block, then fluxes + divergence.
+        T* rec = m.rec.as<T>();
+        T* drec = m.drec.as<T>();
+        T* fiur = m.fiur.as<T>();
+        T* dfiur = m.dfiur.as<T>();
+        for (auto& bp : m.blocks) {
+            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+            int s = prof_begin(ctx, KIND_INTERP);
+            int r = launch_interp_rec<T>(K, m.nvar, U, rec, fiur, ctx->flag.as<int>(), ctx->nsm, ctx->stream);
+            prof_end(ctx, s);
+            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "record path not instantiated");
+            ++ctx->launches;
+            if (dU) {
+                s = prof_begin(ctx, KIND_INTERP);
+                launch_interp_rec<T>(K, m.nvar, dU, drec, dfiur, ctx->flag.as<int>(), ctx->nsm, ctx->stream);
+                prof_end(ctx, s);
+                ++ctx->launches;
+            }
+        }
+        for (auto& bp : m.blocks) {
+            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+            const int s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
+            launch_flux_rec<T>(K, sys, rec, dU ? drec : nullptr, fiur, dU ? dfiur : nullptr, P, E, ctx->nsm,
+                               ctx->stream);
+            prof_end(ctx, s);
+            ++ctx->launches;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+        return SDRT_OK;
+    }
     for (auto& bp : m.blocks) {
         const EType& et = *ctx->etypes[bp->etype];
         KBlock<T> K = make_kblock<T>(et, *bp);
@@ -354,6 +406,12 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
     const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
     if (!m.ufe.p) SDRT_CUDA(m.ufe.alloc((size_t)m.nvar * m.Ftot * es));
     if (need_dual && !m.dufe.p) SDRT_CUDA(m.dufe.alloc((size_t)m.nvar * m.Ftot * es));
+    if (m.fast) {
+        if (!m.rec.p) SDRT_CUDA(m.rec.alloc((size_t)m.rec_total * es));
+        if (!m.fiur.p) SDRT_CUDA(m.fiur.alloc((size_t)m.fiur_total * es));
+        if (need_dual && !m.drec.p) SDRT_CUDA(m.drec.alloc((size_t)m.rec_total * es));
+        if (need_dual && !m.dfiur.p) SDRT_CUDA(m.dfiur.alloc((size_t)m.fiur_total * es));
+    }
     if (need_rk && !m.ustage.p) {
         SDRT_CUDA(m.ustage.alloc((size_t)m.state_len * es));
         SDRT_CUDA(m.uacc.alloc((size_t)m.state_len * es));
@@ -439,6 +497,14 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
         for (int k = 0; k < R.nfi; ++k) Ad[(size_t)(R.nfe + k) * et->Md_pad + r] = R.M13[(size_t)r * R.nfi + k];
     }
     std::vector<float> Aif(Ai.begin(), Ai.end()), Adf(Ad.begin(), Ad.end());
+    // Row-major interpolation operator for the register-blocked kernels.
+    et->Mir = round_up(et->Mi + 2, 4);   // zero rows past Mi: row pairs (j, j + 2) stay in bounds
+    std::vector<double> Air((size_t)et->Mir * et->Md_pad, 0.0);
+    for (int j = 0; j < et->Mi; ++j)
+        for (int r = 0; r < R.nsol; ++r)
+            Air[(size_t)j * et->Md_pad + r] =
+                j < R.nfe ? R.M0[(size_t)j * R.nsol + r] : R.M12[(size_t)(j - R.nfe) * R.nsol + r];
+    std::vector<float> Airf(Air.begin(), Air.end());
     std::vector<int> tab((size_t)R.nfiu * 4, 0);
     for (int nu = 0; nu < R.nfi; ++nu) {
         int k = R.fi_point[nu];
@@ -454,6 +520,8 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
         SDRT_CUDA(upload(et->Ad[1], Adf));
         SDRT_CUDA(upload(et->fe_face, R.fe_face));
         SDRT_CUDA(upload(et->fi_tab, tab));
+        SDRT_CUDA(upload(et->Air[0], Air));
+        SDRT_CUDA(upload(et->Air[1], Airf));
     }
     ctx->etypes.push_back(std::move(et));
     *etype_id = (int)ctx->etypes.size() - 1;
@@ -508,6 +576,7 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
 
     // Layout.
     int64_t canon = 0;
+    m->fast = true;
     for (int b = 0; b < nblocks; ++b) {
         const sdrt_block& B = blocks[b];
         if (B.etype < 0 || B.etype >= (int)ctx->etypes.size()) return fail(ctx, SDRT_ERR_ARG, "bad etype id");
@@ -525,9 +594,35 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
         m->Ftot += (int64_t)R.nfe * mb->ld;
         m->ndof += (int64_t)R.nsol * m->nvar * B.nelem;
         canon += (int64_t)R.nfe * B.nelem;
+        if (!fast_path_available(R.shape, R.nsol, nd,
+                                 phys->system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER, phys->riemann))
+            m->fast = false;
         m->blocks.push_back(std::move(mb));
     }
     m->nfe_total = canon;
+    if (m->fast) {
+        // Record strides: multiples of 4 values (16-byte bulk copies), odd multiples
+        // of 4 for conflict-free shared-memory rows.
+        auto odd4 = [](int x) {
+            x = round_up(x, 4);
+            return ((x / 4) % 2 == 1) ? x : x + 4;
+        };
+        for (int b = 0; b < nblocks; ++b) {
+            MBlock& mb = *m->blocks[b];
+            const RefElement& R = ctx->etypes[mb.etype]->R;
+            const int npf = R.nfe / R.nfaces;
+            mb.frec = round_up(npf * m->nvar, 4);
+            mb.ers = odd4(R.nfaces * mb.frec);
+            mb.frs = odd4(R.nfiu * m->nvar);
+            mb.nmp = odd4(1 + nd * nd + R.nfaces * (nd + 1));
+            mb.pstride = round_up(R.nfe, 16);
+            if ((mb.pstride / 16) % 2 == 0) mb.pstride += 16;
+            mb.rec_base = m->rec_total;
+            mb.fiur_base = m->fiur_total;
+            m->rec_total += (int64_t)mb.nelem * mb.ers;
+            m->fiur_total += (int64_t)mb.nelem * mb.frs;
+        }
+    }
     if (canon >= INT32_MAX || m->Ftot >= INT32_MAX) return fail(ctx, SDRT_ERR_UNSUPPORTED, "mesh too large for int32 maps");
 
     // Metrics, physical points.
@@ -682,6 +777,49 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
                 SDRT_CUDA(upload(mb.metric, mf));
             } else {
                 SDRT_CUDA(upload(mb.metric, hb[b].metric));
+            }
+        }
+        if (m->fast) {
+            // Record-path tables: metric rows per element, partner face-record
+            // offsets, partner permutations, point offsets inside a record.
+            const int NM = 1 + nd * nd + R.nfaces * (nd + 1);
+            std::vector<double> maos((size_t)mb.nelem * mb.nmp, 0.0);
+            for (int e = 0; e < mb.nelem; ++e)
+                for (int k = 0; k < NM; ++k) maos[(size_t)e * mb.nmp + k] = hb[b].metric[(size_t)k * mb.ld + e];
+            std::vector<int> first(R.nfaces, -1);
+            for (int s = 0; s < R.nfe; ++s)
+                if (first[R.fe_face[s]] < 0) first[R.fe_face[s]] = s;
+            std::vector<int> recoff(R.nfe);
+            for (int s = 0; s < R.nfe; ++s)
+                recoff[s] = R.fe_face[s] * mb.frec + (s - first[R.fe_face[s]]) * m->nvar;
+            std::vector<int> pfr((size_t)mb.nelem * R.nfaces, 0);
+            std::vector<uint8_t> perm((size_t)mb.nelem * mb.pstride, 0);
+            for (int e = 0; e < mb.nelem; ++e)
+                for (int s = 0; s < R.nfe; ++s) {
+                    int64_t g = m->partner[mb.canon_base + (int64_t)e * R.nfe + s];
+                    int pb = nblocks - 1;
+                    while (m->blocks[pb]->canon_base > g) --pb;
+                    const MBlock& q = *m->blocks[pb];
+                    const RefElement& RQ = ctx->etypes[q.etype]->R;
+                    const int64_t rel = g - q.canon_base;
+                    const int pe = (int)(rel / RQ.nfe), ps = (int)(rel % RQ.nfe);
+                    const int pf = RQ.fe_face[ps];
+                    int pfirst = 0;
+                    while (RQ.fe_face[pfirst] != pf) ++pfirst;
+                    pfr[(size_t)e * R.nfaces + R.fe_face[s]] = (int)(q.rec_base + (int64_t)pe * q.ers + pf * q.frec);
+                    perm[(size_t)e * mb.pstride + s] = (uint8_t)(ps - pfirst);
+                }
+            if (m->rec_total >= INT32_MAX) return fail(ctx, SDRT_ERR_UNSUPPORTED, "mesh too large for int32 record offsets");
+            if (!ctx->host_only) {
+                if (f32) {
+                    std::vector<float> mf(maos.begin(), maos.end());
+                    SDRT_CUDA(upload(mb.maos, mf));
+                } else {
+                    SDRT_CUDA(upload(mb.maos, maos));
+                }
+                SDRT_CUDA(upload(mb.pfr, pfr));
+                SDRT_CUDA(upload(mb.perm, perm));
+                SDRT_CUDA(upload(mb.recoff, recoff));
             }
         }
         // Tile widths: keep the residual kernel's shared memory within ~100 KB

@@ -35,6 +35,25 @@ struct KBlock {
     const int* fi_tab;   // [nfiu][4]: count, then (nu | axis << 16) per internal DOF of the point
     const T* metric;     // [NM][ld]
     const int* map;      // [nfe][ld] UFE index (without the v * F_tot term) of the paired point
+    const T* Air;        // interpolation operator row-major: [Mir][Md_pad], rows [M0; M12], Mir = Mi rounded to 4
+    int Mir;
+    // Record layout of the register-blocked path (kernels_fast.cu): every
+    // element owns one contiguous record of its external-point states, face by
+    // face (face f at frecoff[f], point l of the face at + l * V, variable v at
+    // + v), and one record of its internal-point states (point k at k * V + v).
+    // Strides are multiples of 4 values (16-byte aligned bulk copies) and odd
+    // multiples of 4 where possible (conflict-free shared-memory rows).
+    int ers;             // element record stride in REC (values)
+    int frs;             // internal-point record stride in FIUR (values)
+    int frec;            // face record size (values): points per face * V rounded up to 4
+    int nmp;             // metric record stride in MAOS (values)
+    int pstride;         // permutation row stride (bytes)
+    int64_t rec_base;    // offset of element 0's record in REC
+    int64_t fiur_base;   // offset of element 0's record in FIUR
+    const T* maos;       // [nelem][nmp] metric rows (same content as `metric`)
+    const int* pfr;      // [nelem][nfaces] REC offset of the partner's face record
+    const unsigned char* perm;  // [nelem][pstride] local index, in the partner's face record, of each external point
+    const int* recoff;   // [nfe] offset of external point j in the element record
 };
 
 template <typename T>

@@ -1,0 +1,684 @@
+// Register-blocked SDRT residual kernels for tetrahedra of degree 3 and 4
+// (sm_103a), exchanging face states through per-element records staged with
+// bulk asynchronous copies.
+//
+// One residual evaluation (paper Sec. 2.1, App. B) is two launches per block:
+//   k_interp_rec : [u_fe; u_fiu] = [M0; M12] U (Eqs. "interpolation_procedure"),
+//                  two threads per element, operator in shared memory; the
+//                  tile's records are assembled in shared memory and written
+//                  with one cp.async.bulk store each (REC: external points,
+//                  FIUR: internal points).
+//   k_flux_rec   : per tile, cp.async.bulk loads (completing on an mbarrier)
+//                  bring the tile's own records, the four partner face records
+//                  of every element, the metric rows and the partner
+//                  permutations into shared memory; G threads per element
+//                  compute the common fluxes (Sec. 2.1) and the normal
+//                  transformed internal fluxes (Eq. "normal_transformed_flux")
+//                  of their share of the points, exchange them with warp
+//                  shuffles and accumulate their share of the rows of
+//                  R~ = [M14 | M13] [F~_fe; F~_fi] (Eq. "residual_sdrt_matrices")
+//                  in registers; dU/dt = -R~ / det J goes through the fused RK4
+//                  stage epilogue.
+//   k_flux_rec_dual : the JVP (dual numbers), reading the records directly.
+#include <cstdint>
+
+#include "device_math.cuh"
+#include "kargs.hpp"
+#include "launch.hpp"
+
+namespace sdrt {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr long long kWaitLimit = 1ll << 26;   // try_wait polls before giving up (seconds of waiting)
+
+// ---- PTX helpers: mbarrier and bulk copies -------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Global -> shared bulk copy completing on bar (16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Shared -> global bulk copy (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// ---- fluxes ----------------------------------------------------------------
+template <int SYS, int RIE, int ND, typename S, typename T>
+__device__ __forceinline__ void common_flux_f(const S* uL, const S* uR, const T* n, const KPhys<T>& P, S* F) {
+    if constexpr (SYS == SYS_EULER) {
+        if constexpr (RIE == RIE_ROE) roe<S, T, ND>(uL, uR, n, P.gamma, F);
+        else rusanov<S, T, ND>(uL, uR, n, P.gamma, F);
+    } else {
+        T an = P.a[0] * n[0];
+        #pragma unroll
+        for (int d = 1; d < ND; ++d) an = fma(P.a[d], n[d], an);
+        const T aa = an >= T(0) ? an : -an;
+        F[0] = T(0.5) * an * (uL[0] + uR[0]) + T(0.5) * aa * (uL[0] - uR[0]);
+    }
+}
+
+template <int SYS, int ND, typename S, typename T>
+__device__ __forceinline__ void internal_flux_f(const S* u, const T* Srow, const KPhys<T>& P, S* Ft) {
+    if constexpr (SYS == SYS_EULER) {
+        S v[ND], p;
+        euler_prim<S, T, ND>(u, v, p, P.gamma);
+        euler_nflux<S, T, ND>(u, v, p, Srow, Ft);
+    } else {
+        T an = P.a[0] * Srow[0];
+        #pragma unroll
+        for (int d = 1; d < ND; ++d) an = fma(P.a[d], Srow[d], an);
+        Ft[0] = an * u[0];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void epi_store(const KEpi<T>& E, size_t idx, T r) {
+    if (!isfinite(r)) *E.flag = 1;
+    switch (E.mode) {
+        case EPI_STORE: E.out[idx] = r; break;
+        case EPI_RK_FIRST: {
+            const T u0 = E.u0[idx];
+            E.uacc[idx] = fma(E.cacc, r, u0);
+            E.unext[idx] = fma(E.cnext, r, u0);
+            break;
+        }
+        case EPI_RK_MID:
+            E.uacc[idx] = fma(E.cacc, r, E.uacc[idx]);
+            E.unext[idx] = fma(E.cnext, r, E.u0[idx]);
+            break;
+        default: E.out[idx] = fma(E.cacc, r, E.uacc[idx]); break;
+    }
+}
+
+// Stage update of the RS x V values R = inv * acc[i][v] owned by one thread
+// (rows r0 + i < nrows, variables v at base + (r * V + v) * ld).  All loads are
+// issued before any store: the state arrays are distinct, but the compiler
+// cannot prove it, and interleaved load/store pairs would serialise.
+template <int RS, int V, typename T>
+__device__ __forceinline__ void epi_block(const KEpi<T>& E, const T (&acc)[RS][V], T inv, size_t base, int ld,
+                                          int r0, int nrows) {
+    T a[RS][V], b[RS][V];
+    const bool need_u0 = E.mode == EPI_RK_FIRST || E.mode == EPI_RK_MID;
+    const bool need_acc = E.mode == EPI_RK_MID || E.mode == EPI_RK_LAST;
+    #pragma unroll
+    for (int i = 0; i < RS; ++i)
+        #pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const size_t idx = base + (size_t)((r0 + i) * V + v) * ld;
+            const bool ok = r0 + i < nrows;
+            a[i][v] = (ok && need_u0) ? __ldg(E.u0 + idx) : T(0);
+            b[i][v] = (ok && need_acc) ? E.uacc[idx] : T(0);
+        }
+    bool bad = false;
+    #pragma unroll
+    for (int i = 0; i < RS; ++i) {
+        if (r0 + i >= nrows) continue;
+        #pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const size_t idx = base + (size_t)((r0 + i) * V + v) * ld;
+            const T r = acc[i][v] * inv;
+            bad |= !isfinite(r);
+            switch (E.mode) {
+                case EPI_STORE: E.out[idx] = r; break;
+                case EPI_RK_FIRST:
+                    E.uacc[idx] = fma(E.cacc, r, a[i][v]);
+                    E.unext[idx] = fma(E.cnext, r, a[i][v]);
+                    break;
+                case EPI_RK_MID:
+                    E.uacc[idx] = fma(E.cacc, r, b[i][v]);
+                    E.unext[idx] = fma(E.cnext, r, a[i][v]);
+                    break;
+                default: E.out[idx] = fma(E.cacc, r, b[i][v]); break;
+            }
+        }
+    }
+    if (bad) *E.flag = 1;
+}
+
+// 16-byte shared-memory vector of T.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+    __device__ static void get(const type& x, float* o) { o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = x.w; }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+    __device__ static void get(const type& x, double* o) { o[0] = x.x; o[1] = x.y; }
+};
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Interpolation to the external and internal flux points, written as records.
+// 2 * TE threads, TE elements per tile, thread pair (h = 0, 1) per element.
+template <typename T, int NS, int V, int NFE, int NFIU, int TE>
+__global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __restrict__ U, T* __restrict__ REC,
+                                                    T* __restrict__ FIUR, int* __restrict__ err) {
+    constexpr int NSP = (NS + 7) / 8 * 8;                 // equals B.Md_pad
+    constexpr int MI = NFE + NFIU;
+    constexpr int VB = 400 / (NS * (int)sizeof(T));
+    constexpr int VG = (V <= VB) ? V : (VB > 0 ? VB : 1);
+    using VT = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* As = reinterpret_cast<T*>(smem_raw);                                   // [Mir][NSP]
+    T* Rs = reinterpret_cast<T*>(smem_raw + align16((size_t)B.Mir * NSP * sizeof(T)));   // [TE][ers]
+    T* Fs = Rs + (size_t)TE * B.ers;                                          // [TE][frs]
+    int* roff = reinterpret_cast<int*>(Fs + (size_t)TE * B.frs);             // [NFE]
+    for (int i = threadIdx.x; i < B.Mir * NSP; i += blockDim.x) As[i] = B.Air[i];
+    for (int i = threadIdx.x; i < NFE; i += blockDim.x) roff[i] = B.recoff[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int el = (threadIdx.x >> 5) * 16 + (lane & 15);
+    const int h = lane >> 4;
+    const int ntiles = (B.nelem + TE - 1) / TE;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int e0 = tile * TE;
+        const int n = min(TE, B.nelem - e0);
+        if (el < n) {
+            const T* Ue = U + B.u_off + e0 + el;
+            #pragma unroll 1
+            for (int v0 = 0; v0 < V; v0 += VG) {
+                T u[VG][NS];
+                #pragma unroll
+                for (int w = 0; w < VG; ++w) {
+                    const int v = (v0 + w < V) ? v0 + w : V - 1;
+                    #pragma unroll
+                    for (int r = 0; r < NS; ++r) u[w][r] = __ldg(Ue + (size_t)(r * V + v) * B.ld);
+                }
+                // rows j = h, h + 2, ... in pairs (j, j + 2)
+                #pragma unroll 1
+                for (int jb = h; jb < MI; jb += 4) {
+                    T acc[2][VG];
+                    #pragma unroll
+                    for (int i = 0; i < 2; ++i)
+                        #pragma unroll
+                        for (int w = 0; w < VG; ++w) acc[i][w] = T(0);
+                    const VT* a0 = reinterpret_cast<const VT*>(As + jb * NSP);
+                    const VT* a1 = reinterpret_cast<const VT*>(As + (jb + 2) * NSP);
+                    #pragma unroll
+                    for (int r = 0; r < NSP; r += VN) {
+                        T x0[VN], x1[VN];
+                        Vec16<T>::get(a0[r / VN], x0);
+                        Vec16<T>::get(a1[r / VN], x1);
+                        #pragma unroll
+                        for (int q = 0; q < VN; ++q)
+                            if (r + q < NS) {
+                                #pragma unroll
+                                for (int w = 0; w < VG; ++w) {
+                                    acc[0][w] = fma(x0[q], u[w][r + q], acc[0][w]);
+                                    acc[1][w] = fma(x1[q], u[w][r + q], acc[1][w]);
+                                }
+                            }
+                    }
+                    #pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int j = jb + 2 * i;
+                        #pragma unroll
+                        for (int w = 0; w < VG; ++w) {
+                            const int v = v0 + w;
+                            if (v < V) {
+                                if (j < NFE) Rs[(size_t)el * B.ers + roff[j] + v] = acc[i][w];
+                                else if (j < MI) Fs[(size_t)el * B.frs + (j - NFE) * V + v] = acc[i][w];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            bulk_s2g(REC + B.rec_base + (size_t)e0 * B.ers, Rs, (uint32_t)(n * B.ers * sizeof(T)));
+            bulk_s2g(FIUR + B.fiur_base + (size_t)e0 * B.frs, Fs, (uint32_t)(n * B.frs * sizeof(T)));
+            bulk_commit();
+            bulk_wait_read0();     // the tile buffers may be reused once the copies have read them
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bulk_wait0();   // writes visible before the kernel completes
+    (void)err;
+}
+
+// ---------------------------------------------------------------------------
+// Flux and divergence of one tile staged in shared memory (value path).
+template <typename T, int V, int ND, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW>
+__global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __restrict__ REC,
+                                                      const T* __restrict__ FIUR, KPhys<T> P, KEpi<T> E) {
+    static_assert(NFE % G == 0, "external points must split evenly across the G threads");
+    constexpr int EPW = 32 / G;
+    constexpr int TE = NW * EPW;
+    constexpr int RS = (NS + G - 1) / G;
+    constexpr int RSP = (RS + 3) / 4 * 4;
+    constexpr int NDOF = ND;                  // DOFs per internal point (tetrahedra)
+    constexpr int K2 = NFE + NDOF * NFIU;
+    constexpr int NFACE = ND + 1;
+    constexpr int ND2 = ND * ND;
+    using VT = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    size_t off = 16;
+    T* As = reinterpret_cast<T*>(smem_raw + off);                 // [K2][G][RSP]
+    off = align16(off + (size_t)K2 * G * RSP * sizeof(T));
+    T* own = reinterpret_cast<T*>(smem_raw + off);                // [TE][ers]
+    off = align16(off + (size_t)TE * B.ers * sizeof(T));
+    T* part = reinterpret_cast<T*>(smem_raw + off);               // [TE][ers]: partner face records
+    off = align16(off + (size_t)TE * B.ers * sizeof(T));
+    T* fiu = reinterpret_cast<T*>(smem_raw + off);                // [TE][frs]
+    off = align16(off + (size_t)TE * B.frs * sizeof(T));
+    T* met = reinterpret_cast<T*>(smem_raw + off);                // [TE][nmp]
+    off = align16(off + (size_t)TE * B.nmp * sizeof(T));
+    unsigned char* prm = smem_raw + off;                          // [TE][pstride]
+    off = align16(off + (size_t)TE * B.pstride);
+    int* roff = reinterpret_cast<int*>(smem_raw + off);           // [NFE]
+    int* fface = roff + NFE;                                      // [NFE]
+
+    for (int i = threadIdx.x; i < K2 * G * RSP; i += blockDim.x) {
+        const int j = i / (G * RSP);
+        const int hh = (i / RSP) % G;
+        const int r = hh * RS + i % RSP;
+        As[i] = (i % RSP < RS && r < NS) ? B.Ad[(size_t)j * B.Md_pad + r] : T(0);
+    }
+    for (int i = threadIdx.x; i < NFE; i += blockDim.x) {
+        roff[i] = B.recoff[i];
+        fface[i] = B.fe_face[i];
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int h = lane / EPW;
+    const int el = warp * EPW + lane % EPW;
+    const int ntiles = (B.nelem + TE - 1) / TE;
+    uint32_t parity = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, parity ^= 1u) {
+        const int e0 = tile * TE;
+        const int n = min(TE, B.nelem - e0);
+        // Stage the tile.
+        if (threadIdx.x == 0) {
+            // own records + partner face records + internal records + metric rows + permutations
+            const uint32_t bytes =
+                (uint32_t)((size_t)n * (B.ers + NFACE * B.frec + B.frs + B.nmp) * sizeof(T) + (size_t)n * B.pstride);
+            mbar_arrive_expect_tx(bar, bytes);
+            fence_proxy_async();
+            bulk_g2s(own, REC + B.rec_base + (size_t)e0 * B.ers, (uint32_t)(n * B.ers * sizeof(T)), bar);
+            bulk_g2s(fiu, FIUR + B.fiur_base + (size_t)e0 * B.frs, (uint32_t)(n * B.frs * sizeof(T)), bar);
+            bulk_g2s(met, B.maos + (size_t)e0 * B.nmp, (uint32_t)(n * B.nmp * sizeof(T)), bar);
+            bulk_g2s(prm, B.perm + (size_t)e0 * B.pstride, (uint32_t)(n * B.pstride), bar);
+        }
+        for (int t = threadIdx.x; t < n * NFACE; t += blockDim.x) {
+            const int le = t / NFACE, f = t % NFACE;
+            const int src = __ldg(B.pfr + (size_t)(e0 + le) * NFACE + f);
+            fence_proxy_async();
+            bulk_g2s(part + (size_t)le * B.ers + f * B.frec, REC + src, (uint32_t)(B.frec * sizeof(T)), bar);
+        }
+        if (!mbar_wait(bar, parity)) {
+            *E.flag = 2;
+            mbar_wait(bar, parity);
+        }
+
+        const bool valid = el < n;
+        const int le = valid ? el : 0;
+        const T* own_e = own + (size_t)le * B.ers;
+        const T* part_e = part + (size_t)le * B.ers;
+        const T* met_e = met + (size_t)le * B.nmp;
+        const unsigned char* prm_e = prm + (size_t)le * B.pstride;
+        T acc[RS][V];
+        #pragma unroll
+        for (int i = 0; i < RS; ++i)
+            #pragma unroll
+            for (int v = 0; v < V; ++v) acc[i][v] = T(0);
+        auto accumulate = [&](int j, const T* F) {
+            const VT* a = reinterpret_cast<const VT*>(As + ((size_t)j * G + h) * RSP);
+            #pragma unroll
+            for (int r = 0; r < RSP; r += VN) {
+                T x[VN];
+                Vec16<T>::get(a[r / VN], x);
+                #pragma unroll
+                for (int q = 0; q < VN; ++q)
+                    if (r + q < RS) {
+                        #pragma unroll
+                        for (int v = 0; v < V; ++v) acc[r + q][v] = fma(x[q], F[v], acc[r + q][v]);
+                    }
+            }
+        };
+        // Accumulate the G fluxes of one round: thread h holds the flux of point
+        // base + h; the value of thread h ^ m arrives with one xor-shuffle and
+        // belongs to point base + (h ^ m).
+        auto accumulate_round = [&](int base, const T* F) {
+            accumulate(base + h, F);
+            #pragma unroll
+            for (int m = 1; m < G; ++m) {
+                T Fm[V];
+                #pragma unroll
+                for (int v = 0; v < V; ++v) Fm[v] = __shfl_xor_sync(FULL, F[v], m * EPW);
+                accumulate(base + (h ^ m), Fm);
+            }
+        };
+        // External points j = q * G + h.
+        #pragma unroll 1
+        for (int q = 0; q < NFE / G; ++q) {
+            const int j = q * G + h;
+            const int f = fface[j];
+            const int mrow = 1 + ND2 + f * (ND + 1);
+            T nrm[ND];
+            #pragma unroll
+            for (int c = 0; c < ND; ++c) nrm[c] = met_e[mrow + c];
+            const T s = met_e[mrow + ND];
+            const T* uo_p = own_e + roff[j];
+            const T* un_p = part_e + f * B.frec + (int)prm_e[j] * V;
+            T uo[V], un[V], F[V];
+            #pragma unroll
+            for (int v = 0; v < V; ++v) {
+                uo[v] = uo_p[v];
+                un[v] = un_p[v];
+            }
+            if (s > T(0)) common_flux_f<SYS, RIE, ND>(uo, un, nrm, P, F);
+            else common_flux_f<SYS, RIE, ND>(un, uo, nrm, P, F);
+            #pragma unroll
+            for (int v = 0; v < V; ++v) F[v] *= s;
+            accumulate_round(q * G, F);
+        }
+        // Internal points: every axis is a DOF (nu = axis * NFIU + k).
+        T Srow[NDOF][ND];
+        #pragma unroll
+        for (int d = 0; d < NDOF; ++d)
+            #pragma unroll
+            for (int i = 0; i < ND; ++i) Srow[d][i] = met_e[1 + d * ND + i];
+        #pragma unroll 1
+        for (int q = 0; q < (NFIU + G - 1) / G; ++q) {
+            const int k = q * G + h;
+            const int kc = k < NFIU ? k : NFIU - 1;   // past the last point: computed, never accumulated
+            T u[V];
+            #pragma unroll
+            for (int v = 0; v < V; ++v) u[v] = fiu[(size_t)le * B.frs + kc * V + v];
+            #pragma unroll
+            for (int d = 0; d < NDOF; ++d) {
+                T Ft[V];
+                internal_flux_f<SYS, ND>(u, Srow[d], P, Ft);
+                if (k >= NFIU) {
+                    #pragma unroll
+                    for (int v = 0; v < V; ++v) Ft[v] = T(0);   // past the last point: contributes nothing
+                }
+                // Points past the last one hold zero fluxes; their operator
+                // column index is clamped to a real column.
+                const int base = NFE + d * NFIU + q * G;
+                accumulate(min(base + h, NFE + d * NFIU + NFIU - 1), Ft);
+                #pragma unroll
+                for (int m = 1; m < G; ++m) {
+                    T Fm[V];
+                    #pragma unroll
+                    for (int v = 0; v < V; ++v) Fm[v] = __shfl_xor_sync(FULL, Ft[v], m * EPW);
+                    accumulate(min(base + (h ^ m), NFE + d * NFIU + NFIU - 1), Fm);
+                }
+            }
+        }
+        if (valid) {
+            const int e = e0 + el;
+            const T inv = -met_e[0];
+            epi_block<RS, V>(E, acc, inv, (size_t)B.u_off + e, B.ld, h * RS, NS);
+        }
+        __syncthreads();      // the tile buffers are free for the next tile's copies
+    }
+}
+
+// ---------------------------------------------------------------------------
+// JVP: the residual with dual numbers, records read directly from global memory.
+template <typename T, int V, int ND, int SYS, int RIE, int NS>
+__global__ void __launch_bounds__(32 * V, 4) k_flux_rec_dual(KBlock<T> B, const T* __restrict__ REC,
+                                                             const T* __restrict__ dREC, const T* __restrict__ FIUR,
+                                                             const T* __restrict__ dFIUR, KPhys<T> P, KEpi<T> E) {
+    using S = Dual<T>;
+    constexpr int TE = 32;
+    constexpr int NCOL = V * TE;
+    constexpr int ND2 = ND * ND;
+    constexpr int NFACE = ND + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NSP = B.Md_pad;
+    const int K2 = B.nfe + B.nfi;
+    T* As = reinterpret_cast<T*>(smem_raw);                                   // [K2][NSP]
+    S* Fs = reinterpret_cast<S*>(smem_raw + (size_t)K2 * NSP * sizeof(T));    // [K2][V * TE]
+    for (int i = threadIdx.x; i < K2 * NSP; i += blockDim.x) As[i] = B.Ad[i];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int ntiles = (B.nelem + TE - 1) / TE;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int e = tile * TE + lane;
+        const bool valid = e < B.nelem;
+        const int ec = valid ? e : B.nelem - 1;
+        const size_t rec_e = (size_t)B.rec_base + (size_t)ec * B.ers;
+        __syncthreads();
+        for (int sg = warp; sg < B.nfe; sg += V) {
+            const int f = __ldg(B.fe_face + sg);
+            const int mrow = 1 + ND2 + f * (ND + 1);
+            T n[ND];
+            #pragma unroll
+            for (int c = 0; c < ND; ++c) n[c] = __ldg(B.metric + (size_t)(mrow + c) * B.ld + ec);
+            const T s = __ldg(B.metric + (size_t)(mrow + ND) * B.ld + ec);
+            const size_t po = (size_t)__ldg(B.pfr + (size_t)ec * NFACE + f) +
+                              (size_t)__ldg(B.perm + (size_t)ec * B.pstride + sg) * V;
+            const size_t oo = rec_e + __ldg(B.recoff + sg);
+            S uo[V], un[V], F[V];
+            #pragma unroll
+            for (int v = 0; v < V; ++v) {
+                uo[v] = {__ldg(REC + oo + v), __ldg(dREC + oo + v)};
+                un[v] = {__ldg(REC + po + v), __ldg(dREC + po + v)};
+            }
+            if (s > T(0)) common_flux_f<SYS, RIE, ND>(uo, un, n, P, F);
+            else common_flux_f<SYS, RIE, ND>(un, uo, n, P, F);
+            #pragma unroll
+            for (int v = 0; v < V; ++v) Fs[(size_t)sg * NCOL + v * TE + lane] = s * F[v];
+        }
+        for (int k = warp; k < B.nfiu; k += V) {
+            S u[V];
+            const size_t fo = (size_t)B.fiur_base + (size_t)ec * B.frs + (size_t)k * V;
+            #pragma unroll
+            for (int v = 0; v < V; ++v) u[v] = {__ldg(FIUR + fo + v), __ldg(dFIUR + fo + v)};
+            const int4 tab = __ldg(reinterpret_cast<const int4*>(B.fi_tab) + k);
+            const int dofs[3] = {tab.y, tab.z, tab.w};
+            for (int q = 0; q < tab.x; ++q) {
+                const int nu = dofs[q] & 0xffff;
+                const int ax = dofs[q] >> 16;
+                T Srow[ND];
+                #pragma unroll
+                for (int i = 0; i < ND; ++i) Srow[i] = __ldg(B.metric + (size_t)(1 + ax * ND + i) * B.ld + ec);
+                S Ft[V];
+                internal_flux_f<SYS, ND>(u, Srow, P, Ft);
+                #pragma unroll
+                for (int v = 0; v < V; ++v) Fs[(size_t)(B.nfe + nu) * NCOL + v * TE + lane] = Ft[v];
+            }
+        }
+        __syncthreads();
+        {
+            const int v = warp;
+            S acc[NS];
+            #pragma unroll
+            for (int r = 0; r < NS; ++r) acc[r] = szero<S>();
+            const S* fcol = Fs + v * TE + lane;
+            #pragma unroll 2
+            for (int j = 0; j < K2; ++j) {
+                const S b = fcol[(size_t)j * NCOL];
+                const T* a = As + j * NSP;
+                #pragma unroll
+                for (int r = 0; r < NS; ++r) mac(acc[r], a[r], b);
+            }
+            if (valid) {
+                const T inv = -__ldg(B.metric + e);
+                #pragma unroll
+                for (int r = 0; r < NS; ++r) {
+                    const T d = acc[r].d * inv;
+                    if (!isfinite(d)) *E.flag = 1;
+                    E.out[(size_t)B.u_off + (size_t)(r * V + v) * B.ld + e] = d;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+
+namespace {
+
+template <typename K>
+int blocks_per_sm(K kernel, int threads, int smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+template <typename T, int NS, int V, int NFE, int NFIU, int TE>
+void interp_rec_tile(const KBlock<T>& B, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st,
+                     size_t smem) {
+    auto k = k_interp_rec<T, NS, V, NFE, NFIU, TE>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int per = blocks_per_sm(k, 2 * TE, (int)smem);
+    const int need = (B.nelem + TE - 1) / TE;
+    const int grid = need < nsm * per ? need : nsm * per;
+    k<<<grid, 2 * TE, smem, st>>>(B, U, REC, FIUR, err);
+}
+
+template <typename T, int NS, int V, int NFE, int NFIU>
+void interp_rec_impl(const KBlock<T>& B, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st) {
+    auto smem_of = [&](int TE) {
+        return ((size_t)B.Mir * B.Md_pad * sizeof(T) + 15) / 16 * 16 + (size_t)TE * (B.ers + B.frs) * sizeof(T) +
+               NFE * sizeof(int);
+    };
+    // 64-element tiles unless their records exceed ~150 KB of shared memory.
+    if (smem_of(64) <= 150 * 1024) interp_rec_tile<T, NS, V, NFE, NFIU, 64>(B, U, REC, FIUR, err, nsm, st, smem_of(64));
+    else interp_rec_tile<T, NS, V, NFE, NFIU, 32>(B, U, REC, FIUR, err, nsm, st, smem_of(32));
+}
+
+template <typename T, int V, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW>
+void flux_rec_impl(const KBlock<T>& B, const T* REC, const T* FIUR, const KPhys<T>& P, const KEpi<T>& E, int nsm,
+                   cudaStream_t st) {
+    auto k = k_flux_rec<T, V, 3, SYS, RIE, NS, G, NFE, NFIU, NW>;
+    constexpr int TE = NW * (32 / G);
+    constexpr int RSP = ((NS + G - 1) / G + 3) / 4 * 4;
+    auto a16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    size_t smem = 16;
+    smem = a16(smem + (size_t)(NFE + 3 * NFIU) * G * RSP * sizeof(T));
+    smem = a16(smem + (size_t)TE * B.ers * sizeof(T));
+    smem = a16(smem + (size_t)TE * B.ers * sizeof(T));
+    smem = a16(smem + (size_t)TE * B.frs * sizeof(T));
+    smem = a16(smem + (size_t)TE * B.nmp * sizeof(T));
+    smem = a16(smem + (size_t)TE * B.pstride);
+    smem += 2 * NFE * sizeof(int);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int per = blocks_per_sm(k, 32 * NW, (int)smem);
+    const int need = (B.nelem + TE - 1) / TE;
+    const int grid = need < nsm * per ? need : nsm * per;
+    k<<<grid, 32 * NW, smem, st>>>(B, REC, FIUR, P, E);
+}
+
+template <typename T, int V, int SYS, int RIE, int NS>
+void flux_rec_dual_impl(const KBlock<T>& B, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,
+                        const KPhys<T>& P, const KEpi<T>& E, int nsm, cudaStream_t st) {
+    auto k = k_flux_rec_dual<T, V, 3, SYS, RIE, NS>;
+    const int K2 = B.nfe + B.nfi;
+    const int smem = K2 * B.Md_pad * (int)sizeof(T) + K2 * V * 32 * (int)sizeof(Dual<T>);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int per = blocks_per_sm(k, 32 * V, smem);
+    const int need = (B.nelem + 31) / 32;
+    const int grid = need < nsm * per ? need : nsm * per;
+    k<<<grid, 32 * V, smem, st>>>(B, REC, dREC, FIUR, dFIUR, P, E);
+}
+
+}  // namespace
+
+bool fast_path_available(int shape, int nsol, int nd, int system, int riemann) {
+    if (nd != 3 || shape != 2 /* tetrahedron */) return false;
+    if (nsol != 20 && nsol != 35) return false;
+    if (system == SYS_ADVECTION) return true;
+    return system == SYS_EULER && riemann == RIE_RUSANOV;
+}
+
+template <typename T>
+int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st) {
+    if (V == 5 && B.nsol == 20) interp_rec_impl<T, 20, 5, 40, 10>(B, U, REC, FIUR, err, nsm, st);
+    else if (V == 5 && B.nsol == 35) interp_rec_impl<T, 35, 5, 60, 20>(B, U, REC, FIUR, err, nsm, st);
+    else if (V == 1 && B.nsol == 20) interp_rec_impl<T, 20, 1, 40, 10>(B, U, REC, FIUR, err, nsm, st);
+    else if (V == 1 && B.nsol == 35) interp_rec_impl<T, 35, 1, 60, 20>(B, U, REC, FIUR, err, nsm, st);
+    else return -1;
+    return 0;
+}
+
+template <typename T>
+int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,
+                    const KPhys<T>& P, const KEpi<T>& E, int nsm, cudaStream_t st) {
+    const bool dual = dREC != nullptr;
+    if (system == SYS_EULER) {
+        if (B.nsol == 20) {
+            if (dual) flux_rec_dual_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20>(B, REC, dREC, FIUR, dFIUR, P, E, nsm, st);
+            else flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20, 4, 40, 10, 4>(B, REC, FIUR, P, E, nsm, st);
+        } else {
+            if (dual) flux_rec_dual_impl<T, 5, SYS_EULER, RIE_RUSANOV, 35>(B, REC, dREC, FIUR, dFIUR, P, E, nsm, st);
+            else flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 35, 4, 60, 20, 2>(B, REC, FIUR, P, E, nsm, st);
+        }
+    } else {
+        if (B.nsol == 20) {
+            if (dual) flux_rec_dual_impl<T, 1, SYS_ADVECTION, RIE_UPWIND, 20>(B, REC, dREC, FIUR, dFIUR, P, E, nsm, st);
+            else flux_rec_impl<T, 1, SYS_ADVECTION, RIE_UPWIND, 20, 2, 40, 10, 4>(B, REC, FIUR, P, E, nsm, st);
+        } else {
+            if (dual) flux_rec_dual_impl<T, 1, SYS_ADVECTION, RIE_UPWIND, 35>(B, REC, dREC, FIUR, dFIUR, P, E, nsm, st);
+            else flux_rec_impl<T, 1, SYS_ADVECTION, RIE_UPWIND, 35, 4, 60, 20, 4>(B, REC, FIUR, P, E, nsm, st);
+        }
+    }
+    return 0;
+}
+
+template int launch_interp_rec<float>(const KBlock<float>&, int, const float*, float*, float*, int*, int,
+                                      cudaStream_t);
+template int launch_interp_rec<double>(const KBlock<double>&, int, const double*, double*, double*, int*, int,
+                                       cudaStream_t);
+template int launch_flux_rec<float>(const KBlock<float>&, int, const float*, const float*, const float*,
+                                    const float*, const KPhys<float>&, const KEpi<float>&, int, cudaStream_t);
+template int launch_flux_rec<double>(const KBlock<double>&, int, const double*, const double*, const double*,
+                                     const double*, const KPhys<double>&, const KEpi<double>&, int, cudaStream_t);
+
+}  // namespace sdrt

@@ -26,4 +26,18 @@ int launch_residual(const KBlock<T>& B, int system, int riemann, int nd, const T
 template <typename T>
 int residual_smem(const KBlock<T>& B, int V, int TE, bool dual, int* rowsA);
 
+// Register-blocked record path (kernels_fast.cu) for the element types
+// instantiated there (tetrahedra of degree 3 and 4).
+bool fast_path_available(int shape, int nsol, int nd, int system, int riemann);
+
+// [u_fe; u_fiu] = [M0; M12] U written as element records (REC, FIUR).
+// Returns -1 if not instantiated.
+template <typename T>
+int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st);
+
+// Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
+template <typename T>
+int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,
+                    const KPhys<T>& P, const KEpi<T>& E, int nsm, cudaStream_t st);
+
 }  // namespace sdrt
