@@ -228,6 +228,15 @@ int sdrt_sync(sdrt_ctx* ctx);
  * accounting). */
 int64_t sdrt_launch_count(const sdrt_ctx* ctx);
 
+/* Options of a context.
+ *   SDRT_OPT_TENSOR_CORES (default 0): 1 = run the interpolation of FP32
+ *     tetrahedra of degree 3 on the tensor cores (tcgen05, products split
+ *     into three TF32 products, FP32 accumulation); 0 = CUDA-core FMA kernels
+ *     only (currently the faster of the two for that kernel).  Results agree
+ *     to FP32 rounding. */
+#define SDRT_OPT_TENSOR_CORES 0
+int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
+
 /* Per-launch device timing with CUDA events recorded on the context's stream
  * around every kernel the context launches, including inside the captured
  * RK4 graphs (enabling or disabling drops captured graphs, which are then

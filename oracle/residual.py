@@ -86,8 +86,14 @@ def _gradients(geom, phys, U, ufe, ufiu, fr=False):
     return qfe, qfiu
 
 
-def residual(geom, phys, U, fr=False):
-    """dU/dt for every block.  U: list of (N_s, V, E) arrays (real or complex)."""
+def residual(geom, phys, U, fr=False, terms=False):
+    """dU/dt for every block.  U: list of (N_s, V, E) arrays (real or complex).
+
+    terms=True also returns, per block, the magnitude of the divergence's terms
+    S = (|M14| |F~_fe| + |M13| |F~_fi|) / det J (same shape as dU/dt): the scale
+    of the rounding errors of a finite-precision evaluation (forward error
+    bound |dR| <= gamma S)."""
+    scales = []
     ufe = [np.einsum("sr,rve->sve", g.ops.M0, u) for g, u in zip(geom.blocks, U)]
     ufiu = [np.einsum("kr,rve->kve", g.ops.M12, u) for g, u in zip(geom.blocks, U)]
     if phys.viscous:
@@ -115,6 +121,9 @@ def residual(geom, phys, U, fr=False):
             ftp = ft[:, ops.fi_point]                          # (E, N_fi, ND, V)
             Ft_fi = np.einsum("nd,endv->nve", ops.fi_dir, ftp)  # (N_fi, V, E)
             div = np.einsum("sf,fve->sve", ops.M14, Ft_fe) + np.einsum("sn,nve->sve", ops.M13, Ft_fi)
+            if terms:
+                scales.append((np.einsum("sf,fve->sve", np.abs(ops.M14), np.abs(Ft_fe)) +
+                               np.einsum("sn,nve->sve", np.abs(ops.M13), np.abs(Ft_fi))) / g.detJ[None, None, :])
         else:
             u_s = np.moveaxis(U[b], -1, 0)                      # (E, N_s, V)
             if phys.viscous:
@@ -129,7 +138,7 @@ def residual(geom, phys, U, fr=False):
             jump = Ft_fe - np.moveaxis(np.einsum("efdv,fd->efv", ft_fe, ops.nrm_fe), 0, -1)
             div = div + np.einsum("sf,fve->sve", ops.M14, jump)
         out.append(-div / g.detJ[None, None, :])
-    return out
+    return (out, scales) if terms else out
 
 
 def _fr_sol_grad(g, phys, U, ufe, uL, uR):

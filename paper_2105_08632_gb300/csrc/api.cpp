@@ -102,6 +102,7 @@ struct sdrt_ctx {
     cudaStream_t stream = nullptr;
     int nsm = 1;
     bool host_only = false;       // device == -1: host-side setup only, no compute
+    bool use_tc = false;          // tensor-core kernels where instantiated (SDRT_OPT_TENSOR_CORES)
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
     std::vector<std::unique_ptr<Mesh>> meshes;
@@ -304,15 +305,29 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
         T* fiur = m.fiur.as<T>();
         T* dfiur = m.dfiur.as<T>();
         for (auto& bp : m.blocks) {
-            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+            const EType& et = *ctx->etypes[bp->etype];
+            KBlock<T> K = make_kblock<T>(et, *bp);
+            // Interpolation: tensor cores (tcgen05, 3xTF32) where instantiated, else CUDA cores.
+            auto interp = [&](const T* X, T* rec_out, T* fiur_out) {
+                int r = -1;
+                if constexpr (std::is_same<T, float>::value) {
+                    if (ctx->use_tc && tc_interp_available(et.R.shape, et.R.nsol, m.nvar))
+                        r = launch_interp_tc(K, m.nvar, X, rec_out, fiur_out, ctx->flag.as<int>(), ctx->nsm,
+                                             ctx->stream);
+                }
+                if (r != 0)
+                    r = launch_interp_rec<T>(K, m.nvar, X, rec_out, fiur_out, ctx->flag.as<int>(), ctx->nsm,
+                                             ctx->stream);
+                return r;
+            };
             int s = prof_begin(ctx, KIND_INTERP);
-            int r = launch_interp_rec<T>(K, m.nvar, U, rec, fiur, ctx->flag.as<int>(), ctx->nsm, ctx->stream);
+            int r = interp(U, rec, fiur);
             prof_end(ctx, s);
             if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "record path not instantiated");
             ++ctx->launches;
             if (dU) {
                 s = prof_begin(ctx, KIND_INTERP);
-                launch_interp_rec<T>(K, m.nvar, dU, drec, dfiur, ctx->flag.as<int>(), ctx->nsm, ctx->stream);
+                interp(dU, drec, dfiur);
                 prof_end(ctx, s);
                 ++ctx->launches;
             }
@@ -963,6 +978,18 @@ int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
     }
     // Events inside the graph hold the timings of its last replay.
     if (ctx->prof) ctx->pending.insert(ctx->pending.end(), m.graph_slots.begin(), m.graph_slots.end());
+    return SDRT_OK;
+}
+
+int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
+    if (!ctx) return SDRT_ERR_ARG;
+    if (option != SDRT_OPT_TENSOR_CORES) return fail(ctx, SDRT_ERR_ARG, "unknown option");
+    ctx->use_tc = value != 0;
+    for (auto& m : ctx->meshes)
+        if (m && m->graph) {
+            cudaGraphExecDestroy(m->graph);
+            m->graph = nullptr;
+        }
     return SDRT_OK;
 }
 

@@ -266,9 +266,9 @@ __global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __r
                 }
             }
         }
+        fence_proxy_async();         // every writer orders its staging stores before the bulk store
         __syncthreads();
         if (threadIdx.x == 0) {
-            fence_proxy_async();
             bulk_s2g(REC + B.rec_base + (size_t)e0 * B.ers, Rs, (uint32_t)(n * B.ers * sizeof(T)));
             bulk_s2g(FIUR + B.fiur_base + (size_t)e0 * B.frs, Fs, (uint32_t)(n * B.frs * sizeof(T)));
             bulk_commit();
@@ -463,6 +463,7 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
             const T inv = -met_e[0];
             epi_block<RS, V>(E, acc, inv, (size_t)B.u_off + e, B.ld, h * RS, NS);
         }
+        fence_proxy_async();  // this thread's reads of the tile precede the next tile's async copies
         __syncthreads();      // the tile buffers are free for the next tile's copies
     }
 }

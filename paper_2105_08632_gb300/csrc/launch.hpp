@@ -35,6 +35,13 @@ bool fast_path_available(int shape, int nsol, int nd, int system, int riemann);
 template <typename T>
 int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st);
 
+// Tensor-core (tcgen05, 3xTF32) variant of launch_interp_rec for FP32
+// tetrahedra of degree 3 with 5 variables (kernels_tc.cu).  Returns -1 if
+// the block is not of that kind.
+bool tc_interp_available(int shape, int nsol, int nvar);
+int launch_interp_tc(const KBlock<float>& B, int V, const float* U, float* REC, float* FIUR, int* err, int nsm,
+                     cudaStream_t st);
+
 // Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,

@@ -25,7 +25,7 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_get_etype_info", "sdrt_get_operator", "sdrt_setup_mesh", "sdrt_get_mesh_info",
             "sdrt_get_block_layout", "sdrt_get_sol_points", "sdrt_get_face_map", "sdrt_residual",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
-            "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc"]
+            "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option"]
 
 
 class SdrtError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
         "sdrt_profile_enable": (I, [P, I]),
         "sdrt_profile_collect": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "sdrt_residual_noalloc": (I, [P, I, P, P]),
+        "sdrt_set_option": (I, [P, I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -257,6 +258,13 @@ def sdrt_sync(ctx):
 
 def sdrt_launch_count(ctx):
     return int(lib().sdrt_launch_count(ctx))
+
+
+SDRT_OPT_TENSOR_CORES = 0
+
+
+def sdrt_set_option(ctx, option, value):
+    _check(ctx, lib().sdrt_set_option(ctx, int(option), int(value)))
 
 
 def sdrt_profile_enable(ctx, enable=True):

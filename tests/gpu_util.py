@@ -52,3 +52,15 @@ def rel_errors(got, want):
     w = np.concatenate([x.ravel() for x in want])
     scale = np.abs(w).max()
     return np.abs(g - w).max() / scale, np.sqrt(np.mean((g - w) ** 2)) / scale
+
+
+U32 = 2.0 ** -24
+
+
+def fp32_bound_ratio(got, want, scale):
+    """max over all values of |got - want| / (u S): the observed error in units
+    of the FP32 forward-error scale u * S (u = 2^-24, S = oracle term magnitudes)."""
+    g = np.concatenate([x.ravel() for x in got])
+    w = np.concatenate([x.ravel() for x in want])
+    S = np.concatenate([x.ravel() for x in scale])
+    return float(np.max(np.abs(g - w) / (U32 * S + 1e-300)))
