@@ -185,6 +185,9 @@ int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev);
  *    fixed SDRT_NOALLOC_SCRATCH_BYTES buffer that is part of the library image
  *    on every GPU that loads the library (held until process exit).  The
  *    caller passes U_dev and R_dev as for sdrt_residual.
+ *  - Inviscid systems only (advection, Euler): the viscous systems need
+ *    flux-point gradients that do not fit a fixed buffer of this size;
+ *    they return SDRT_ERR_UNSUPPORTED.
  *  - The mesh must need at most SDRT_NOALLOC_SCRATCH_BYTES of face states
  *    (nvar * external flux points (rows padded to 32 elements) * 4 or 8
  *    bytes); larger meshes are rejected with SDRT_ERR_UNSUPPORTED and a
@@ -216,8 +219,14 @@ int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* U_in_host, void* 
  * is taken. */
 int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* V_dev, void* JV_dev);
 
-/* Vector-Jacobian product JTW = (dR/dU)(U)^T . W (device arrays).  Inviscid
- * systems only (SDRT_ERR_UNSUPPORTED for advection-diffusion / Navier-Stokes). */
+/* Vector-Jacobian product JTW = (dR/dU)(U)^T . W (device arrays, state
+ * layout; the adjoint of the discrete operator of Sec. 2.1 / App. B, which the
+ * paper does not spell out: W is carried back through the divergence
+ * [M14 | M13]^T, the transposed Jacobians of the common and internal fluxes,
+ * and the interpolation [M0; M12]^T).  Same branch convention at ties as
+ * sdrt_jvp, so <W, J V> = <J^T W, V> up to rounding.  Inviscid systems only
+ * (SDRT_ERR_UNSUPPORTED for advection-diffusion / Navier-Stokes).  Uses the
+ * mesh's face-state buffers (allocated on first use). */
 int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* W_dev, void* JTW_dev);
 
 /* Synchronise the context's stream; returns SDRT_ERR_NONFINITE (and clears the
@@ -246,7 +255,7 @@ int sdrt_profile_enable(sdrt_ctx* ctx, int enable);
 /* Synchronise the stream, then ADD to ms_out[kind] the device milliseconds and
  * to count_out[kind] the number of launches recorded since the last collect.
  * kind: 0 = interpolation to external points, 1 = residual / divergence
- * kernel, 2 = its JVP variant, 3 = reserved.  Arrays of 4 entries, caller
+ * kernel, 2 = its JVP variant, 3 = flux-point gradients (viscous systems).  Arrays of 4 entries, caller
  * owned.  A graph replayed several times between two collects keeps only its
  * last replay's timings: collect after every sdrt_rk4_step call. */
 int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out);

@@ -56,8 +56,8 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& h) {
 struct EType {
     sdrt_etype_desc desc{};
     RefElement R;
-    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0, Mir = 0;
-    DevBuf Ai[2], Ad[2], Air[2];  // [0] double, [1] float
+    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0, Mir = 0, Mdt_pad = 0;
+    DevBuf Ai[2], Ad[2], Air[2], Ag[2], Adt[2];  // [0] double, [1] float
     DevBuf fe_face, fi_tab;
 };
 
@@ -67,6 +67,9 @@ struct MBlock {
     DevBuf metric, map;
     int tile = 32;                // elements per CTA tile
     int tile_dual = 32;
+    int gtile = 0, gtile_dual = 0;  // gradient kernel (viscous systems)
+    int vtile = 0;                // VJP kernels (0: not available for this block)
+    int64_t qfiu_off = 0;         // element offset of the block in QFIU
     // Record layout of the register-blocked path (kernels_fast.cu).
     int ers = 0, frs = 0, frec = 0, nmp = 0, pstride = 0;
     int64_t rec_base = 0, fiur_base = 0;
@@ -80,10 +83,12 @@ struct Mesh {
     int64_t state_len = 0, Ftot = 0, ndof = 0, nfe_total = 0;
     bool fast = false;                // every block on the register-blocked record path
     int64_t rec_total = 0, fiur_total = 0;
+    int64_t qfiu_total = 0;           // viscous: length of QFIU
     std::vector<int32_t> partner;     // canonical face map
     std::vector<uint8_t> is_left;
     std::vector<double> sol_xyz;
     DevBuf ufe, dufe, ustage, uacc, uhost_dev, rec, drec, fiur, dfiur;
+    DevBuf qfe, dqfe, qfiu, dqfiu;    // viscous: flux-point gradients (kargs.hpp layout)
     // RK4 graph cache
     cudaGraphExec_t graph = nullptr;
     const void* graph_u = nullptr;
@@ -123,7 +128,7 @@ struct sdrt_ctx {
 
 namespace {
 
-enum { KIND_INTERP = 0, KIND_RESIDUAL = 1, KIND_JVP = 2, KIND_COUNT = 4 };
+enum { KIND_INTERP = 0, KIND_RESIDUAL = 1, KIND_JVP = 2, KIND_GRAD = 3, KIND_COUNT = 4 };
 
 int new_slot(sdrt_ctx* ctx, int kind) {
     cudaEvent_t a, b;
@@ -167,6 +172,10 @@ void prof_end(sdrt_ctx* ctx, int s) {
     if (s < 0) return;
     if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s + 1], ctx->stream, cudaEventRecordExternal);
     else cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream);
+}
+
+bool viscous(const Mesh& m) {
+    return m.phys.system == SDRT_ADVDIFF || m.phys.system == SDRT_NAVIER_STOKES;
 }
 
 int fail(sdrt_ctx* c, int code, const std::string& msg) {
@@ -250,9 +259,11 @@ KBlock<T> make_kblock(const EType& et, const MBlock& b) {
     K.Mi_pad = et.Mi_pad;
     K.Ad = et.Ad[pi].as<T>();
     K.Md_pad = et.Md_pad;
-    K.Ag = nullptr;
-    K.Agf = nullptr;
+    K.Ag = et.Ag[pi].as<T>();
+    K.Adt = et.Adt[pi].as<T>();
+    K.Mdt_pad = et.Mdt_pad;
     K.Mg_pad = et.Mg_pad;
+    K.qfiu_off = b.qfiu_off;
     K.fe_face = et.fe_face.as<int>();
     K.fi_tab = et.fi_tab.as<int>();
     K.metric = b.metric.as<T>();
@@ -297,8 +308,12 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
     const KPhys<T> P = make_phys<T>(m.phys);
     T* ufe = m.ufe.as<T>();
     T* dufe = m.dufe.as<T>();
-    const int sys = m.phys.system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER;
-    if (m.fast) {
+    const int sys = m.phys.system;   // sdrt_system and System share their values
+    bool fast = m.fast;
+    if (fast && dU)
+        for (auto& bp : m.blocks)
+            if (!fast_jvp_available<T>(make_kblock<T>(*ctx->etypes[bp->etype], *bp), m.nvar)) fast = false;
+    if (fast) {
         // Register-blocked record path: interpolation of every block, then fluxes + divergence.
         T* rec = m.rec.as<T>();
         T* drec = m.drec.as<T>();
@@ -358,19 +373,66 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
             ++ctx->launches;
         }
     }
+    KVisc<T> Q{};
+    if (viscous(m)) {
+        // Flux-point gradients of every block (they read every block's u_fe).
+        Q = {m.qfe.as<T>(), dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr};
+        for (auto& bp : m.blocks) {
+            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+            const int TE = dU ? bp->gtile_dual : bp->gtile;
+            if (TE == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
+            const int s = prof_begin(ctx, KIND_GRAD);
+            int r = launch_grad<T>(K, sys, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, m.qfe.as<T>(),
+                                   dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr, TE,
+                                   grid_for(ctx, *bp, TE, 2), ctx->stream);
+            prof_end(ctx, s);
+            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
+            ++ctx->launches;
+        }
+    }
     for (auto& bp : m.blocks) {
         const EType& et = *ctx->etypes[bp->etype];
         KBlock<T> K = make_kblock<T>(et, *bp);
         const int TE = dU ? bp->tile_dual : bp->tile;
         if (TE == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
         const int s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
-        int r = launch_residual<T>(K, m.phys.system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER, m.phys.riemann,
-                                   m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, E, TE,
+        int r = launch_residual<T>(K, sys, m.phys.riemann, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, E, Q, TE,
                                    grid_for(ctx, *bp, TE, 2), ctx->stream);
         prof_end(ctx, s);
         if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
         ++ctx->launches;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+// W^T dR/dU: forward interpolation of every block, the face adjoints GS of
+// every block (in the tangent face-state buffer), then the element pass.
+template <typename T>
+int run_vjp(sdrt_ctx* ctx, Mesh& m, const T* U, const T* W, T* out) {
+    const KPhys<T> P = make_phys<T>(m.phys);
+    T* ufe = m.ufe.as<T>();
+    T* gs = m.dufe.as<T>();
+    for (auto& bp : m.blocks)
+        if (bp->vtile == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP tile does not fit in shared memory for this element type");
+    for (auto& bp : m.blocks) {
+        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+        const int s = prof_begin(ctx, KIND_INTERP);
+        launch_interp_ext<T>(K, m.nvar, U, ufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
+        prof_end(ctx, s);
+        ++ctx->launches;
+    }
+    for (int pass = 0; pass < 2; ++pass)
+        for (auto& bp : m.blocks) {
+            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+            const int s = prof_begin(ctx, KIND_JVP);
+            int r = launch_vjp<T>(K, pass, m.phys.system, m.phys.riemann, m.nd, U, W, ufe, gs, m.Ftot, P, out,
+                                  ctx->flag.as<int>(), bp->vtile, grid_for(ctx, *bp, bp->vtile, 2), ctx->stream);
+            prof_end(ctx, s);
+            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported by the VJP");
+            ++ctx->launches;
+        }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SDRT_OK;
@@ -421,6 +483,13 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
     const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
     if (!m.ufe.p) SDRT_CUDA(m.ufe.alloc((size_t)m.nvar * m.Ftot * es));
     if (need_dual && !m.dufe.p) SDRT_CUDA(m.dufe.alloc((size_t)m.nvar * m.Ftot * es));
+    if (viscous(m)) {
+        const size_t nq = (size_t)m.nd * m.nvar * m.Ftot;
+        if (!m.qfe.p) SDRT_CUDA(m.qfe.alloc(nq * es));
+        if (!m.qfiu.p) SDRT_CUDA(m.qfiu.alloc((size_t)m.qfiu_total * es));
+        if (need_dual && !m.dqfe.p) SDRT_CUDA(m.dqfe.alloc(nq * es));
+        if (need_dual && !m.dqfiu.p) SDRT_CUDA(m.dqfiu.alloc((size_t)m.qfiu_total * es));
+    }
     if (m.fast) {
         if (!m.rec.p) SDRT_CUDA(m.rec.alloc((size_t)m.rec_total * es));
         if (!m.fiur.p) SDRT_CUDA(m.fiur.alloc((size_t)m.fiur_total * es));
@@ -504,14 +573,34 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
     et->Mi_pad = round_up(et->Mi, 8);
     et->Md_pad = round_up(R.nsol, 8);
     et->Mg_pad = round_up(R.nd * R.nsol, 8);
-    std::vector<double> Ai((size_t)R.nsol * et->Mi_pad, 0.0), Ad((size_t)(R.nfe + R.nfi) * et->Md_pad, 0.0);
+    // Ai has kMR (8) trailing zeros: a GEMM over its M12 columns alone reads up to
+    // 8 rows past the last one.
+    std::vector<double> Ai((size_t)R.nsol * et->Mi_pad + 8, 0.0), Ad((size_t)(R.nfe + R.nfi) * et->Md_pad, 0.0);
+    const int nfe_pad = round_up(R.nfe, 8);
+    et->Mdt_pad = nfe_pad + round_up(R.nfi, 8);
+    std::vector<double> Adt((size_t)R.nsol * et->Mdt_pad, 0.0);
     for (int r = 0; r < R.nsol; ++r) {
         for (int j = 0; j < R.nfe; ++j) Ai[(size_t)r * et->Mi_pad + j] = R.M0[(size_t)j * R.nsol + r];
         for (int j = 0; j < R.nfiu; ++j) Ai[(size_t)r * et->Mi_pad + R.nfe + j] = R.M12[(size_t)j * R.nsol + r];
         for (int k = 0; k < R.nfe; ++k) Ad[(size_t)k * et->Md_pad + r] = R.M14[(size_t)r * R.nfe + k];
         for (int k = 0; k < R.nfi; ++k) Ad[(size_t)(R.nfe + k) * et->Md_pad + r] = R.M13[(size_t)r * R.nfi + k];
+        for (int k = 0; k < R.nfe; ++k) Adt[(size_t)r * et->Mdt_pad + k] = R.M14[(size_t)r * R.nfe + k];
+        for (int k = 0; k < R.nfi; ++k) Adt[(size_t)r * et->Mdt_pad + nfe_pad + k] = R.M13[(size_t)r * R.nfi + k];
     }
+    std::vector<float> Adtf(Adt.begin(), Adt.end());
     std::vector<float> Aif(Ai.begin(), Ai.end()), Adf(Ad.begin(), Ad.end());
+    // Gradient operator [M16 | M15 P M12] transposed: row k < nfe is column k of
+    // M16, row nfe + r is column r of M15 P M12 (P: internal DOF -> its point).
+    std::vector<double> Ag((size_t)(R.nfe + R.nsol) * et->Mg_pad, 0.0);
+    for (int m = 0; m < R.nd * R.nsol; ++m) {
+        for (int k = 0; k < R.nfe; ++k) Ag[(size_t)k * et->Mg_pad + m] = R.M16[(size_t)m * R.nfe + k];
+        for (int nu = 0; nu < R.nfi; ++nu) {
+            const double a = R.M15[(size_t)m * R.nfi + nu];
+            const double* row = &R.M12[(size_t)R.fi_point[nu] * R.nsol];
+            for (int r = 0; r < R.nsol; ++r) Ag[(size_t)(R.nfe + r) * et->Mg_pad + m] += a * row[r];
+        }
+    }
+    std::vector<float> Agf(Ag.begin(), Ag.end());
     // Row-major interpolation operator for the register-blocked kernels.
     et->Mir = round_up(et->Mi + 2, 4);   // zero rows past Mi: row pairs (j, j + 2) stay in bounds
     std::vector<double> Air((size_t)et->Mir * et->Md_pad, 0.0);
@@ -537,6 +626,10 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
         SDRT_CUDA(upload(et->fi_tab, tab));
         SDRT_CUDA(upload(et->Air[0], Air));
         SDRT_CUDA(upload(et->Air[1], Airf));
+        SDRT_CUDA(upload(et->Ag[0], Ag));
+        SDRT_CUDA(upload(et->Ag[1], Agf));
+        SDRT_CUDA(upload(et->Adt[0], Adt));
+        SDRT_CUDA(upload(et->Adt[1], Adtf));
     }
     ctx->etypes.push_back(std::move(et));
     *etype_id = (int)ctx->etypes.size() - 1;
@@ -578,10 +671,9 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
         return fail(ctx, SDRT_ERR_ARG, "null or empty argument");
     if (phys->ndim != 2 && phys->ndim != 3) return fail(ctx, SDRT_ERR_ARG, "ndim must be 2 or 3");
     if (phys->precision != SDRT_FP32 && phys->precision != SDRT_FP64) return fail(ctx, SDRT_ERR_ARG, "bad precision");
-    if (phys->system != SDRT_ADVECTION && phys->system != SDRT_EULER)
-        return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by this build");
-    if (phys->system == SDRT_ADVECTION && phys->riemann == SDRT_ROE)
-        return fail(ctx, SDRT_ERR_ARG, "Roe flux needs the Euler system");
+    if (phys->system < SDRT_ADVECTION || phys->system > SDRT_NAVIER_STOKES) return fail(ctx, SDRT_ERR_ARG, "bad system");
+    const bool scalar = phys->system == SDRT_ADVECTION || phys->system == SDRT_ADVDIFF;
+    if (scalar && phys->riemann == SDRT_ROE) return fail(ctx, SDRT_ERR_ARG, "Roe flux needs the Euler or Navier-Stokes system");
     auto m = std::make_unique<Mesh>();
     m->phys = *phys;
     const int nd = phys->ndim;
@@ -609,9 +701,11 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
         m->Ftot += (int64_t)R.nfe * mb->ld;
         m->ndof += (int64_t)R.nsol * m->nvar * B.nelem;
         canon += (int64_t)R.nfe * B.nelem;
-        if (!fast_path_available(R.shape, R.nsol, nd,
-                                 phys->system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER, phys->riemann))
-            m->fast = false;
+        if (!fast_path_available(R.shape, R.nsol, nd, phys->system, phys->riemann)) m->fast = false;
+        if (phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES) {
+            mb->qfiu_off = m->qfiu_total;
+            m->qfiu_total += (int64_t)R.nfiu * nd * m->nvar * mb->ld;
+        }
         m->blocks.push_back(std::move(mb));
     }
     m->nfe_total = canon;
@@ -853,6 +947,27 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
             }
             (dual ? mb.tile_dual : mb.tile) = TE;
         }
+        if (phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES) {
+            auto gsmem_of = [&](int TE, bool dual) {
+                return (R.nsol + R.nfe + nd * R.nsol) * m->nvar * TE * (f32 ? 4 : 8) * (dual ? 2 : 1);
+            };
+            for (int dual = 0; dual < 2; ++dual) {
+                int TE = 32;
+                while (TE > 4 && gsmem_of(TE, dual) > 100 * 1024) TE /= 2;
+                while (TE > 1 && gsmem_of(TE, dual) > 220 * 1024) TE /= 2;
+                if (gsmem_of(TE, dual) > 220 * 1024) {
+                    if (!dual) return fail(ctx, SDRT_ERR_UNSUPPORTED, "element type too large for the gradient tile");
+                    TE = 0;
+                }
+                (dual ? mb.gtile_dual : mb.gtile) = TE;
+            }
+        }
+        {
+            auto vsmem_of = [&](int TE) { return (R.nsol + R.nfiu + R.nfi + R.nfe) * m->nvar * TE * (f32 ? 4 : 8); };
+            int TE = 32;
+            while (TE > 1 && vsmem_of(TE) > 100 * 1024) TE /= 2;
+            mb.vtile = vsmem_of(TE) <= 220 * 1024 ? TE : 0;
+        }
     }
     ctx->meshes.push_back(std::move(m));
     *mesh_id = (int)ctx->meshes.size() - 1;
@@ -1059,10 +1174,15 @@ int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* V, void* JV)
 int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW) {
     int r = check_compute(ctx, mesh_id);
     if (r) return r;
-    (void)U;
-    (void)W;
-    (void)JTW;
-    return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP not available in this build");
+    if (!U || !W || !JTW || JTW == U || JTW == W) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (viscous(m)) return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP of the viscous systems is not implemented");
+    if ((r = ensure_workspace(ctx, m, true, false))) return r;
+    if (m.phys.precision == SDRT_FP32)
+        return run_vjp<float>(ctx, m, static_cast<const float*>(U), static_cast<const float*>(W),
+                              static_cast<float*>(JTW));
+    return run_vjp<double>(ctx, m, static_cast<const double*>(U), static_cast<const double*>(W),
+                           static_cast<double*>(JTW));
 }
 
 int sdrt_sync(sdrt_ctx* ctx) {
@@ -1102,9 +1222,8 @@ int residual_into(sdrt_ctx* ctx, Mesh& m, const T* U, T* R, T* ufe) {
     }
     for (auto& bp : m.blocks) {
         KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
-        int r = launch_residual<T>(K, m.phys.system == SDRT_ADVECTION ? SYS_ADVECTION : SYS_EULER, m.phys.riemann,
-                                   m.nd, U, nullptr, ufe, nullptr, m.Ftot, P, E, bp->tile,
-                                   grid_for(ctx, *bp, bp->tile, 2), ctx->stream);
+        int r = launch_residual<T>(K, m.phys.system, m.phys.riemann, m.nd, U, nullptr, ufe, nullptr, m.Ftot, P, E,
+                                   KVisc<T>{}, bp->tile, grid_for(ctx, *bp, bp->tile, 2), ctx->stream);
         if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
         ++ctx->launches;
     }
@@ -1127,6 +1246,8 @@ int internal_residual_with_scratch(sdrt_ctx* ctx, int mesh_id, const void* U, vo
     if (r) return r;
     if (!U || !R || U == R || !scratch) return fail(ctx, SDRT_ERR_ARG, "U and R must be distinct device arrays");
     Mesh& m = *ctx->meshes[mesh_id];
+    if (viscous(m))
+        return fail(ctx, SDRT_ERR_UNSUPPORTED, "the allocation-free entry point covers the inviscid systems only");
     const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
     const size_t need = (size_t)m.nvar * (size_t)m.Ftot * es;
     if (need > scratch_bytes)

@@ -163,4 +163,49 @@ __device__ __forceinline__ void roe(const S* uL, const S* uR, const T* n, T gamm
     for (int k = 0; k < V; ++k) F[k] = T(0.5) * (fL[k] + fR[k]) - T(0.5) * diss[k];
 }
 
+// ---------------------------------------------------------------------------
+// Viscous fluxes (paper Eq. "fluxOperatorNavierStokes"; mu dynamic,
+// mu c_p / Pr grad T = mu gamma / Pr grad e with e = E/rho - |v|^2/2).
+// q[d][v]: physical gradient of conserved variable v along x_d.
+// fv[d][v]: viscous part of the flux along x_d (zero for the density).
+template <typename S, typename T, int ND>
+__device__ __forceinline__ void ns_viscous(const S* u, const S (*q)[ND + 2], T mu, T gamma, T prandtl,
+                                           S (*fv)[ND + 2]) {
+    const S inv = T(1) / u[0];
+    S v[ND];
+    #pragma unroll
+    for (int i = 0; i < ND; ++i) v[i] = u[1 + i] * inv;
+    S gv[ND][ND];                 // gv[d][i] = d v_i / d x_d
+    #pragma unroll
+    for (int d = 0; d < ND; ++d)
+        #pragma unroll
+        for (int i = 0; i < ND; ++i) gv[d][i] = (q[d][1 + i] - q[d][0] * v[i]) * inv;
+    S div = gv[0][0];
+    #pragma unroll
+    for (int i = 1; i < ND; ++i) div = div + gv[i][i];
+    S tau[ND][ND];
+    #pragma unroll
+    for (int i = 0; i < ND; ++i)
+        #pragma unroll
+        for (int j = 0; j < ND; ++j) tau[i][j] = mu * (gv[j][i] + gv[i][j]);
+    #pragma unroll
+    for (int i = 0; i < ND; ++i) tau[i][i] = tau[i][i] - T(2.0 / 3.0) * mu * div;
+    const S Eo = u[ND + 1] * inv;
+    const T kap = mu * gamma / prandtl;
+    #pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        S ge = (q[d][ND + 1] - Eo * q[d][0]) * inv;
+        #pragma unroll
+        for (int i = 0; i < ND; ++i) ge = ge - v[i] * gv[d][i];
+        fv[d][0] = szero<S>();
+        S w = szero<S>();
+        #pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            fv[d][1 + i] = -tau[i][d];
+            w = w + tau[d][i] * v[i];
+        }
+        fv[d][ND + 1] = -w - kap * ge;
+    }
+}
+
 }  // namespace sdrt

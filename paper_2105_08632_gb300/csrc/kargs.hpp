@@ -28,9 +28,11 @@ struct KBlock {
     int Mi, Mi_pad;      // Mi = nfe + nfiu
     const T* Ad;         // divergence operator, transposed: [nfe + nfi][Md_pad], columns [M14 | M13]
     int Md_pad;
-    const T* Ag;         // viscous: gradient operator on U, transposed: [nsol][Mg_pad], rows (d, rho) of M15 P M12
-    const T* Agf;        // viscous: M16 transposed: [nfe][Mg_pad]
-    int Mg_pad;
+    const T* Adt;        // VJP: [M14 | M13] row-major: [nsol][Mdt_pad], M13 from column round_up(nfe, 8)
+    int Mdt_pad;
+    const T* Ag;         // viscous: [M16 | M15 P M12] transposed: [nfe + nsol][Mg_pad], columns (d, rho)
+    int Mg_pad;          // ND * nsol rounded up to 8
+    int64_t qfiu_off;    // viscous: element offset of the block in QFIU
     const int* fe_face;  // [nfe] local face of each external point
     const int* fi_tab;   // [nfiu][4]: count, then (nu | axis << 16) per internal DOF of the point
     const T* metric;     // [NM][ld]
@@ -54,6 +56,19 @@ struct KBlock {
     const int* pfr;      // [nelem][nfaces] REC offset of the partner's face record
     const unsigned char* perm;  // [nelem][pstride] local index, in the partner's face record, of each external point
     const int* recoff;   // [nfe] offset of external point j in the element record
+};
+
+// Physical gradients of the viscous systems at the flux points.
+//   QFE  [ND][V][F_tot]: gradient at external points (UFE indexing), component d
+//        of variable v at (d * V + v) * F_tot + fe_base + sigma * ld + e;
+//   QFIU per block: (k, d, v, e) at qfiu_off + ((k * ND + d) * V + v) * ld + e.
+// d-prefixed arrays: tangents (JVP).
+template <typename T>
+struct KVisc {
+    const T* qfe;
+    const T* dqfe;
+    const T* qfiu;
+    const T* dqfiu;
 };
 
 template <typename T>

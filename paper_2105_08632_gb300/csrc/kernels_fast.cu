@@ -617,12 +617,17 @@ void flux_rec_impl(const KBlock<T>& B, const T* REC, const T* FIUR, const KPhys<
     k<<<grid, 32 * NW, smem, st>>>(B, REC, FIUR, P, E);
 }
 
+template <typename T>
+int flux_rec_dual_smem(const KBlock<T>& B, int V) {
+    const int K2 = B.nfe + B.nfi;
+    return K2 * B.Md_pad * (int)sizeof(T) + K2 * V * 32 * (int)sizeof(Dual<T>);
+}
+
 template <typename T, int V, int SYS, int RIE, int NS>
 void flux_rec_dual_impl(const KBlock<T>& B, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,
                         const KPhys<T>& P, const KEpi<T>& E, int nsm, cudaStream_t st) {
     auto k = k_flux_rec_dual<T, V, 3, SYS, RIE, NS>;
-    const int K2 = B.nfe + B.nfi;
-    const int smem = K2 * B.Md_pad * (int)sizeof(T) + K2 * V * 32 * (int)sizeof(Dual<T>);
+    const int smem = flux_rec_dual_smem(B, V);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int per = blocks_per_sm(k, 32 * V, smem);
     const int need = (B.nelem + 31) / 32;
@@ -631,6 +636,13 @@ void flux_rec_dual_impl(const KBlock<T>& B, const T* REC, const T* dREC, const T
 }
 
 }  // namespace
+
+template <typename T>
+bool fast_jvp_available(const KBlock<T>& B, int V) {
+    return flux_rec_dual_smem(B, V) <= 227 * 1024;
+}
+template bool fast_jvp_available<float>(const KBlock<float>&, int);
+template bool fast_jvp_available<double>(const KBlock<double>&, int);
 
 bool fast_path_available(int shape, int nsol, int nd, int system, int riemann) {
     if (nd != 3 || shape != 2 /* tetrahedron */) return false;

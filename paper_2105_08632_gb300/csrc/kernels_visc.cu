@@ -1,0 +1,219 @@
+// Viscous systems (advection-diffusion, Navier-Stokes) on the generic FMA path.
+//
+// The viscous flux needs the gradient of the solution at the flux points
+// (paper Sec. 3 and App. B).  Per block and tile of TE elements, k_grad forms
+//   C  = (1/2 - beta) u_L + (1/2 + beta) u_R     common value at the external
+//                                                points (u_L, u_R: the face's sides)
+//   q~ = M16 C + (M15 P M12) U                   transformed gradient at the
+//                                                solution points, rows (axis d, point)
+//   q  = J^{-T} q~, i.e. q_i = sum_d (J^{-1})_{di} q~_d
+//   [q_fe; q_fiu] = [M0; M12] q                  written to QFE / QFIU
+// after which k_residual (generic.cuh) adds the LDG viscous common flux at the
+// external points and the viscous part of the transformed flux at the
+// internal DOFs.  One evaluation is three launches per block: k_interp_ext,
+// k_grad (after every block's interpolation) and k_residual (after every
+// block's gradient).
+#include <cstdint>
+
+#include "generic.cuh"
+#include "launch.hpp"
+
+namespace sdrt {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void store_state(T* X, T*, size_t i, T v) { X[i] = v; }
+template <typename T>
+__device__ __forceinline__ void store_state(T* X, T* dX, size_t i, Dual<T> v) {
+    X[i] = v.v;
+    dX[i] = v.d;
+}
+
+}  // namespace
+
+// Shared memory: RU = U tile (nsol rows), RC = C (nfe rows), both of V * TE
+// columns (v, te); RQ = q (nsol rows of ND * V * TE columns (d, v, te)).
+template <typename S, typename T, int V, int ND>
+__global__ void __launch_bounds__(256) k_grad(KBlock<T> B, const T* __restrict__ U, const T* __restrict__ dU,
+                                              const T* __restrict__ UFE, const T* __restrict__ dUFE, int64_t Ftot,
+                                              KPhys<T> P, T* __restrict__ QFE, T* __restrict__ dQFE,
+                                              T* __restrict__ QFIU, T* __restrict__ dQFIU, int TE) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NCOL = V * TE;
+    const int QCOL = ND * NCOL;
+    S* RU = reinterpret_cast<S*>(smem_raw);
+    S* RC = RU + (size_t)B.nsol * NCOL;
+    S* RQ = RC + (size_t)B.nfe * NCOL;
+    const int ntiles = (B.nelem + TE - 1) / TE;
+    constexpr int ND2 = ND * ND;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int e0 = tile * TE;
+        __syncthreads();
+        load_tile<S, T, V>(B, U, dU, e0, TE, RU);
+        // Common value at the external points.
+        for (int it = threadIdx.x; it < B.nfe * TE; it += blockDim.x) {
+            const int sg = it / TE;
+            const int te = it - sg * TE;
+            const int e = min(e0 + te, B.nelem - 1);
+            const int f = __ldg(B.fe_face + sg);
+            const T s = __ldg(B.metric + (size_t)(1 + ND2 + f * (ND + 1) + ND) * B.ld + e);
+            const T wo = s > T(0) ? T(0.5) - P.beta : T(0.5) + P.beta;   // own side is L when s > 0
+            const T wn = T(1) - wo;
+            S own[V], nbr[V];
+            gather_partner<S, T, V>(UFE, dUFE, Ftot, (int)(B.fe_base + (int64_t)sg * B.ld + e), own);
+            gather_partner<S, T, V>(UFE, dUFE, Ftot, __ldg(B.map + (size_t)sg * B.ld + e), nbr);
+            #pragma unroll
+            for (int v = 0; v < V; ++v) RC[(size_t)sg * NCOL + v * TE + te] = wo * own[v] + wn * nbr[v];
+        }
+        __syncthreads();
+        // q~ = [M16 | M15 P M12] [C; U]; row m = d * nsol + s goes to RQ row s, column block d.
+        tile_gemm<S, T>(B.Ag, B.Mg_pad, ND * B.nsol, B.nfe + B.nsol, RC, B.nfe, RU, NCOL,
+                        [&](int m0, int col, const S* acc) {
+                            #pragma unroll
+                            for (int i = 0; i < kMR; ++i) {
+                                const int m = m0 + i;
+                                if (m >= ND * B.nsol) break;
+                                const int d = m / B.nsol, sp = m - d * B.nsol;
+                                RQ[(size_t)sp * QCOL + d * NCOL + col] = acc[i];
+                            }
+                        });
+        __syncthreads();
+        // q = J^{-T} q~ at every solution point (metric rows S_di = det J (J^{-1})_di).
+        for (int it = threadIdx.x; it < B.nsol * NCOL; it += blockDim.x) {
+            const int sp = it / NCOL;
+            const int col = it - sp * NCOL;
+            const int te = col % TE;
+            const int e = min(e0 + te, B.nelem - 1);
+            const T inv = __ldg(B.metric + e);
+            S qt[ND];
+            #pragma unroll
+            for (int d = 0; d < ND; ++d) qt[d] = RQ[(size_t)sp * QCOL + d * NCOL + col];
+            #pragma unroll
+            for (int i = 0; i < ND; ++i) {
+                S q = qt[0] * (__ldg(B.metric + (size_t)(1 + i) * B.ld + e) * inv);
+                #pragma unroll
+                for (int d = 1; d < ND; ++d) q = q + qt[d] * (__ldg(B.metric + (size_t)(1 + d * ND + i) * B.ld + e) * inv);
+                RQ[(size_t)sp * QCOL + i * NCOL + col] = q;
+            }
+        }
+        __syncthreads();
+        // [q_fe; q_fiu] = [M0; M12] q; column (d, v, te) -> d * V + v = col / TE.
+        tile_gemm<S, T>(B.Ai, B.Mi_pad, B.Mi, B.nsol, RQ, B.nsol, RQ, QCOL,
+                        [&](int m0, int col, const S* acc) {
+                            const int dv = col / TE, te = col - dv * TE, e = e0 + te;
+                            if (e >= B.nelem) return;
+                            #pragma unroll
+                            for (int i = 0; i < kMR; ++i) {
+                                const int m = m0 + i;
+                                if (m >= B.Mi) break;
+                                if (m < B.nfe)
+                                    store_state(QFE, dQFE, (size_t)dv * Ftot + B.fe_base + (size_t)m * B.ld + e, acc[i]);
+                                else
+                                    store_state(QFIU, dQFIU,
+                                                (size_t)B.qfiu_off + ((size_t)(m - B.nfe) * (ND * V) + dv) * B.ld + e,
+                                                acc[i]);
+                            }
+                        });
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+
+template <typename T>
+int grad_smem(const KBlock<T>& B, int V, int nd, int TE, bool dual) {
+    return (B.nsol + B.nfe + nd * B.nsol) * V * TE * (int)sizeof(T) * (dual ? 2 : 1);
+}
+
+template <typename S, typename T, int V, int ND>
+static void launch_grad_impl(const KBlock<T>& B, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
+                             const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int TE, int smem, int grid,
+                             cudaStream_t st) {
+    auto k = k_grad<S, T, V, ND>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k<<<grid, 256, smem, st>>>(B, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, TE);
+}
+
+template <typename T>
+int launch_grad(const KBlock<T>& B, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
+                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int TE, int grid,
+                cudaStream_t st) {
+    const bool dual = dU != nullptr;
+    const int V = system == SYS_ADVDIFF ? 1 : nd + 2;
+    const int smem = grad_smem(B, V, nd, TE, dual);
+#define SDRT_GRAD(VV, NDD)                                                                                         \
+    do {                                                                                                           \
+        if (dual)                                                                                                  \
+            launch_grad_impl<Dual<T>, T, VV, NDD>(B, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, TE, smem,  \
+                                                  grid, st);                                                       \
+        else                                                                                                       \
+            launch_grad_impl<T, T, VV, NDD>(B, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, TE, smem, grid,  \
+                                            st);                                                                   \
+    } while (0)
+    if (system == SYS_ADVDIFF) {
+        if (nd == 2) SDRT_GRAD(1, 2);
+        else SDRT_GRAD(1, 3);
+        return 0;
+    }
+    if (system == SYS_NS) {
+        if (nd == 2) SDRT_GRAD(4, 2);
+        else SDRT_GRAD(5, 3);
+        return 0;
+    }
+#undef SDRT_GRAD
+    return -1;
+}
+
+template <typename T>
+int launch_residual_visc(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU,
+                         const T* UFE, const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E,
+                         const KVisc<T>& Q, int TE, int grid, cudaStream_t st) {
+    const bool dual = dU != nullptr;
+    int rowsA = 0;
+    const int V = system == SYS_ADVDIFF ? 1 : nd + 2;
+    const int smem = residual_smem(B, V, TE, dual, &rowsA);
+#define SDRT_RES(VV, NDD, SYSS, RIEE)                                                                             \
+    do {                                                                                                          \
+        if (dual)                                                                                                 \
+            launch_res_impl<Dual<T>, T, VV, NDD, SYSS, RIEE>(B, U, dU, UFE, dUFE, Ftot, P, E, Q, TE, rowsA, smem, \
+                                                             grid, st);                                           \
+        else                                                                                                      \
+            launch_res_impl<T, T, VV, NDD, SYSS, RIEE>(B, U, dU, UFE, dUFE, Ftot, P, E, Q, TE, rowsA, smem, grid, \
+                                                       st);                                                       \
+    } while (0)
+    if (system == SYS_ADVDIFF) {
+        if (nd == 2) SDRT_RES(1, 2, SYS_ADVDIFF, RIE_UPWIND);
+        else SDRT_RES(1, 3, SYS_ADVDIFF, RIE_UPWIND);
+        return 0;
+    }
+    if (system == SYS_NS) {
+        if (nd == 2) {
+            if (riemann == RIE_ROE) SDRT_RES(4, 2, SYS_NS, RIE_ROE);
+            else SDRT_RES(4, 2, SYS_NS, RIE_RUSANOV);
+        } else {
+            if (riemann == RIE_ROE) SDRT_RES(5, 3, SYS_NS, RIE_ROE);
+            else SDRT_RES(5, 3, SYS_NS, RIE_RUSANOV);
+        }
+        return 0;
+    }
+#undef SDRT_RES
+    return -1;
+}
+
+template int grad_smem<float>(const KBlock<float>&, int, int, int, bool);
+template int grad_smem<double>(const KBlock<double>&, int, int, int, bool);
+template int launch_grad<float>(const KBlock<float>&, int, int, const float*, const float*, const float*,
+                                const float*, int64_t, const KPhys<float>&, float*, float*, float*, float*, int, int,
+                                cudaStream_t);
+template int launch_grad<double>(const KBlock<double>&, int, int, const double*, const double*, const double*,
+                                 const double*, int64_t, const KPhys<double>&, double*, double*, double*, double*,
+                                 int, int, cudaStream_t);
+template int launch_residual_visc<float>(const KBlock<float>&, int, int, int, const float*, const float*,
+                                         const float*, const float*, int64_t, const KPhys<float>&,
+                                         const KEpi<float>&, const KVisc<float>&, int, int, cudaStream_t);
+template int launch_residual_visc<double>(const KBlock<double>&, int, int, int, const double*, const double*,
+                                          const double*, const double*, int64_t, const KPhys<double>&,
+                                          const KEpi<double>&, const KVisc<double>&, int, int, cudaStream_t);
+
+}  // namespace sdrt

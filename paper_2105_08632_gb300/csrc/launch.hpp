@@ -17,10 +17,40 @@ void launch_interp_ext(const KBlock<T>& B, int V, const T* U, T* UFE, int64_t Ft
 // Residual of one block with a fused epilogue.  dU / dUFE non-null: JVP mode
 // (tangent of the residual written to E.out, E.mode must be EPI_STORE).
 // Returns -1 for an unsupported (system, riemann, nd) combination.
+// Viscous systems read the flux-point gradients from Q (written by launch_grad).
 template <typename T>
 int launch_residual(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU, const T* UFE,
-                    const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E, int TE, int grid,
-                    cudaStream_t st);
+                    const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int TE,
+                    int grid, cudaStream_t st);
+
+// The viscous instantiations of launch_residual (kernels_visc.cu).
+template <typename T>
+int launch_residual_visc(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU,
+                         const T* UFE, const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E,
+                         const KVisc<T>& Q, int TE, int grid, cudaStream_t st);
+
+// Physical gradients of a viscous system at the flux points of one block
+// (UFE must hold u_fe of every block): QFE / QFIU (kargs.hpp layout), and with
+// dU / dUFE non-null also their tangents dQFE / dQFIU.  Returns -1 for an
+// unsupported (system, nd) combination.
+template <typename T>
+int launch_grad(const KBlock<T>& B, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
+                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int TE, int grid,
+                cudaStream_t st);
+
+// Vector-Jacobian product of the inviscid residual for one block (kernels_vjp.cu).
+// pass 0: GS (UFE layout) = s G at the block's external points from W;
+// pass 1 (after pass 0 of every block): out = W^T dR/dU, with UFE = u_fe of
+// every block.  Returns -1 for an unsupported combination.
+template <typename T>
+int launch_vjp(const KBlock<T>& B, int pass, int system, int riemann, int nd, const T* U, const T* W, const T* UFE,
+               T* GS, int64_t Ftot, const KPhys<T>& P, T* out, int* flag, int TE, int grid, cudaStream_t st);
+template <typename T>
+int vjp_smem(const KBlock<T>& B, int V, int TE);
+
+// Dynamic shared memory of the gradient kernel for tile width TE.
+template <typename T>
+int grad_smem(const KBlock<T>& B, int V, int nd, int TE, bool dual);
 
 // Dynamic shared memory of the residual kernel for tile width TE.
 template <typename T>
@@ -29,6 +59,11 @@ int residual_smem(const KBlock<T>& B, int V, int TE, bool dual, int* rowsA);
 // Register-blocked record path (kernels_fast.cu) for the element types
 // instantiated there (tetrahedra of degree 3 and 4).
 bool fast_path_available(int shape, int nsol, int nd, int system, int riemann);
+
+// Whether the JVP variant of the record path fits in shared memory for this
+// block (FP64 degree-4 tetrahedra do not: their JVP takes the generic path).
+template <typename T>
+bool fast_jvp_available(const KBlock<T>& B, int V);
 
 // [u_fe; u_fiu] = [M0; M12] U written as element records (REC, FIUR).
 // Returns -1 if not instantiated.

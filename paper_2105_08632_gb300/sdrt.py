@@ -271,7 +271,7 @@ def sdrt_profile_enable(ctx, enable=True):
     _check(ctx, lib().sdrt_profile_enable(ctx, 1 if enable else 0))
 
 
-KERNEL_KINDS = ("interp_ext", "residual", "residual_jvp", "reserved")
+KERNEL_KINDS = ("interp_ext", "residual", "residual_jvp", "gradient")
 
 
 def sdrt_profile_collect(ctx):

@@ -138,8 +138,8 @@ def test_rk4_host_entry_point_matches_device(ctx):
     assert np.array_equal(out, Ud.cpu().numpy())
 
 
-@pytest.mark.parametrize("kind,p,system", [("tet", 3, "euler"), ("pri", 2, "euler"), ("hex", 2, "euler"),
-                                           ("tet", 4, "advection")])
+@pytest.mark.parametrize("kind,p,system", [("tet", 3, "euler"), ("tet", 4, "euler"), ("pri", 2, "euler"),
+                                           ("hex", 2, "euler"), ("tet", 4, "advection")])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_jvp(ctx, kind, p, system, precision):
     riem = "rusanov" if system == "euler" else "upwind"

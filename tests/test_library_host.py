@@ -136,3 +136,19 @@ def test_error_codes(hctx):
     with pytest.raises(sdrt.SdrtError) as ei:
         sdrt.sdrt_residual(hctx, mid, 1, 2)
     assert ei.value.code == -4
+
+
+def test_viscous_mesh_setup_on_host(hctx):
+    """Advection-diffusion and Navier-Stokes meshes set up (host side); the
+    Roe flux is refused for the scalar systems."""
+    mesh = meshes.box_mesh("tet", (2, 2, 2), [0, 0, 0], [1, 1, 1])
+    et = sdrt.sdrt_setup_element_type(hctx, "tet", 3)
+    blocks = [(et, mesh["blocks"][0]["verts"])]
+    faces = (mesh["faces"], mesh["shift"])
+    for system, riem, nvar in (("ns", "roe", 5), ("ns", "rusanov", 5), ("advdiff", "upwind", 1)):
+        phys = sdrt.make_physics(system, 3, riem, "fp32", mu=0.01)
+        mid = sdrt.sdrt_setup_mesh(hctx, phys, blocks, faces)
+        assert sdrt.sdrt_get_mesh_info(hctx, mid)["nvar"] == nvar
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, sdrt.make_physics("advdiff", 3, "roe", "fp32", mu=0.01), blocks, faces)
+    assert ei.value.code == -1

@@ -278,6 +278,27 @@ def test_jvp_of_linear_advection_is_the_residual():
     assert max(np.abs(a - b).max() for a, b in zip(Jv, Rv)) < 1e-13
 
 
+def test_vjp_is_the_gradient_of_the_weighted_residual():
+    """W^T J is the gradient of phi(U) = <W, R(U)>: checked by central
+    differences of phi along random directions (independent of the JVP)."""
+    geom, _ = _geom("tet", 1)
+    phys = phx.Physics("euler", 3, "rusanov")
+    rng = np.random.default_rng(10)
+    U = _eval(geom, _smooth_gas_state, 5)
+    W = [rng.normal(size=u.shape) for u in U]
+    g = ores.vjp(geom, phys, U, W)
+
+    def phi(X):
+        return sum(float(np.sum(w * r)) for w, r in zip(W, ores.residual(geom, phys, X)))
+
+    h = 1e-6
+    for _ in range(3):
+        d = [rng.normal(size=u.shape) for u in U]
+        fd = (phi([u + h * x for u, x in zip(U, d)]) - phi([u - h * x for u, x in zip(U, d)])) / (2 * h)
+        ad = sum(float(np.sum(a * x)) for a, x in zip(g, d))
+        assert abs(fd - ad) < 1e-6 * max(1.0, abs(ad)), (fd, ad)
+
+
 def test_face_map_is_an_involution_pairing_coincident_points():
     for shape in ("tri", "tet", "pri", "hex", "quad"):
         geom, m = _geom(shape, 2)
