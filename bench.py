@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU path and the accuracy check")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--accuracy-steps", type=int, default=20)
+    ap.add_argument("--ncell", type=int, default=NCELL, help="cubes per axis (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -206,6 +210,76 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def fp64_leg(sdrt, ctx, mesh, stream, flush, U0, ndof, args):
+    """The plain FP64 GPU path on the same workload (timed like the main arm,
+    fewer steps) and the accuracy of the FP32 path against it: one residual,
+    and the state after a few RK4 steps (relative L2 / L-inf over all values;
+    'update' errors are relative to the FP64 change of the state)."""
+    import torch
+    M32 = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
+    M64 = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp64", gamma=1.4))
+    dev = flush.device
+    h64 = M64.pack([U0])
+    U64 = torch.from_numpy(h64).to(dev)
+    for i in range(3):
+        flush.fill_(float(i))
+        M64.rk4_step(U64, DT, 1)
+    M64.sync()
+    ms = []
+    for i in range(args.fp64_steps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M64.rk4_step(U64, DT, 1)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    M64.sync()
+    ms64 = float(np.mean(ms))
+    fp64 = {"value": ndof * 4 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+            "dtype": "f64"}
+    # accuracy of the FP32 path against the FP64 path
+    a64 = torch.from_numpy(h64).to(dev)
+    a32 = torch.from_numpy(M32.pack([U0])).to(dev)
+    r64 = torch.zeros_like(a64)
+    r32 = torch.zeros_like(a32)
+    M64.residual(a64, r64)
+    M32.residual(a32, r32)
+    M64.rk4_step(a64, DT, args.accuracy_steps)
+    M32.rk4_step(a32, DT, args.accuracy_steps)
+    M32.sync()
+    M64.sync()
+    R64, R32 = M64.unpack(r64.cpu().numpy())[0], M32.unpack(r32.cpu().numpy())[0].astype(np.float64)
+    S64, S32 = M64.unpack(a64.cpu().numpy())[0], M32.unpack(a32.cpu().numpy())[0].astype(np.float64)
+    dR, dS, dU = R32 - R64, S32 - S64, S64 - U0
+
+    def rel(a, b):
+        return {"rel_l2": float(np.linalg.norm(a) / np.linalg.norm(b)),
+                "rel_linf": float(np.abs(a).max() / np.abs(b).max())}
+
+    accuracy = {"reference": "FP64 GPU path on the same workload",
+                "residual": rel(dR, R64),
+                f"state_after_{args.accuracy_steps}_steps": rel(dS, S64),
+                f"update_after_{args.accuracy_steps}_steps": rel(dS, dU)}
+    return fp64, accuracy
+
+
+def aggregate(total_ms, steps, ndof, dist=None, device="cpu"):
+    """Whole-job timing of the replicas: the timed region is the maximum over
+    ranks, the throughput counts every rank's DOF updates (4 residual
+    evaluations per RK4 step).  Returns (total ms, ms per step, DOF-updates/s)."""
+    world = 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        world = dist.get_world_size()
+    ms_per_step = total_ms / steps
+    return total_ms, ms_per_step, world * ndof * 4 / (ms_per_step / 1e3)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -228,7 +302,7 @@ def main():
     stream = torch.cuda.Stream(local)
     torch.cuda.set_stream(stream)
     ctx = sdrt.Context(local, stream.cuda_stream)
-    mesh = workload_mesh()
+    mesh = workload_mesh(args.ncell)
     phys = sdrt.make_physics("euler", 3, "rusanov", args.precision, gamma=1.4)
     M = sdrt.Mesh(ctx, mesh, 3, phys)
     lay = M.layouts[0]
@@ -270,13 +344,7 @@ def main():
     clocks = sampler.stop()
     sdrt.sdrt_profile_enable(ctx.ptr, False)
     M.sync()
-    total_ms = float(np.sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * ndof * 4 / (ms_per_step / 1e3)
+    total_ms, ms_per_step, value = aggregate(float(np.sum(step_ms)), args.steps, ndof, dist, f"cuda:{local}")
 
     # Roofline of the dominant kernel (the residual / divergence kernel).
     s = 4 if args.precision == "fp32" else 8
@@ -317,20 +385,25 @@ def main():
         e2e = {"value": world * ndof * 4 / float(np.mean(e2e_t)), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "api": "sdrt_rk4_step_host (pinned host buffers, 1 step per call)"}
 
+    fp64, accuracy = None, None
+    if rank == 0 and args.precision == "fp32" and not args.no_fp64:
+        fp64, accuracy = fp64_leg(sdrt, ctx, mesh, stream, flush, U0, ndof, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
 
     if rank == 0:
+        workload = WORKLOAD if args.ncell == NCELL else f"euler3d_tet_p3_{6 * args.ncell ** 3}_rk4"
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "elements": nelem, "degree": 3, "nsol": nsol, "nvar": nvar,
+                "config": {"workload": workload, "elements": nelem, "degree": 3, "nsol": nsol, "nvar": nvar,
                            "ndof": ndof, "residuals_per_step": 4, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MiB write, untimed)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks}
+                "clocks": clocks, "fp64_path": fp64, "accuracy": accuracy}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -372,19 +372,50 @@ class Mesh:
     def face_map(self):
         return sdrt_get_face_map(self.ctx.ptr, self.id, self.info["nfe_total"])
 
+    def _check(self, *arrays, device=True):
+        """The C ABI takes bare pointers: check length, dtype, contiguity and
+        placement of every state array before a call reaches the device."""
+        for a in arrays:
+            if isinstance(a, int):
+                continue                      # raw pointer: the caller vouches for it
+            n = a.numel() if hasattr(a, "numel") else a.size
+            if n != self.state_len:
+                raise ValueError(f"state array has {n} values, the mesh needs {self.state_len}")
+            if hasattr(a, "is_cuda"):
+                if a.is_cuda != device:
+                    raise ValueError("state array on the wrong device" if device else "host buffer expected")
+                if device and a.device.index != self.ctx.device:
+                    raise ValueError(f"state array on cuda:{a.device.index}, context on cuda:{self.ctx.device}")
+                if not a.is_contiguous():
+                    raise ValueError("state array must be contiguous")
+                ok = str(a.dtype) == ("torch.float32" if self.dtype_np == np.float32 else "torch.float64")
+            else:
+                if device:
+                    raise ValueError("device computation needs a CUDA tensor or a raw device pointer")
+                if not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("state array must be contiguous")
+                ok = a.dtype == self.dtype_np
+            if not ok:
+                raise ValueError("state array dtype does not match the mesh precision")
+
     def residual(self, U, R):
+        self._check(U, R)
         sdrt_residual(self.ctx.ptr, self.id, U, R)
 
     def rk4_step(self, U, dt, nsteps=1):
+        self._check(U)
         sdrt_rk4_step(self.ctx.ptr, self.id, U, dt, nsteps)
 
     def rk4_step_host(self, U_in, U_out, dt, nsteps=1):
+        self._check(U_in, U_out, device=False)
         sdrt_rk4_step_host(self.ctx.ptr, self.id, U_in, U_out, dt, nsteps)
 
     def jvp(self, U, V, JV):
+        self._check(U, V, JV)
         sdrt_jvp(self.ctx.ptr, self.id, U, V, JV)
 
     def vjp(self, U, W, JTW):
+        self._check(U, W, JTW)
         sdrt_vjp(self.ctx.ptr, self.id, U, W, JTW)
 
     def sync(self):

@@ -133,3 +133,41 @@ def test_vjp_viscous_rejected(ctx):
     with pytest.raises(sdrt.SdrtError) as ei:
         M.vjp(U, U.clone(), torch.zeros_like(U))
     assert ei.value.code == -2
+
+
+def test_autograd_function_matches_the_c_abi(ctx):
+    from paper_2105_08632_gb300 import autograd
+    M, geom, oph, _ = gu.build_pair(ctx, "tet", (3, 3, 2), 3, "euler", "rusanov", "fp64")
+    U = _dev(M, _state(geom, oph, 37))
+    rng = np.random.default_rng(38)
+    V = _dev(M, [rng.normal(size=(g.ops.n_sol, 5, g.nelem)) for g in geom.blocks])
+    W = _dev(M, [rng.normal(size=(g.ops.n_sol, 5, g.nelem)) for g in geom.blocks])
+    # forward
+    R = autograd.residual(U, M)
+    R_ref = torch.zeros_like(U)
+    M.residual(U, R_ref)
+    assert torch.equal(R, R_ref)
+    # reverse mode = VJP
+    Ug = U.clone().requires_grad_(True)
+    (g,) = torch.autograd.grad((autograd.residual(Ug, M) * W).sum(), Ug)
+    g_ref = torch.zeros_like(U)
+    M.vjp(U, W, g_ref)
+    assert torch.equal(g, g_ref)
+    # forward mode = JVP
+    import torch.autograd.forward_ad as fwAD
+    with fwAD.dual_level():
+        out = autograd.residual(fwAD.make_dual(U, V), M)
+        tangent = fwAD.unpack_dual(out).tangent
+    j_ref = torch.zeros_like(U)
+    M.jvp(U, V, j_ref)
+    assert torch.equal(tangent, j_ref)
+
+
+def test_binding_rejects_bad_state_arrays(ctx):
+    M, geom, oph, _ = gu.build_pair(ctx, "tet", (2, 2, 2), 2, "euler", "rusanov", "fp32")
+    good = torch.zeros(M.state_len, dtype=torch.float32, device="cuda")
+    for bad in (torch.zeros(M.state_len - 1, dtype=torch.float32, device="cuda"),
+                torch.zeros(M.state_len, dtype=torch.float64, device="cuda"),
+                torch.zeros(M.state_len, dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            M.residual(bad, good)
