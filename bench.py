@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--accuracy-steps", type=int, default=20)
     ap.add_argument("--ncell", type=int, default=NCELL, help="cubes per axis (profiling of smaller cases)")
+    ap.add_argument("--tc-div", type=int, default=0, choices=[0, 1],
+                    help="divergence on the tensor cores (SDRT_OPT_TC_DIVERGENCE)")
+    ap.add_argument("--tc-interp", type=int, default=0, choices=[0, 1],
+                    help="interpolation on the tensor cores (SDRT_OPT_TENSOR_CORES)")
     return ap.parse_args()
 
 
@@ -302,6 +306,8 @@ def main():
     stream = torch.cuda.Stream(local)
     torch.cuda.set_stream(stream)
     ctx = sdrt.Context(local, stream.cuda_stream)
+    sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TC_DIVERGENCE, args.tc_div)
+    sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TENSOR_CORES, args.tc_interp)
     mesh = workload_mesh(args.ncell)
     phys = sdrt.make_physics("euler", 3, "rusanov", args.precision, gamma=1.4)
     M = sdrt.Mesh(ctx, mesh, 3, phys)
@@ -398,7 +404,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-                "config": {"workload": workload, "elements": nelem, "degree": 3, "nsol": nsol, "nvar": nvar,
+                "config": {"workload": workload, "elements": nelem, "tc_divergence": args.tc_div,
+                           "tc_interpolation": args.tc_interp, "degree": 3, "nsol": nsol, "nvar": nvar,
                            "ndof": ndof, "residuals_per_step": 4, "precision": args.precision,
                            "l2": "flushed between timed steps (256 MiB write, untimed)",
                            "parallelism": f"replicas x{world}"},

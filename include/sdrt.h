@@ -244,6 +244,11 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     only (currently the faster of the two for that kernel).  Results agree
  *     to FP32 rounding. */
 #define SDRT_OPT_TENSOR_CORES 0
+/*   SDRT_OPT_TC_DIVERGENCE (default 0): 1 = for FP32 Euler / Rusanov on
+ *     tetrahedra of degree 3, compute the fluxes on the CUDA cores and the
+ *     divergence [M14 | M13] F~ on the tensor cores (tcgen05, 3xTF32, FP32
+ *     accumulation in tensor memory); 0 = CUDA-core FMA accumulation. */
+#define SDRT_OPT_TC_DIVERGENCE 1
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 
 /* Per-launch device timing with CUDA events recorded on the context's stream

@@ -107,7 +107,8 @@ struct sdrt_ctx {
     cudaStream_t stream = nullptr;
     int nsm = 1;
     bool host_only = false;       // device == -1: host-side setup only, no compute
-    bool use_tc = false;          // tensor-core kernels where instantiated (SDRT_OPT_TENSOR_CORES)
+    bool use_tc = false;          // tensor-core interpolation where instantiated (SDRT_OPT_TENSOR_CORES)
+    bool use_tc_div = false;      // tensor-core divergence where instantiated (SDRT_OPT_TC_DIVERGENCE)
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
     std::vector<std::unique_ptr<Mesh>> meshes;
@@ -348,10 +349,17 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
             }
         }
         for (auto& bp : m.blocks) {
-            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+            const EType& et = *ctx->etypes[bp->etype];
+            KBlock<T> K = make_kblock<T>(et, *bp);
             const int s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
-            launch_flux_rec<T>(K, sys, rec, dU ? drec : nullptr, fiur, dU ? dfiur : nullptr, P, E, ctx->nsm,
-                               ctx->stream);
+            int r = -1;
+            if constexpr (std::is_same<T, float>::value) {
+                if (!dU && ctx->use_tc_div && tc_flux_available(et.R.shape, et.R.nsol, m.nvar, sys, m.phys.riemann))
+                    r = launch_flux_tc(K, rec, fiur, P, E, ctx->nsm, ctx->stream);
+            }
+            if (r != 0)
+                launch_flux_rec<T>(K, sys, rec, dU ? drec : nullptr, fiur, dU ? dfiur : nullptr, P, E, ctx->nsm,
+                                   ctx->stream);
             prof_end(ctx, s);
             ++ctx->launches;
         }
@@ -1098,8 +1106,9 @@ int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
 
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     if (!ctx) return SDRT_ERR_ARG;
-    if (option != SDRT_OPT_TENSOR_CORES) return fail(ctx, SDRT_ERR_ARG, "unknown option");
-    ctx->use_tc = value != 0;
+    if (option == SDRT_OPT_TENSOR_CORES) ctx->use_tc = value != 0;
+    else if (option == SDRT_OPT_TC_DIVERGENCE) ctx->use_tc_div = value != 0;
+    else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {
             cudaGraphExecDestroy(m->graph);

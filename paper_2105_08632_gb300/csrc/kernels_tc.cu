@@ -17,6 +17,7 @@
 // (the same layout as k_interp_rec).
 #include <cstdint>
 
+#include "flux_rec.cuh"
 #include "kargs.hpp"
 #include "launch.hpp"
 
@@ -47,6 +48,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(bar)), "r"(bytes) : "memory");
+}
+// Global -> shared bulk copy completing on bar (16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s32(dst)),
+                 "l"(src), "r"(bytes), "r"(s32(bar))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(s32(src)), "r"(bytes)
                  : "memory");
@@ -278,6 +289,339 @@ __global__ void __launch_bounds__(128, 1) k_interp_tc(KBlock<float> B, const flo
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// ---------------------------------------------------------------------------
+// Euler fluxes on the CUDA cores, divergence on the tensor cores: tetrahedra of
+// degree 3, FP32 states, 3xTF32 products with FP32 accumulation.
+//
+// Per tile of TE = 24 elements the divergence R~_v = [M14 | M13] F~_v of every
+// variable v (paper App. B, Eq. "residual_sdrt_matrices") is one GEMM
+//   D (128 x 32, FP32 in TMEM) = A (128 x K) B^T (32 x K)
+// with rows v * 24 + e of A holding element e's transformed fluxes of variable
+// v (rows 120..127 stay zero) and B the operator (N = 32 rows for the 20
+// solution points).  K runs in two phases over one 40-column A buffer:
+//   phase 1: the 40 external points; thread h (0..9) of an element owns points
+//            4h .. 4h+3 and writes them with one 16-byte store per variable;
+//   phase 2: the 10 internal points, point h with its 3 axis DOFs in columns
+//            4h .. 4h+2 (column 4h+3 zero); the operator's internal columns are
+//            reordered to this layout when it is staged.
+// The tensor core thus replaces the per-element FMA accumulation and the
+// exchange of fluxes between threads.  Each thread finally reads 10 rows of one
+// TMEM lane (v, e) and applies dU/dt = -R~ / det J with the RK stage update.
+// Records are staged as in k_flux_rec (bulk copies completing on an mbarrier).
+template <int NS, int NFE, int NFIU>
+__global__ void __launch_bounds__(256, 2) k_flux_tc(KBlock<float> B, const float* __restrict__ REC,
+                                                    const float* __restrict__ FIUR, KPhys<float> P,
+                                                    KEpi<float> E) {
+    constexpr int V = 5, ND = 3, NFACE = 4, ND2 = 9;
+    constexpr int TE = 24;                           // elements per tile
+    constexpr int G = 10;                            // threads per element
+    constexpr int KA = 40;                           // K columns per phase
+    constexpr int KB = 2 * KA;                       // operator K columns
+    constexpr int NP = 32;                           // N: solution points padded
+    static_assert(NFE == KA && 4 * NFIU == KA && NFE == 4 * G && NFIU == G && NS <= NP, "tetrahedra of degree 3");
+    constexpr uint32_t LBO = 128;
+    constexpr uint32_t SBO_A = (KA / 4) * 128;
+    constexpr uint32_t SBO_B = (KB / 4) * 128;
+    constexpr int A_BYTES = 128 * KA * 4;
+    constexpr int B_BYTES = NP * KB * 4;
+    constexpr uint32_t IDESC = idesc_tf32(128, NP);
+    constexpr uint32_t kCols = 32;
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* Bh = smem_raw;                    // operator [NP][KB], TF32 hi / lo
+    unsigned char* Bl = Bh + B_BYTES;
+    unsigned char* Ah = Bl + B_BYTES;                // fluxes [128][KA], TF32 hi / lo
+    unsigned char* Al = Ah + A_BYTES;
+    float* own = reinterpret_cast<float*>(Al + A_BYTES);          // [TE][ers]
+    float* part = own + (size_t)TE * B.ers;                        // [TE][ers]
+    float* fiu = part + (size_t)TE * B.ers;                        // [TE][frs]
+    float* met = fiu + (size_t)TE * B.frs;                         // [TE][nmp]
+    unsigned char* prm = reinterpret_cast<unsigned char*>(met + (size_t)TE * B.nmp);   // [TE][pstride]
+    int* roff = reinterpret_cast<int*>(prm + (size_t)TE * B.pstride);                 // [NFE]
+    int* fface = roff + NFE;                                                           // [NFE]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(fface + NFE);                          // [2]: loads, MMAs
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    if (warp == 0) tmem_alloc(tslot, kCols);
+    // Operator B[r][k]: k < 40 external point k; k = 40 + 4 q + d internal
+    // point q, axis d (< 3), i.e. operator column NFE + d NFIU + q.
+    for (int i = tid; i < NP * KB; i += blockDim.x) {
+        const int r = i / KB, k = i % KB;
+        float x = 0.f;
+        if (r < NS) {
+            if (k < NFE) {
+                x = B.Ad[(size_t)k * B.Md_pad + r];
+            } else {
+                const int q = (k - NFE) >> 2, d = (k - NFE) & 3;
+                if (d < ND) x = B.Ad[(size_t)(NFE + d * NFIU + q) * B.Md_pad + r];
+            }
+        }
+        const float h = to_tf32(x);
+        *reinterpret_cast<float*>(Bh + core_off(r, k, KB)) = h;
+        *reinterpret_cast<float*>(Bl + core_off(r, k, KB)) = to_tf32(x - h);
+    }
+    for (int i = tid; i < 2 * A_BYTES / 4; i += blockDim.x) reinterpret_cast<float*>(Ah)[i] = 0.f;
+    for (int i = tid; i < NFE; i += blockDim.x) {
+        roff[i] = B.recoff[i];
+        fface[i] = B.fe_face[i];
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // Flux work: thread (e, h) with e = tid % TE, h = tid / TE (tid < TE * G).
+    const bool worker = tid < TE * G;
+    const int fe_ = tid % TE;
+    const int h = worker ? tid / TE : 0;
+    // Epilogue: TMEM lane L = 32 (warp % 4) + lane holds row (v, e) = (L / TE, L % TE);
+    // warps 0-3 apply solution rows 0..9, warps 4-7 rows 10..19.
+    const int lrow = 32 * (warp & 3) + (tid & 31);
+    const int r0 = (warp >> 2) * 10;
+
+    uint32_t ph_ld = 0, ph_mma = 0;
+    int* err = E.flag;
+    const int ntiles = (B.nelem + TE - 1) / TE;
+    // Bulk copies of one tile's records (own external-point records, internal-
+    // point records, metric rows, permutations, and the four partner face
+    // records of every element), all completing on bar[0].
+    auto issue_loads = [&](int t_) {
+        const int e0_ = t_ * TE;
+        const int n_ = min(TE, B.nelem - e0_);
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)((size_t)n_ * (B.ers + NFACE * B.frec + B.frs + B.nmp) * sizeof(float) +
+                                              (size_t)n_ * B.pstride);
+            mbar_arrive_expect_tx(&bar[0], bytes);
+            fence_proxy_async();
+            bulk_g2s(own, REC + B.rec_base + (size_t)e0_ * B.ers, (uint32_t)(n_ * B.ers * sizeof(float)), &bar[0]);
+            bulk_g2s(fiu, FIUR + B.fiur_base + (size_t)e0_ * B.frs, (uint32_t)(n_ * B.frs * sizeof(float)), &bar[0]);
+            bulk_g2s(met, B.maos + (size_t)e0_ * B.nmp, (uint32_t)(n_ * B.nmp * sizeof(float)), &bar[0]);
+            bulk_g2s(prm, B.perm + (size_t)e0_ * B.pstride, (uint32_t)(n_ * B.pstride), &bar[0]);
+        }
+        for (int t = tid; t < n_ * NFACE; t += blockDim.x) {
+            const int le_ = t / NFACE, f = t % NFACE;
+            const int src = __ldg(B.pfr + (size_t)(e0_ + le_) * NFACE + f);
+            fence_proxy_async();
+            bulk_g2s(part + (size_t)le_ * B.ers + f * B.frec, REC + src, (uint32_t)(B.frec * sizeof(float)), &bar[0]);
+        }
+    };
+    if (blockIdx.x < ntiles) issue_loads(blockIdx.x);
+    const bool need_u0 = E.mode == EPI_RK_FIRST || E.mode == EPI_RK_MID;
+    const bool need_acc = E.mode == EPI_RK_MID || E.mode == EPI_RK_LAST;
+    const int ev = lrow / TE, ee = lrow % TE;      // epilogue row (v, e) of this thread's TMEM lane
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int e0 = tile * TE;
+        const int n = min(TE, B.nelem - e0);
+        const bool epi = lrow < V * TE && ee < n;
+        const size_t ebase = (size_t)B.u_off + (size_t)ev * B.ld + e0 + ee;
+        const size_t ers_ = (size_t)V * B.ld;
+        // Stage-update inputs of the epilogue, loaded early (independent of the fluxes).
+        float a[10], b[10];
+        #pragma unroll
+        for (int i = 0; i < 10; ++i) {
+            const size_t idx = ebase + (size_t)(r0 + i) * ers_;
+            a[i] = (epi && need_u0) ? __ldg(E.u0 + idx) : 0.f;
+            b[i] = (epi && need_acc) ? E.uacc[idx] : 0.f;
+        }
+        if (!mbar_wait(&bar[0], ph_ld)) {
+            *err = 2;
+            mbar_wait(&bar[0], ph_ld);
+        }
+        ph_ld ^= 1u;
+
+        const int le = fe_ < n ? fe_ : 0;     // past the tile's end: a real element, never stored
+        const float* own_e = own + (size_t)le * B.ers;
+        const float* part_e = part + (size_t)le * B.ers;
+        const float* met_e = met + (size_t)le * B.nmp;
+        const unsigned char* prm_e = prm + (size_t)le * B.pstride;
+        // Phase 1: external points 4h .. 4h+3.
+        if (worker) {
+            float F[4][V];
+            #pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * h + jj;
+                const int f = fface[j];
+                const int mrow = 1 + ND2 + f * (ND + 1);
+                float nrm[ND];
+                #pragma unroll
+                for (int c = 0; c < ND; ++c) nrm[c] = met_e[mrow + c];
+                const float s = met_e[mrow + ND];
+                const float* uo_p = own_e + roff[j];
+                const float* un_p = part_e + f * B.frec + (int)prm_e[j] * V;
+                float uo[V], un[V];
+                #pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    uo[v] = uo_p[v];
+                    un[v] = un_p[v];
+                }
+                if (s > 0.f) rusanov_rec<float, ND>(uo, un, nrm, P.gamma, s, F[jj]);
+                else rusanov_rec<float, ND>(un, uo, nrm, P.gamma, s, F[jj]);
+            }
+            #pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float4 hi, lo;
+                float* hp = &hi.x;
+                float* lp = &lo.x;
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    hp[q] = to_tf32(F[q][v]);
+                    lp[q] = to_tf32(F[q][v] - hp[q]);
+                }
+                const uint32_t o = core_off(v * TE + fe_, 4 * h, KA);
+                *reinterpret_cast<float4*>(Ah + o) = hi;
+                *reinterpret_cast<float4*>(Al + o) = lo;
+            }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            #pragma unroll
+            for (int kk = 0; kk < KA / 8; ++kk) {
+                const uint32_t ko = (uint32_t)kk * 2 * LBO;
+                const uint64_t dah = smem_desc(Ah + ko, LBO, SBO_A), dal = smem_desc(Al + ko, LBO, SBO_A);
+                const uint64_t dbh = smem_desc(Bh + ko, LBO, SBO_B), dbl = smem_desc(Bl + ko, LBO, SBO_B);
+                mma_tf32(tmem, dah, dbh, IDESC, kk > 0 ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, IDESC, 1u);
+                mma_tf32(tmem, dal, dbh, IDESC, 1u);
+            }
+            mma_commit(&bar[1]);
+        }
+        // Phase 2 fluxes (registers) while the tensor core works: internal point h.
+        float Ft[ND][V];
+        if (worker) {
+            float u[V];
+            #pragma unroll
+            for (int v = 0; v < V; ++v) u[v] = fiu[(size_t)le * B.frs + h * V + v];
+            float pinv, pv[ND], pp;
+            prim_rec<float, ND>(u, P.gamma, pinv, pv, pp);
+            #pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const float* S = met_e + 1 + d * ND;
+                float sv = pv[0] * S[0];
+                #pragma unroll
+                for (int i = 1; i < ND; ++i) sv = fmaf(pv[i], S[i], sv);
+                Ft[d][0] = u[0] * sv;
+                #pragma unroll
+                for (int i = 0; i < ND; ++i) Ft[d][1 + i] = fmaf(u[1 + i], sv, pp * S[i]);
+                Ft[d][V - 1] = (u[V - 1] + pp) * sv;
+            }
+        }
+        const float inv = epi ? -met[(size_t)ee * B.nmp] : 0.f;   // -1 / det J of the epilogue's element
+        if (!mbar_wait(&bar[1], ph_mma)) {       // phase 1 MMAs have read A
+            *err = 2;
+            mbar_wait(&bar[1], ph_mma);
+        }
+        ph_mma ^= 1u;
+        tc_fence_after();
+        if (worker) {
+            #pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float4 hi, lo;
+                float* hp = &hi.x;
+                float* lp = &lo.x;
+                #pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    hp[d] = to_tf32(Ft[d][v]);
+                    lp[d] = to_tf32(Ft[d][v] - hp[d]);
+                }
+                hp[3] = 0.f;
+                lp[3] = 0.f;
+                const uint32_t o = core_off(v * TE + fe_, 4 * h, KA);
+                *reinterpret_cast<float4*>(Ah + o) = hi;
+                *reinterpret_cast<float4*>(Al + o) = lo;
+            }
+        }
+        fence_proxy_async();     // A stores before the MMAs; record reads before the next tile's copies
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            #pragma unroll
+            for (int kk = 0; kk < KA / 8; ++kk) {
+                const uint32_t ko = (uint32_t)kk * 2 * LBO;
+                const uint32_t kob = (uint32_t)(KA / 8 + kk) * 2 * LBO;
+                const uint64_t dah = smem_desc(Ah + ko, LBO, SBO_A), dal = smem_desc(Al + ko, LBO, SBO_A);
+                const uint64_t dbh = smem_desc(Bh + kob, LBO, SBO_B), dbl = smem_desc(Bl + kob, LBO, SBO_B);
+                mma_tf32(tmem, dah, dbh, IDESC, 1u);
+                mma_tf32(tmem, dah, dbl, IDESC, 1u);
+                mma_tf32(tmem, dal, dbh, IDESC, 1u);
+            }
+            mma_commit(&bar[1]);
+        }
+        // The records of this tile are consumed: the next tile's copies overlap
+        // the MMAs and the epilogue.
+        if (tile + (int)gridDim.x < ntiles) issue_loads(tile + gridDim.x);
+        if (!mbar_wait(&bar[1], ph_mma)) {
+            *err = 2;
+            mbar_wait(&bar[1], ph_mma);
+        }
+        ph_mma ^= 1u;
+        tc_fence_after();
+        // Epilogue: rows r0 .. r0+9 of TMEM lane lrow (warp-collective loads).
+        {
+            float x[32];
+            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            tmem_ld16(ta, x);
+            tmem_ld16(ta + 16, x + 16);
+            if (epi) {
+                bool bad = false;
+                #pragma unroll
+                for (int i = 0; i < 10; ++i) {
+                    const size_t idx = ebase + (size_t)(r0 + i) * ers_;
+                    const float r = (r0 == 0 ? x[i] : x[10 + i]) * inv;
+                    bad |= !isfinite(r);
+                    switch (E.mode) {
+                        case EPI_STORE: E.out[idx] = r; break;
+                        case EPI_RK_FIRST:
+                            E.uacc[idx] = fmaf(E.cacc, r, a[i]);
+                            E.unext[idx] = fmaf(E.cnext, r, a[i]);
+                            break;
+                        case EPI_RK_MID:
+                            E.uacc[idx] = fmaf(E.cacc, r, b[i]);
+                            E.unext[idx] = fmaf(E.cnext, r, a[i]);
+                            break;
+                        default: E.out[idx] = fmaf(E.cacc, r, b[i]); break;
+                    }
+                }
+                if (bad) *err = 1;
+            }
+        }
+        tc_fence_before();       // this thread's TMEM loads precede the next tile's MMAs
+        __syncthreads();
+    }
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+bool tc_flux_available(int shape, int nsol, int nvar, int system, int riemann) {
+    return shape == 2 && nsol == 20 && nvar == 5 && system == SYS_EULER && riemann == RIE_RUSANOV;
+}
+
+int launch_flux_tc(const KBlock<float>& B, const float* REC, const float* FIUR, const KPhys<float>& P,
+                   const KEpi<float>& E, int nsm, cudaStream_t st) {
+    if (!(B.nsol == 20 && B.nfe == 40 && B.nfiu == 10 && B.nfaces == 4)) return -1;
+    auto k = k_flux_tc<20, 40, 10>;
+    constexpr int TE = 24;
+    const size_t smem = 2 * (size_t)32 * 80 * 4 + 2 * (size_t)128 * 40 * 4 +
+                        (size_t)TE * (2 * B.ers + B.frs + B.nmp) * 4 + (size_t)TE * B.pstride + 2 * 40 * 4 + 2 * 8 + 16;
+    if (smem > 227 * 1024) return -1;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int need = (B.nelem + TE - 1) / TE;
+    const int grid = need < 2 * nsm ? need : 2 * nsm;
+    k<<<grid, 256, smem, st>>>(B, REC, FIUR, P, E);
+    return 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -77,6 +77,13 @@ bool tc_interp_available(int shape, int nsol, int nvar);
 int launch_interp_tc(const KBlock<float>& B, int V, const float* U, float* REC, float* FIUR, int* err, int nsm,
                      cudaStream_t st);
 
+// Fluxes on the CUDA cores and divergence on the tensor cores (tcgen05,
+// 3xTF32) from the records, for FP32 Euler / Rusanov on tetrahedra of degree 3
+// (kernels_tc.cu).  Returns -1 if the block is not of that kind.
+bool tc_flux_available(int shape, int nsol, int nvar, int system, int riemann);
+int launch_flux_tc(const KBlock<float>& B, const float* REC, const float* FIUR, const KPhys<float>& P,
+                   const KEpi<float>& E, int nsm, cudaStream_t st);
+
 // Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,

@@ -261,6 +261,7 @@ def sdrt_launch_count(ctx):
 
 
 SDRT_OPT_TENSOR_CORES = 0
+SDRT_OPT_TC_DIVERGENCE = 1
 
 
 def sdrt_set_option(ctx, option, value):

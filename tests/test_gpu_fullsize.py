@@ -1,5 +1,5 @@
 """Parity at the benchmark's size and launch configuration, and agreement of the
-tensor-core (tcgen05, 3xTF32) and CUDA-core interpolation paths.
+tensor-core (tcgen05, 3xTF32) and CUDA-core interpolation and divergence paths.
 
 The full-size case is the benchmark workload: Euler on the periodic cube
 [-5, 5]^3 split into 24^3 x 6 = 82,944 tetrahedra of degree 3, isentropic
@@ -41,22 +41,55 @@ def _residual(M, U_blocks):
     return M.unpack(R.cpu().numpy())
 
 
-@pytest.mark.parametrize("use_tc", [1, 0])
-def test_tensor_core_and_fma_interpolation(ctx, use_tc):
+def _options(ctx, interp_tc, div_tc):
     from paper_2105_08632_gb300 import sdrt
-    sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TENSOR_CORES, use_tc)
+    sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TENSOR_CORES, interp_tc)
+    sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TC_DIVERGENCE, div_tc)
+
+
+@pytest.mark.parametrize("interp_tc,div_tc", [(1, 0), (0, 0), (0, 1), (1, 1)])
+def test_tensor_core_and_fma_paths(ctx, interp_tc, div_tc):
+    _options(ctx, interp_tc, div_tc)
     try:
-        # 5 x 5 x 5 x 6 = 750 tets: 5 tensor-core tiles of 128, the last one ragged
+        # 5 x 5 x 5 x 6 = 750 tets: 6 interpolation tiles of 128 and 32
+        # divergence tiles of 24, the last ones ragged
         M, geom, oph, _ = gu.build_pair(ctx, "tet", (5, 5, 5), 3, "euler", "rusanov", "fp32")
         U = gu.perturb(gu.oracle_state(geom, gu.smooth_gas, 5), 31, 0.02)
         linf, l2 = gu.rel_errors(_residual(M, U), ores.residual(geom, oph, U))
-        assert linf < TOL32[0] and l2 < TOL32[1], (use_tc, linf, l2)
+        assert linf < TOL32[0] and l2 < TOL32[1], (interp_tc, div_tc, linf, l2)
     finally:
-        sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TENSOR_CORES, 1)
+        _options(ctx, 0, 0)
 
 
-def test_full_size_benchmark_workload(ctx):
+@pytest.mark.parametrize("div_tc", [1, 0])
+def test_rk4_stages_on_tensor_core_divergence(ctx, div_tc):
+    """Every epilogue mode (RK stages 1..4) of the tensor-core divergence
+    against the FMA kernel over three RK4 steps on 4 x 4 x 3 x 6 tets."""
     from paper_2105_08632_gb300 import sdrt
+    M, geom, oph, _ = gu.build_pair(ctx, "tet", (4, 4, 3), 3, "euler", "rusanov", "fp32")
+    U = gu.perturb(gu.oracle_state(geom, gu.smooth_gas, 5), 32, 0.01)
+    dt = 2e-3
+    want = U
+    for _ in range(3):
+        want = ores.rk4_step(geom, oph, want, dt)
+    _options(ctx, 0, div_tc)
+    try:
+        Ud = torch.from_numpy(M.pack(U)).to("cuda")
+        M.rk4_step(Ud, dt, 3)
+        M.sync()
+        got = M.unpack(Ud.cpu().numpy())
+    finally:
+        _options(ctx, 0, 0)
+    d_got = [g - u for g, u in zip(got, U)]
+    d_want = [w - u for w, u in zip(want, U)]
+    linf, _ = gu.rel_errors(d_got, d_want)
+    assert linf < 5e-3, (div_tc, linf)
+
+
+@pytest.mark.parametrize("div_tc", [1, 0])
+def test_full_size_benchmark_workload(ctx, div_tc):
+    from paper_2105_08632_gb300 import sdrt
+    _options(ctx, 0, div_tc)
     mesh = meshes.box_mesh("tet", (24, 24, 24), [-5.0] * 3, [5.0] * 3)
     M = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
     geom = omesh.build(mesh, 3)
@@ -66,7 +99,10 @@ def test_full_size_benchmark_workload(ctx):
     u = u * (1 + fields.uniform_noise(u.shape, 20210518, 1e-3))
     U = [np.ascontiguousarray(u.reshape(g.nelem, g.ops.n_sol, 5).transpose(1, 2, 0))]
     want, scale = ores.residual(geom, ophx.Physics("euler", 3, "rusanov", gamma=1.4), U, terms=True)
-    got = _residual(M, U)
+    try:
+        got = _residual(M, U)
+    finally:
+        _options(ctx, 0, 0)
     linf, l2 = gu.rel_errors(got, want)
     # The vortex is close to a free stream: dU/dt is a small difference of large
     # flux terms, so the FP32 error is bounded elementwise by the forward-error
