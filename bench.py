@@ -1,16 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the SDRT residual on GB300: DOF-updates/s of classical RK4 steps.
 
-Workload (default): compressible Euler (5 variables, gamma = 1.4) on the
-periodic cube [-5, 5]^3 split into 24^3 x 6 = 82,944 tetrahedra, SDRT degree
-p = 3 (20 solution points per element), Rusanov common flux, isentropic vortex
-(Ma 0.5, S = 13.5, R = 1.5) times (1 + 1e-3 U(-1, 1)) with NumPy PCG64 seed
-20210518, RK4 with dt = 1e-3.  One step = one RK4 step = 4 residual
-evaluations, each fused with its stage update.  DOF-updates/s =
-nsol * nvar * nelem * 4 / step time (paper App. C's PM metric inverted).
+Workloads (all periodic, synthetic, seeded; one step = one RK4 step = 4
+residual evaluations, each fused with its stage update; DOF-updates/s =
+sum over blocks of nsol * nvar * nelem * 4 / step time, the inverse of the
+paper's App. C PM metric):
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
-  python bench.py --impl reference      # the FP64 CPU oracle on the same workload
+  euler (default)  compressible Euler (5 variables, gamma = 1.4) on [-5, 5]^3
+                   split into 24^3 x 6 = 82,944 tetrahedra, degree 3, Rusanov,
+                   isentropic vortex (Ma 0.5, S = 13.5, R = 1.5) times
+                   (1 + 1e-3 U(-1, 1)), NumPy PCG64 seed 20210518, dt = 1e-3
+  tgv              Navier-Stokes Taylor-Green vortex (Re 1600, Ma 0.1,
+                   Pr 0.71, LDG beta = 0.5, eta = 0.1) on [0, 2 pi]^3 split into
+                   48^3 x 6 = 663,552 tetrahedra of degree 4, dt = 2e-4
+  mixed            four independent Euler meshes batched into one (degrees
+                   1..4; hexahedra / x-extruded prisms and tetrahedra /
+                   z-extruded prisms in seeded slab orders), the same vortex
+                   with one seed per mesh, dt = 1e-3
+
+  python bench.py [--workload W] [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
 
 Multi-GPU (torchrun): every rank steps its own replica of the workload
 (independent problems, no data-path collective); value = all ranks' DOF
@@ -40,16 +49,17 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="sdrt", choices=["sdrt", "reference"])
+    ap.add_argument("--workload", default="euler", choices=["euler", "tgv", "mixed"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU path and the accuracy check")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--accuracy-steps", type=int, default=20)
-    ap.add_argument("--ncell", type=int, default=NCELL, help="cubes per axis (profiling of smaller cases)")
+    ap.add_argument("--ncell", type=int, default=None, help="size parameter (profiling of smaller cases)")
     ap.add_argument("--tc-div", type=int, default=0, choices=[0, 1],
                     help="divergence on the tensor cores (SDRT_OPT_TC_DIVERGENCE)")
     ap.add_argument("--tc-interp", type=int, default=0, choices=[0, 1],
@@ -68,6 +78,99 @@ def initial_field(X, seed):
     return u * (1 + fields.uniform_noise(u.shape, seed, 1e-3))
 
 
+# Batched mixed meshes: (structure, degree, cubes per slab side, slab kinds).
+# Slab counts give element counts of ~300k, 120k, 50k and 20k at full size.
+MIXED_PARTS = [("hex", 1, 40, 100, 44), ("tet", 2, 32, 16, 10), ("hex", 3, 24, 45, 21), ("tet", 4, 16, 11, 6)]
+
+
+def workload_label(name, ncell=None):
+    """The label Workload(name, ncell).label has, without building the mesh."""
+    if name == "euler":
+        n = ncell or NCELL
+        return f"euler3d_tet_p3_{6 * n ** 3}_rk4"
+    if name == "tgv":
+        n = ncell or 48
+        return f"tgv_ns_tet_p4_{6 * n ** 3}_rk4"
+    f = ncell / 40.0 if ncell else 1.0
+    per = {"hex": 1, "pri_x": 2, "tet": 6, "pri": 2}
+    total = 0
+    for kind, p, nc, n1, n2 in MIXED_PARTS:
+        m = max(12, int(round(nc * f)))
+        a, b_ = max(1, int(round(n1 * f))), max(1, int(round(n2 * f)))
+        total += m * m * (a * per[kind] + b_ * per["pri_x" if kind == "hex" else "pri"])
+    return f"mixed_euler_hex_pri_tet_p1-4_{total}_rk4"
+
+
+class Workload:
+    """Mesh, degrees, physics and initial state of one benchmark workload.
+    scale < 1 shrinks the mesh (bounded oracle samples)."""
+
+    def __init__(self, name, ncell=None, rank=0, scale=1.0):
+        from inputs import fields, meshes
+        self.name = name
+        self.nd = 3
+        self.block_mesh = None
+        if name == "euler":
+            n = ncell or NCELL
+            if scale != 1.0:
+                n = max(2, int(round(n * scale)))
+            self.mesh = workload_mesh(n)
+            self.degrees = [3] * len(self.mesh["blocks"])
+            self.system, self.riemann, self.kw, self.dt = "euler", "rusanov", {"gamma": 1.4}, DT
+            self._init = lambda b, X: initial_field(X, SEED + rank)
+        elif name == "tgv":
+            n = ncell or 48
+            if scale != 1.0:
+                n = max(2, int(round(n * scale)))
+            self.mesh = meshes.box_mesh("tet", (n,) * 3, [0.0] * 3, [2 * np.pi] * 3)
+            self.degrees = [4] * len(self.mesh["blocks"])
+            self.system, self.riemann, self.dt = "ns", "rusanov", 2e-4
+            self.kw = {"gamma": 1.4, "mu": 1.0 / 1600.0, "prandtl": 0.71, "beta": 0.5, "eta": 0.1}
+            self._init = lambda b, X: fields.taylor_green(X, gamma=1.4, mach=0.1)
+        elif name == "mixed":
+            f = (ncell / 40.0 if ncell else 1.0) * scale
+            parts, self.degrees, self.block_mesh = [], [], []
+            for k, (kind, p, nc, n1, n2) in enumerate(MIXED_PARTS):
+                m = max(12, int(round(nc * f)))    # coarser cross-sections under-resolve the vortex core
+                a, b_ = max(1, int(round(n1 * f))), max(1, int(round(n2 * f)))
+                slabs = (["hex"] * a + ["pri_x"] * b_) if kind == "hex" else (["tet"] * a + ["pri"] * b_)
+                order = np.random.default_rng(SEED + k).permutation(len(slabs))
+                mk = meshes.box_mesh([slabs[i] for i in order], (m, m, len(slabs)), [-5.0] * 3, [5.0] * 3)
+                parts.append(mk)
+                self.degrees += [p] * len(mk["blocks"])
+                self.block_mesh += [k] * len(mk["blocks"])
+            self.mesh = meshes.merge_meshes(parts)
+            self.system, self.riemann, self.kw, self.dt = "euler", "rusanov", {"gamma": 1.4}, DT
+            self._init = lambda b, X: initial_field(X, SEED + 1000 * self.block_mesh[b] + rank)
+        else:
+            raise ValueError(name)
+        self.nelem = sum(len(b["verts"]) for b in self.mesh["blocks"])
+        self.nvar = 1 if self.system in ("advection", "advdiff") else self.nd + 2
+        shapes = sorted({b["shape"] for b in self.mesh["blocks"]})
+        tag = {"euler": f"euler3d_tet_p3_{self.nelem}_rk4", "tgv": f"tgv_ns_tet_p4_{self.nelem}_rk4",
+               "mixed": f"mixed_euler_{'_'.join(shapes)}_p1-4_{self.nelem}_rk4"}[name]
+        self.label = tag
+
+    def physics(self, sdrt, precision):
+        return sdrt.make_physics(self.system, self.nd, self.riemann, precision, **self.kw)
+
+    def state(self, sol_points):
+        """Initial state per block, (N_s, V, E), from the solution points (E, N_s, ND)."""
+        out = []
+        for b, X in enumerate(sol_points):
+            E, ns = X.shape[0], X.shape[1]
+            u = self._init(b, X.reshape(-1, X.shape[-1])).reshape(E, ns, self.nvar)
+            out.append(np.ascontiguousarray(u.transpose(1, 2, 0)))
+        return out
+
+    def composition(self):
+        c = {}
+        for b, p in zip(self.mesh["blocks"], self.degrees):
+            key = f"{b['shape']}_p{p}"
+            c[key] = c.get(key, 0) + len(b["verts"])
+        return c
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -77,28 +180,47 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def algorithmic_bytes(nsol, nfe, nfiu, nvar, nfaces, nd, s, nelem):
-    """Algorithmic bytes per launch of the two kernels of one RK4 stage
-    (padding of the records excluded).
+def record_path(infos, system, riemann):
+    """Whether every block runs on the register-blocked record path
+    (tetrahedra of degree 3 or 4, Euler / Rusanov or advection)."""
+    ok_sys = system == "advection" or (system == "euler" and riemann == "rusanov")
+    return ok_sys and all(i["ndim"] == 3 and i["nfaces"] == 4 and i["nsol"] in (20, 35) for i in infos)
 
-    k_interp_rec : read U (nsol V s); write the external-point states (nfe V s)
-                   and the internal-point states (nfiu V s)
-    k_flux_rec   : read own and partner external-point states (2 nfe V s), the
-                   internal-point states (nfiu V s), the metric
-                   ((1 + nd^2 + nfaces (nd+1)) s), the partner permutation
-                   (nfe B) and partner face offsets (nfaces * 4 B); stage update
-                   averaged over the 4 RK4 stages in state volumes (nsol V s):
-                   stage 1 read u0 + 2 writes = 3, stages 2-3 2 reads + 2 writes
-                   = 4, stage 4 read + write = 2 -> 13 / 4 = 3.25
+
+def algorithmic_bytes(info, nelem, nvar, s, record, viscous):
+    """Algorithmic bytes of one RK4 stage per kernel kind for one block
+    (padding excluded; the stage update is averaged over the 4 stages in
+    state volumes N_s V s: stage 1 reads u0 and writes two arrays = 3, stages
+    2-3 read two and write two = 4, stage 4 reads one and writes one = 2 ->
+    13 / 4 = 3.25).
+
+    record path   k_interp_rec : read U, write external + internal point states
+                  k_flux_rec   : own + partner external states, internal states,
+                                 metric, permutation, partner offsets, stage update
+    generic path  k_interp_ext : read U, write external point states
+                  k_grad       : read U, own + partner external states, write the
+                                 physical gradients at all flux points (viscous)
+                  k_residual   : read U, partner external states (+ own and
+                                 partner gradients, internal gradients), metric,
+                                 face map, stage update
     """
-    interp = (nsol + nfe + nfiu) * nvar * s
-    metric = (1 + nd * nd + nfaces * (nd + 1)) * s
-    resid = (2 * nfe + nfiu) * nvar * s + metric + nfe + 4 * nfaces + 3.25 * nsol * nvar * s
-    return interp * nelem, resid * nelem
+    ns, nfe, nfiu, nf, nd = info["nsol"], info["nfe"], info["nfiu"], info["nfaces"], info["ndim"]
+    V = nvar
+    metric = (1 + nd * nd + nf * (nd + 1)) * s
+    upd = 3.25 * ns * V * s
+    if record:
+        return {"interp_ext": (ns + nfe + nfiu) * V * s * nelem,
+                "residual": ((2 * nfe + nfiu) * V * s + metric + nfe + 4 * nf + upd) * nelem}
+    out = {"interp_ext": (ns + nfe) * V * s * nelem,
+           "residual": ((ns + nfe) * V * s + metric + 4 * nfe + upd) * nelem}
+    if viscous:
+        out["residual"] += (2 * nd * nfe + nd * nfiu) * V * s * nelem
+        out["gradient"] = ((ns + 2 * nfe) * V * s + nd * (nfe + nfiu) * V * s + metric + 4 * nfe) * nelem
+    return out
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -110,7 +232,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -169,65 +291,79 @@ def ncu_traffic():
         return None
 
 
-def cpu_baseline(ncell=16):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    the same element type, degree, physics and initial field on a periodic
-    ncell^3 x 6 tetrahedron box, one RK4 step (4 residual evaluations)."""
+def cpu_baseline(spec_small, steps=1):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (the
+    same element types, degrees, physics and initial field on a smaller mesh):
+    `steps` RK4 steps (4 residual evaluations each), single-threaded NumPy."""
     from oracle import mesh as omesh
     from oracle import physics as ophx
     from oracle import residual as ores
-    mesh = workload_mesh(ncell)
-    geom = omesh.build(mesh, 3)
-    phys = ophx.Physics("euler", 3, "rusanov", gamma=1.4)
-    U = []
-    for g in geom.blocks:
-        X = g.xsol.reshape(-1, 3)
-        v = initial_field(X, SEED).reshape(g.nelem, g.ops.n_sol, 5)
-        U.append(np.ascontiguousarray(np.transpose(v, (1, 2, 0))))
+    geom = omesh.build(spec_small.mesh, list(spec_small.degrees))
+    kw = dict(spec_small.kw)
+    oph = ophx.Physics(spec_small.system, spec_small.nd, spec_small.riemann, gamma=kw.get("gamma", 1.4),
+                       mu=kw.get("mu", 0.0), Pr=kw.get("prandtl", 0.72), beta=kw.get("beta", 0.5),
+                       eta=kw.get("eta", 0.1))
+    U = spec_small.state([g.xsol for g in geom.blocks])
     t0 = time.perf_counter()
-    ores.rk4_step(geom, phys, U, DT)
+    for _ in range(steps):
+        U = ores.rk4_step(geom, oph, U, spec_small.dt)
     t = time.perf_counter() - t0
-    ndof = sum(g.ops.n_sol * 5 * g.nelem for g in geom.blocks)
-    return {"value": ndof * 4 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one RK4 step (4 residuals) of the same tet p=3 Euler workload on a {ncell}^3 x 6 = "
-                      f"{6 * ncell ** 3}-element periodic box; NumPy FP64, single-threaded einsum; "
-                      f"{t:.2f} s; host affinity {len(os.sched_getaffinity(0))} cores"}
+    ndof = sum(g.ops.n_sol * spec_small.nvar * g.nelem for g in geom.blocks)
+    return {"value": ndof * 4 * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK4 step(s) (4 residuals each) of the same workload on {spec_small.label} "
+                      f"({spec_small.nelem} elements); NumPy FP64, single-threaded einsum; {t:.2f} s; "
+                      f"host affinity {len(os.sched_getaffinity(0))} cores"}
+
+
+CPU_SCALE = {"euler": 16 / 24, "tgv": 10 / 48, "mixed": 0.35}
+REF_SCALE = {"euler": 5 / 24, "tgv": 3 / 48, "mixed": 0.02}
+REF_BUDGET_S = 150.0
 
 
 def run_reference(args):
+    """The oracle as the reference arm: one RK4 step of a bounded sample of the
+    workload per bench step, warm-up steps untimed; to keep the run within a
+    few minutes for any --steps, timing stops after REF_BUDGET_S seconds and
+    the mean is taken over the steps timed so far."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    small = Workload(args.workload, args.ncell, 0, REF_SCALE[args.workload])
     steps = []
+    t_start = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(ncell=4)
+        cb = cpu_baseline(small)
         if i >= args.warmup:
             steps.append(cb["value"])
+        if steps and time.perf_counter() - t_start > REF_BUDGET_S:
+            break
     v = float(np.mean(steps))
+    label = WORKLOAD if (args.workload == "euler" and not args.ncell) else workload_label(args.workload, args.ncell)
+    sample = (f"{small.label} ({small.nelem} elements), one RK4 step per bench step; {len(steps)} of "
+              f"{args.steps} steps timed within the {REF_BUDGET_S:.0f} s budget; 1 core")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "4^3 x 6 = 384 tetrahedra per step (bounded CPU sample)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one RK4 step on a 4^3 x 6 tetrahedron periodic box per bench step"},
+            "config": {"workload": label, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def fp64_leg(sdrt, ctx, mesh, stream, flush, U0, ndof, args):
+def fp64_leg(sdrt, ctx, spec, stream, flush, U0, ndof, args):
     """The plain FP64 GPU path on the same workload (timed like the main arm,
     fewer steps) and the accuracy of the FP32 path against it: one residual,
     and the state after a few RK4 steps (relative L2 / L-inf over all values;
     'update' errors are relative to the FP64 change of the state)."""
     import torch
-    M32 = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
-    M64 = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp64", gamma=1.4))
+    M32 = sdrt.Mesh(ctx, spec.mesh, list(spec.degrees), spec.physics(sdrt, "fp32"))
+    M64 = sdrt.Mesh(ctx, spec.mesh, list(spec.degrees), spec.physics(sdrt, "fp64"))
     dev = flush.device
-    h64 = M64.pack([U0])
+    h64 = M64.pack(U0)
     U64 = torch.from_numpy(h64).to(dev)
     for i in range(3):
         flush.fill_(float(i))
-        M64.rk4_step(U64, DT, 1)
+        M64.rk4_step(U64, spec.dt, 1)
     M64.sync()
     ms = []
     for i in range(args.fp64_steps):
@@ -235,7 +371,7 @@ def fp64_leg(sdrt, ctx, mesh, stream, flush, U0, ndof, args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        M64.rk4_step(U64, DT, 1)
+        M64.rk4_step(U64, spec.dt, 1)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -243,20 +379,20 @@ def fp64_leg(sdrt, ctx, mesh, stream, flush, U0, ndof, args):
     ms64 = float(np.mean(ms))
     fp64 = {"value": ndof * 4 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
             "dtype": "f64"}
-    # accuracy of the FP32 path against the FP64 path
     a64 = torch.from_numpy(h64).to(dev)
-    a32 = torch.from_numpy(M32.pack([U0])).to(dev)
+    a32 = torch.from_numpy(M32.pack(U0)).to(dev)
     r64 = torch.zeros_like(a64)
     r32 = torch.zeros_like(a32)
     M64.residual(a64, r64)
     M32.residual(a32, r32)
-    M64.rk4_step(a64, DT, args.accuracy_steps)
-    M32.rk4_step(a32, DT, args.accuracy_steps)
+    M64.rk4_step(a64, spec.dt, args.accuracy_steps)
+    M32.rk4_step(a32, spec.dt, args.accuracy_steps)
     M32.sync()
     M64.sync()
-    R64, R32 = M64.unpack(r64.cpu().numpy())[0], M32.unpack(r32.cpu().numpy())[0].astype(np.float64)
-    S64, S32 = M64.unpack(a64.cpu().numpy())[0], M32.unpack(a32.cpu().numpy())[0].astype(np.float64)
-    dR, dS, dU = R32 - R64, S32 - S64, S64 - U0
+    cat = lambda blocks: np.concatenate([b.astype(np.float64).ravel() for b in blocks])   # noqa: E731
+    R64, R32 = cat(M64.unpack(r64.cpu().numpy())), cat(M32.unpack(r32.cpu().numpy()))
+    S64, S32 = cat(M64.unpack(a64.cpu().numpy())), cat(M32.unpack(a32.cpu().numpy()))
+    dR, dS, dU = R32 - R64, S32 - S64, S64 - cat(U0)
 
     def rel(a, b):
         return {"rel_l2": float(np.linalg.norm(a) / np.linalg.norm(b)),
@@ -284,6 +420,10 @@ def aggregate(total_ms, steps, ndof, dist=None, device="cpu"):
     return total_ms, ms_per_step, world * ndof * 4 / (ms_per_step / 1e3)
 
 
+KERNEL_NAMES = {True: {"interp_ext": "k_interp_rec", "residual": "k_flux_rec"},
+                False: {"interp_ext": "k_interp_ext", "residual": "k_residual", "gradient": "k_grad"}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -308,22 +448,18 @@ def main():
     ctx = sdrt.Context(local, stream.cuda_stream)
     sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TC_DIVERGENCE, args.tc_div)
     sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_TENSOR_CORES, args.tc_interp)
-    mesh = workload_mesh(args.ncell)
-    phys = sdrt.make_physics("euler", 3, "rusanov", args.precision, gamma=1.4)
-    M = sdrt.Mesh(ctx, mesh, 3, phys)
-    lay = M.layouts[0]
-    nelem, nsol, nvar = lay["nelem"], lay["nsol"], lay["nvar"]
+    spec = Workload(args.workload, args.ncell, rank)
+    M = sdrt.Mesh(ctx, spec.mesh, list(spec.degrees), spec.physics(sdrt, args.precision))
     ndof = M.info["ndof"]
-    X = M.sol_points()[0].reshape(-1, 3)
-    U0 = initial_field(X, SEED + rank).reshape(nelem, nsol, nvar).transpose(1, 2, 0)
-    host = M.pack([U0])
-    tdtype = torch.float32 if args.precision == "fp32" else torch.float64
+    U0 = spec.state(M.sol_points())
+    host = M.pack(U0)
     U = torch.from_numpy(host).to(f"cuda:{local}")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    dt = spec.dt
 
     for i in range(args.warmup):
         flush.fill_(float(i))
-        M.rk4_step(U, DT, 1)
+        M.rk4_step(U, dt, 1)
     M.sync()
     sdrt.sdrt_profile_enable(ctx.ptr, True)
     sampler = ClockSampler(local)
@@ -339,7 +475,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        M.rk4_step(U, DT, 1)
+        M.rk4_step(U, dt, 1)
         e1.record(stream)
         for k, (ms, n) in sdrt.sdrt_profile_collect(ctx.ptr).items():   # synchronises
             prof[k][0] += ms
@@ -352,28 +488,43 @@ def main():
     M.sync()
     total_ms, ms_per_step, value = aggregate(float(np.sum(step_ms)), args.steps, ndof, dist, f"cuda:{local}")
 
-    # Roofline of the dominant kernel (the residual / divergence kernel).
+    # Roofline of the dominant kernel kind (live CUDA-event durations inside the
+    # timed region against its algorithmic bytes).
     s = 4 if args.precision == "fp32" else 8
-    info = sdrt.sdrt_get_etype_info(ctx.ptr, M.etypes[0])
-    b_interp, b_resid = algorithmic_bytes(nsol, info["nfe"], info["nfiu"], nvar, info["nfaces"], 3, s, nelem)
-    ms_r, n_r = prof["residual"]
-    ms_i, n_i = prof["interp_ext"]
-    avg_r = ms_r / max(n_r, 1)
-    avg_i = ms_i / max(n_i, 1)
+    infos = [sdrt.sdrt_get_etype_info(ctx.ptr, et) for et in M.etypes]
+    rec = record_path(infos, spec.system, spec.riemann)
+    viscous = spec.system in ("advdiff", "ns")
+    names = dict(KERNEL_NAMES[rec])
+    if rec and args.tc_div and args.precision == "fp32":
+        names["residual"] = "k_flux_tc"
+    if rec and args.tc_interp and args.precision == "fp32":
+        names["interp_ext"] = "k_interp_tc"
+    per_stage = {}
+    for info, lay in zip(infos, M.layouts):
+        for k, b in algorithmic_bytes(info, lay["nelem"], spec.nvar, s, rec, viscous).items():
+            per_stage[k] = per_stage.get(k, 0.0) + b
     peak, peak_kind = peaks()
-    achieved = b_resid / (avg_r / 1e3) / 1e9 if n_r else None
-    traffic = ncu_traffic()
-    roofline = {"bound": "hbm", "kernel": "k_flux_rec", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    stages = 4 * args.steps
+    kinds = {}
+    for k, b in per_stage.items():
+        ms_k, n_k = prof[k]
+        kinds[names[k]] = {"algorithmic_bytes_per_stage": b, "launches": n_k, "total_ms": ms_k,
+                           "avg_launch_ms": ms_k / max(n_k, 1),
+                           "achieved_gbs": b * stages / (ms_k / 1e3) / 1e9 if n_k else None,
+                           "step_share": ms_k / max(total_ms, 1e-9) if not dist else None}
+    dom = max(per_stage, key=lambda k: prof[k][0])
+    dk = kinds[names[dom]]
+    achieved = dk["achieved_gbs"]
+    traffic = ncu_traffic() if (args.workload == "euler" and not args.ncell and rec and not args.tc_div) else None
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                                 else "of fallback"),
-                "algorithmic_bytes_per_launch": b_resid, "avg_launch_ms": avg_r,
+                "algorithmic_bytes_per_launch": dk["algorithmic_bytes_per_stage"] / max(len(M.layouts), 1),
+                "avg_launch_ms": dk["avg_launch_ms"],
                 "kernel_sources_sha256_16": kernel_sources_sha(),
-                "k_interp_rec": {"algorithmic_bytes_per_launch": b_interp, "avg_launch_ms": avg_i,
-                                 "achieved_gbs": b_interp / (avg_i / 1e3) / 1e9 if n_i else None},
-                "step_share": {"k_flux_rec": ms_r / max(total_ms, 1e-9) if not dist else None,
-                               "k_interp_rec": ms_i / max(total_ms, 1e-9) if not dist else None},
-                "step_hbm_frac": ((b_resid + b_interp) * 4 / (ms_per_step / 1e3) / 1e9) / peak}
+                "kernels": kinds,
+                "step_hbm_frac": (sum(per_stage.values()) * 4 / (ms_per_step / 1e3) / 1e9) / peak}
 
     # End to end through the host-buffer entry point (pinned memory).
     pin_in = torch.from_numpy(host).pin_memory()
@@ -381,7 +532,7 @@ def main():
     e2e_t = []
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         t0 = time.perf_counter()
-        M.rk4_step_host(pin_in, pin_out, DT, 1)
+        M.rk4_step_host(pin_in, pin_out, dt, 1)
         t1 = time.perf_counter()
         if i > 0:
             e2e_t.append(t1 - t0)
@@ -393,20 +544,22 @@ def main():
 
     fp64, accuracy = None, None
     if rank == 0 and args.precision == "fp32" and not args.no_fp64:
-        fp64, accuracy = fp64_leg(sdrt, ctx, mesh, stream, flush, U0, ndof, args)
+        fp64, accuracy = fp64_leg(sdrt, ctx, spec, stream, flush, U0, ndof, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(Workload(args.workload, args.ncell, 0, CPU_SCALE[args.workload]))
 
     if rank == 0:
-        workload = WORKLOAD if args.ncell == NCELL else f"euler3d_tet_p3_{6 * args.ncell ** 3}_rk4"
+        workload = WORKLOAD if (args.workload == "euler" and not args.ncell) else spec.label
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-                "config": {"workload": workload, "elements": nelem, "tc_divergence": args.tc_div,
-                           "tc_interpolation": args.tc_interp, "degree": 3, "nsol": nsol, "nvar": nvar,
-                           "ndof": ndof, "residuals_per_step": 4, "precision": args.precision,
+                "config": {"workload": workload, "elements": spec.nelem, "composition": spec.composition(),
+                           "system": spec.system, "riemann": spec.riemann, "nvar": spec.nvar, "ndof": ndof,
+                           "dt": dt, "residuals_per_step": 4, "precision": args.precision,
+                           "path": "record" if rec else "generic",
+                           "tc_divergence": args.tc_div, "tc_interpolation": args.tc_interp,
                            "l2": "flushed between timed steps (256 MiB write, untimed)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

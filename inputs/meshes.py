@@ -152,3 +152,19 @@ def box_mesh(kinds, n, lo, hi):
 
 def n_elements(mesh):
     return sum(len(b["verts"]) for b in mesh["blocks"])
+
+
+def merge_meshes(parts):
+    """Disconnected union of meshes (independent problems batched into one):
+    blocks concatenated, face block indices offset, shifts kept."""
+    blocks, faces, shifts = [], [], []
+    nb = 0
+    for m in parts:
+        blocks.extend(m["blocks"])
+        f = np.array(m["faces"], np.int64).copy()
+        f[:, 0] += nb
+        f[:, 3] += nb
+        faces.append(f)
+        shifts.append(m["shift"])
+        nb += len(m["blocks"])
+    return {"blocks": blocks, "faces": np.concatenate(faces), "shift": np.concatenate(shifts)}

@@ -67,12 +67,18 @@ def affine_map(shape, verts):
 
 
 def build(mesh, degrees):
-    """degrees: dict shape -> p (or one int for every block)."""
+    """degrees: one int for every block, a list with one degree per block, or
+    a dict shape -> p."""
     blocks = []
     nd = mesh["blocks"][0]["verts"].shape[2]
-    for blk in mesh["blocks"]:
+    for i, blk in enumerate(mesh["blocks"]):
         shape = blk["shape"]
-        p = degrees if isinstance(degrees, int) else degrees[shape]
+        if isinstance(degrees, int):
+            p = degrees
+        elif isinstance(degrees, (list, tuple)):
+            p = degrees[i]
+        else:
+            p = degrees[shape]
         ops = operators.get(shape, p)
         C = affine_map(shape, blk["verts"])
         J = np.transpose(C[:, :nd, :], (0, 2, 1))          # J_ij = dx_i / dx~_j

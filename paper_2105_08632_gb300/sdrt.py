@@ -323,8 +323,13 @@ class Mesh:
         c = ctx.ptr
         blocks = []
         self.etypes = []
-        for blk in mesh["blocks"]:
-            p = degree if isinstance(degree, int) else degree[blk["shape"]]
+        for i, blk in enumerate(mesh["blocks"]):
+            if isinstance(degree, int):
+                p = degree
+            elif isinstance(degree, (list, tuple)):
+                p = degree[i]                  # one degree per block
+            else:
+                p = degree[blk["shape"]]       # one degree per element shape
             et = sdrt_setup_element_type(c, blk["shape"], p)
             self.etypes.append(et)
             blocks.append((et, blk["verts"]))
