@@ -26,38 +26,111 @@ namespace {
 
 constexpr int kMR = 8;   // rows of a GEMM micro tile
 
-// C[m][col] = sum_k At[k * ldA + m] * B(k)[col]  for m < M, col < NCOL.
-// B rows k < ksplit live at B0 + k * NCOL, the others at B1 + (k - ksplit) * NCOL.
-// Work items are (row block of kMR rows, chunk of 32 columns); each warp takes
-// items round-robin, each lane one column of the chunk.
-template <typename S, typename T, typename Store>
-__device__ __forceinline__ void tile_gemm(const T* __restrict__ At, int ldA, int M, int K,
-                                          const S* B0, int ksplit, const S* B1, int NCOL, Store store) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int nrb = (M + kMR - 1) / kMR;
-    const int ncc = (NCOL + 31) >> 5;
-    for (int item = warp; item < nrb * ncc; item += nwarps) {
-        const int rb = item / ncc;
-        const int col = (item - rb * ncc) * 32 + lane;
-        const bool colok = col < NCOL;
-        const int c = colok ? col : 0;
-        S acc[kMR];
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// 8 consecutive operator entries (16-byte loads when aligned).
+__device__ __forceinline__ void ld_a8(const float* p, float (&a)[8], bool vec) {
+    if (vec) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 y = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+        a[4] = y.x; a[5] = y.y; a[6] = y.z; a[7] = y.w;
+    } else {
         #pragma unroll
-        for (int i = 0; i < kMR; ++i) acc[i] = szero<S>();
+        for (int i = 0; i < 8; ++i) a[i] = __ldg(p + i);
+    }
+}
+__device__ __forceinline__ void ld_a8(const double* p, double (&a)[8], bool vec) {
+    if (vec) {
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double2 x = __ldg(reinterpret_cast<const double2*>(p) + i);
+            a[2 * i] = x.x;
+            a[2 * i + 1] = x.y;
+        }
+    } else {
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = __ldg(p + i);
+    }
+}
+// CW consecutive values of a shared-memory row (16-byte loads for float / double).
+template <int CW>
+__device__ __forceinline__ void ld_b(const float* p, float (&b)[CW]) {
+    if constexpr (CW == 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        b[0] = x.x; b[1] = x.y; b[2] = x.z; b[3] = x.w;
+    } else {
+        #pragma unroll
+        for (int j = 0; j < CW; ++j) b[j] = p[j];
+    }
+}
+template <int CW>
+__device__ __forceinline__ void ld_b(const double* p, double (&b)[CW]) {
+    if constexpr (CW == 4) {
+        const double2 x = *reinterpret_cast<const double2*>(p);
+        const double2 y = *(reinterpret_cast<const double2*>(p) + 1);
+        b[0] = x.x; b[1] = x.y; b[2] = y.x; b[3] = y.y;
+    } else {
+        #pragma unroll
+        for (int j = 0; j < CW; ++j) b[j] = p[j];
+    }
+}
+template <int CW, typename T>
+__device__ __forceinline__ void ld_b(const Dual<T>* p, Dual<T> (&b)[CW]) {
+    #pragma unroll
+    for (int j = 0; j < CW; ++j) b[j] = p[j];
+}
+
+template <int CW, typename S, typename T, typename Store>
+__device__ __forceinline__ void tile_gemm_cw(const T* __restrict__ At, int ldA, int M, int K, const S* B0, int ksplit,
+                                             const S* B1, int NCOL, Store store) {
+    const int nrb = (M + kMR - 1) / kMR;
+    const int ncw = NCOL / CW;
+    const bool avec = aligned16(At) && ((size_t)ldA * sizeof(T)) % 16 == 0;
+    for (int u = threadIdx.x; u < nrb * ncw; u += blockDim.x) {
+        const int rb = u / ncw;
+        const int col0 = (u - rb * ncw) * CW;
+        S acc[kMR][CW];
+        #pragma unroll
+        for (int i = 0; i < kMR; ++i)
+            #pragma unroll
+            for (int j = 0; j < CW; ++j) acc[i][j] = szero<S>();
         const T* a = At + rb * kMR;
         #pragma unroll 2
         for (int k = 0; k < K; ++k) {
-            const S b = (k < ksplit) ? B0[k * NCOL + c] : B1[(k - ksplit) * NCOL + c];
+            S b[CW];
+            ld_b<CW>((k < ksplit ? B0 + (size_t)k * NCOL : B1 + (size_t)(k - ksplit) * NCOL) + col0, b);
             T av[kMR];
+            ld_a8(a + (size_t)k * ldA, av, avec);
             #pragma unroll
-            for (int i = 0; i < kMR; ++i) av[i] = __ldg(a + (size_t)k * ldA + i);
-            #pragma unroll
-            for (int i = 0; i < kMR; ++i) mac(acc[i], av[i], b);
+            for (int i = 0; i < kMR; ++i)
+                #pragma unroll
+                for (int j = 0; j < CW; ++j) mac(acc[i][j], av[i], b[j]);
         }
-        if (colok) store(rb * kMR, col, acc);       // rows m0 .. m0 + kMR - 1 (those < M)
+        #pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            S c[kMR];
+            #pragma unroll
+            for (int i = 0; i < kMR; ++i) c[i] = acc[i][j];
+            store(rb * kMR, col0 + j, c);          // rows rb * kMR .. + kMR - 1 (those < M)
+        }
     }
+}
+
+// C[m][col] = sum_k At[k * ldA + m] * B(k)[col]  for m < M, col < NCOL.
+// B rows k < ksplit live at B0 + k * NCOL, the others at B1 + (k - ksplit) * NCOL.
+// Work units are (row block of kMR rows, CW consecutive columns), spread over
+// all threads of the block: each unit takes 8 operator entries per k (16-byte
+// loads, cached) and CW values of the B row (one 16-byte shared-memory load),
+// i.e. kMR x CW FMAs per three loads.  CW = 4 when NCOL is a multiple of 4
+// (B rows then start 16-byte aligned), else 1.  Every thread must call it
+// (no barrier inside); rows >= M of the last block read zero-padded operator
+// entries and are dropped by the store functor.
+template <typename S, typename T, typename Store>
+__device__ __forceinline__ void tile_gemm(const T* __restrict__ At, int ldA, int M, int K, const S* B0, int ksplit,
+                                          const S* B1, int NCOL, Store store) {
+    if (NCOL % 4 == 0 && aligned16(B0) && aligned16(B1)) tile_gemm_cw<4>(At, ldA, M, K, B0, ksplit, B1, NCOL, store);
+    else tile_gemm_cw<1>(At, ldA, M, K, B0, ksplit, B1, NCOL, store);
 }
 
 template <typename S, typename T>
