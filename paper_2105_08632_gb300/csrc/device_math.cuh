@@ -57,6 +57,19 @@ template <typename S> __device__ __forceinline__ S szero() { return S(0); }
 template <> __device__ __forceinline__ Dual<float> szero<Dual<float>>() { return {0.f, 0.f}; }
 template <> __device__ __forceinline__ Dual<double> szero<Dual<double>>() { return {0.0, 0.0}; }
 
+// (u_L, u_R) of a face point from its own and its partner's state (own is L
+// when `left`), selected value by value so that a warp whose points have both
+// orientations evaluates the common flux once instead of on two divergent
+// paths.  Both sides of a face still pass the same operands in the same order.
+template <int V, typename S>
+__device__ __forceinline__ void orient(bool left, const S* own, const S* nbr, S* uL, S* uR) {
+    #pragma unroll
+    for (int v = 0; v < V; ++v) {
+        uL[v] = left ? own[v] : nbr[v];
+        uR[v] = left ? nbr[v] : own[v];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Euler: primitive velocity and pressure of u = (rho, rho v, rho E).
 template <typename S, typename T, int ND>

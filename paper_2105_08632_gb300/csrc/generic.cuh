@@ -359,8 +359,11 @@ __global__ void __launch_bounds__(256) k_residual(KBlock<T> B, const T* __restri
             const int fp = __ldg(B.map + (size_t)sg * B.ld + e);
             gather_partner<S, T, V>(UFE, dUFE, Ftot, fp, nbr);
             const bool left = s > T(0);       // this point is on its face's L side
-            if (left) common_flux<SYS, RIE, ND>(own, nbr, n, P, F);
-            else common_flux<SYS, RIE, ND>(nbr, own, n, P, F);
+            {
+                S uL[V], uR[V];
+                orient<V>(left, own, nbr, uL, uR);
+                common_flux<SYS, RIE, ND>(uL, uR, n, P, F);
+            }
             if constexpr (is_viscous<SYS>()) {
                 // LDG flux n.[(1/2 + beta) f_v(u_L, q_L) + (1/2 - beta) f_v(u_R, q_R)] + eta (u_L - u_R).
                 const size_t own_q = (size_t)B.fe_base + (size_t)sg * B.ld + e;

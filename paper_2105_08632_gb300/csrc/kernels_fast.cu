@@ -419,12 +419,12 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
                 uo[v] = uo_p[v];
                 un[v] = un_p[v];
             }
+            T uL[V], uR[V];
+            orient<V>(s > T(0), uo, un, uL, uR);
             if constexpr (SYS == SYS_EULER && RIE == RIE_RUSANOV) {
-                if (s > T(0)) rusanov_rec<T, ND>(uo, un, nrm, P.gamma, s, F);
-                else rusanov_rec<T, ND>(un, uo, nrm, P.gamma, s, F);
+                rusanov_rec<T, ND>(uL, uR, nrm, P.gamma, s, F);
             } else {
-                if (s > T(0)) common_flux_f<SYS, RIE, ND>(uo, un, nrm, P, F);
-                else common_flux_f<SYS, RIE, ND>(un, uo, nrm, P, F);
+                common_flux_f<SYS, RIE, ND>(uL, uR, nrm, P, F);
                 #pragma unroll
                 for (int v = 0; v < V; ++v) F[v] *= s;
             }
@@ -529,8 +529,9 @@ __global__ void __launch_bounds__(32 * V, 4) k_flux_rec_dual(KBlock<T> B, const 
                 uo[v] = {__ldg(REC + oo + v), __ldg(dREC + oo + v)};
                 un[v] = {__ldg(REC + po + v), __ldg(dREC + po + v)};
             }
-            if (s > T(0)) common_flux_f<SYS, RIE, ND>(uo, un, n, P, F);
-            else common_flux_f<SYS, RIE, ND>(un, uo, n, P, F);
+            S uL[V], uR[V];
+            orient<V>(s > T(0), uo, un, uL, uR);
+            common_flux_f<SYS, RIE, ND>(uL, uR, n, P, F);
             #pragma unroll
             for (int v = 0; v < V; ++v) Fs[(size_t)sg * NCOL + v * TE + lane] = s * F[v];
         }

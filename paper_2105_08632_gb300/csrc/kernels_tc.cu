@@ -17,6 +17,7 @@
 // (the same layout as k_interp_rec).
 #include <cstdint>
 
+#include "device_math.cuh"
 #include "flux_rec.cuh"
 #include "kargs.hpp"
 #include "launch.hpp"
@@ -464,8 +465,9 @@ __global__ void __launch_bounds__(256, 2) k_flux_tc(KBlock<float> B, const float
                     uo[v] = uo_p[v];
                     un[v] = un_p[v];
                 }
-                if (s > 0.f) rusanov_rec<float, ND>(uo, un, nrm, P.gamma, s, F[jj]);
-                else rusanov_rec<float, ND>(un, uo, nrm, P.gamma, s, F[jj]);
+                float uL[V], uR[V];
+                orient<V>(s > 0.f, uo, un, uL, uR);
+                rusanov_rec<float, ND>(uL, uR, nrm, P.gamma, s, F[jj]);
             }
             #pragma unroll
             for (int v = 0; v < V; ++v) {

@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(256) k_vjp_elem(KBlock<T> B, const T* __restri
                     uo[v] = {own[v], v == c ? T(1) : T(0)};
                     un[v] = {nbr[v], T(0)};
                 }
-                if (left) common_flux<SYS, RIE, ND>(uo, un, n, P, F);
-                else common_flux<SYS, RIE, ND>(un, uo, n, P, F);
+                D uL[V], uR[V];
+                orient<V>(left, uo, un, uL, uR);
+                common_flux<SYS, RIE, ND>(uL, uR, n, P, F);
                 T a = T(0);
                 #pragma unroll
                 for (int v = 0; v < V; ++v) a = fma(F[v].d, H[v], a);
