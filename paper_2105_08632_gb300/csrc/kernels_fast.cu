@@ -21,6 +21,11 @@
 //                  stage epilogue.
 //   k_flux_rec_dual : the JVP (dual numbers), reading the records directly.
 #include <cstdint>
+#include <mutex>
+#include <type_traits>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "device_math.cuh"
 #include "flux_rec.cuh"
@@ -76,6 +81,23 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// 2D tensor copy (TMA) of one box at (x, y) of the tensor map into shared memory,
+// completing on bar.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Barrier among the first `count` threads of the block (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void consumer_sync(int count) {
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -201,7 +223,7 @@ __global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __r
     constexpr int VG = (V <= VB) ? V : (VB > 0 ? VB : 1);
     using VT = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::n;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T* As = reinterpret_cast<T*>(smem_raw);                                   // [Mir][NSP]
     T* Rs = reinterpret_cast<T*>(smem_raw + align16((size_t)B.Mir * NSP * sizeof(T)));   // [TE][ers]
     T* Fs = Rs + (size_t)TE * B.ers;                                          // [TE][frs]
@@ -282,6 +304,143 @@ __global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __r
 }
 
 // ---------------------------------------------------------------------------
+// Interpolation to the flux points as a producer / consumer pipeline (FP32).
+//
+// Warp NC / 32 (the last one) is the producer: for each of the CTA's tiles it
+// streams the tile's solution values U[rho][v][e0 .. e0+TE) (one bulk copy per
+// (rho, v) row) into a two-stage shared-memory ring, completing on full[s].
+// Consumer thread (e, v, g) copies the NS values of variable v of element e
+// to registers, releases the stage (empty[s]) and computes the rows
+// j = g, g + GR, ... of [u_fe; u_fiu] = [M0; M12] U (Eqs.
+// "interpolation_procedure"), four rows at a time, with every lane of a warp
+// reading the same operator rows from shared memory (broadcast).  The results
+// are assembled into one of two record staging buffers that a single thread
+// writes out with bulk stores while the next tile is computed.  One CTA per
+// SM, persistent.
+template <int NS, int V, int NFE, int NFIU, int TE, int GR>
+__global__ void __launch_bounds__(V * TE * GR + 32, 1) k_interp_pipe(KBlock<float> B,
+                                                                     const __grid_constant__ CUtensorMap umap,
+                                                                     float* __restrict__ REC,
+                                                                     float* __restrict__ FIUR, int* __restrict__ err) {
+    constexpr int NROW = NS * V;                      // rows (rho, v) of a U tile
+    constexpr int MI = NFE + NFIU;
+    constexpr int NSP = (NS + 7) / 8 * 8;             // operator row stride (= B.Md_pad)
+    constexpr int NC = V * TE * GR;                   // consumer threads
+    static_assert(NC % 32 == 0 && TE % 32 == 0, "tile layout");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* As = reinterpret_cast<float*>(smem_raw);                            // [Mir][NSP]
+    size_t off = align16((size_t)B.Mir * NSP * sizeof(float));
+    off = (off + 127) & ~size_t(127);
+    float* Ub = reinterpret_cast<float*>(smem_raw + off);                      // [2][NROW][TE], 128-byte aligned
+    off = align16(off + 2 * (size_t)NROW * TE * sizeof(float));
+    const size_t st_elems = (size_t)TE * (B.ers + B.frs);
+    float* St = reinterpret_cast<float*>(smem_raw + off);                      // [2][TE][ers + frs]
+    off = align16(off + 2 * st_elems * sizeof(float));
+    int* roff = reinterpret_cast<int*>(smem_raw + off);                        // [NFE]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + align16(off + NFE * sizeof(int)));   // full[2], empty[2]
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < B.Mir * NSP; i += blockDim.x) As[i] = B.Air[i];
+    for (int i = tid; i < NFE; i += blockDim.x) roff[i] = B.recoff[i];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], NC / 32);
+        mbar_init(&bar[3], NC / 32);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int ntiles = (B.nelem + TE - 1) / TE;
+    const int lane = tid & 31;
+
+    if (tid >= NC) {
+        // Producer: one 2D tensor copy per tile, the box (TE elements x NROW
+        // rows) of the block's state matrix at element e0 (a multiple of TE, so
+        // 16-byte aligned); columns past the matrix's padded width read zeros.
+        if (lane == 0) {
+            int k = 0;
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+                const int s = k & 1;
+                if (k >= 2 && !mbar_wait(&bar[2 + s], ((k >> 1) - 1) & 1)) *err = 2;
+                mbar_arrive_expect_tx(&bar[s], (uint32_t)(NROW * TE * sizeof(float)));
+                fence_proxy_async();
+                tma_load_2d(Ub + (size_t)s * NROW * TE, &umap, t * TE, 0, &bar[s]);
+            }
+        }
+        return;
+    }
+
+    // Consumers.
+    const int el = tid % TE;
+    const int v = (tid / TE) % V;
+    const int g = tid / (TE * V);
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        const int e0 = t * TE;
+        const int n = min(TE, B.nelem - e0);
+        if (!mbar_wait(&bar[s], (k >> 1) & 1)) *err = 2;
+        float u[NS];
+        const float* us = Ub + (size_t)s * NROW * TE + (size_t)v * TE + el;
+        #pragma unroll
+        for (int r = 0; r < NS; ++r) u[r] = us[(size_t)r * V * TE];
+        fence_proxy_async();            // these reads precede the producer's next copies into the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[2 + s]);
+        float* rs = St + (size_t)s * st_elems;
+        float* fs = rs + (size_t)TE * B.ers;
+        // The staging buffer s was last read by the bulk stores of tile k - 2.
+        if (tid == 0) bulk_wait_read1();
+        consumer_sync(NC);
+        const bool store = el < n;
+        // All of this thread's rows j = g + i GR are accumulated in registers
+        // first and stored afterwards: with shared-memory stores between them
+        // the operator-row loads of the next rows could not be issued early.
+        constexpr int NR = (MI + GR - 1) / GR;   // rows per thread (some past MI for g > 0)
+        constexpr int RB = 4;                    // rows per pass: independent accumulation chains
+        float acc[NR];
+        #pragma unroll
+        for (int i0 = 0; i0 < NR; i0 += RB) {
+            #pragma unroll
+            for (int i = i0; i < i0 + RB && i < NR; ++i) acc[i] = 0.f;
+            #pragma unroll
+            for (int r = 0; r < NS; r += 4) {
+                float4 x[RB];
+                #pragma unroll
+                for (int i = 0; i < RB; ++i) {
+                    const int j = min(g + (i0 + i) * GR, MI - 1);   // rows past the end: computed, not stored
+                    x[i] = *reinterpret_cast<const float4*>(As + (size_t)j * NSP + r);
+                }
+                #pragma unroll
+                for (int i = 0; i < RB; ++i) {
+                    if (i0 + i >= NR) break;
+                    const float xa[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (r + q < NS) acc[i0 + i] = fmaf(xa[q], u[r + q], acc[i0 + i]);
+                }
+            }
+        }
+        if (store) {
+            #pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const int j = g + i * GR;
+                if (j < NFE) rs[(size_t)el * B.ers + roff[j] + v] = acc[i];
+                else if (j < MI) fs[(size_t)el * B.frs + (j - NFE) * V + v] = acc[i];
+            }
+        }
+        fence_proxy_async();         // every writer orders its staging stores before the bulk stores
+        consumer_sync(NC);
+        if (tid == 0) {
+            bulk_s2g(REC + B.rec_base + (size_t)e0 * B.ers, rs, (uint32_t)(n * B.ers * sizeof(float)));
+            bulk_s2g(FIUR + B.fiur_base + (size_t)e0 * B.frs, fs, (uint32_t)(n * B.frs * sizeof(float)));
+            bulk_commit();
+        }
+    }
+    if (tid == 0) bulk_wait0();      // writes complete before the kernel ends
+}
+
+// ---------------------------------------------------------------------------
 // Flux and divergence of one tile staged in shared memory (value path).
 template <typename T, int V, int ND, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW>
 __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __restrict__ REC,
@@ -297,7 +456,7 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
     constexpr int ND2 = ND * ND;
     using VT = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::n;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     size_t off = 16;
     T* As = reinterpret_cast<T*>(smem_raw + off);                 // [K2][G][RSP]
@@ -498,7 +657,7 @@ __global__ void __launch_bounds__(32 * V, 4) k_flux_rec_dual(KBlock<T> B, const 
     constexpr int NCOL = V * TE;
     constexpr int ND2 = ND * ND;
     constexpr int NFACE = ND + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int NSP = B.Md_pad;
     const int K2 = B.nfe + B.nfi;
     T* As = reinterpret_cast<T*>(smem_raw);                                   // [K2][NSP]
@@ -671,8 +830,66 @@ bool fast_path_available(int shape, int nsol, int nd, int system, int riemann) {
     return system == SYS_EULER && riemann == RIE_RUSANOV;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of one block's FP32 state matrix: rows (rho, v), columns the
+// padded elements (ld); boxes of te x nrow.
+static bool encode_state_map(CUtensorMap* map, const float* base, uint64_t ld, uint64_t nrow, uint32_t te) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * sizeof(float)) % 16 != 0) return false;
+    const cuuint64_t dims[2] = {ld, nrow};
+    const cuuint64_t strides[1] = {ld * sizeof(float)};
+    const cuuint32_t box[2] = {te, (cuuint32_t)nrow};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NS, int V, int NFE, int NFIU, int TE, int GR>
+static bool interp_pipe_impl(const KBlock<float>& B, const float* U, float* REC, float* FIUR, int* err, int nsm,
+                             cudaStream_t st) {
+    constexpr int NSP = (NS + 7) / 8 * 8;
+    static_assert(NS * V <= 256 && TE <= 256, "tensor copy box");
+    if (B.Md_pad != NSP) return false;
+    CUtensorMap umap;
+    if (!encode_state_map(&umap, U + B.u_off, (uint64_t)B.ld, (uint64_t)NS * V, TE)) return false;
+    auto a16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    size_t smem = (a16((size_t)B.Mir * NSP * 4) + 127) / 128 * 128;
+    smem = a16(smem + 2 * (size_t)NS * V * TE * 4);
+    smem = a16(smem + 2 * (size_t)TE * (B.ers + B.frs) * 4);
+    smem = a16(smem + NFE * 4) + 4 * 8;
+    if (smem > 227 * 1024) return false;
+    auto k = k_interp_pipe<NS, V, NFE, NFIU, TE, GR>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int need = (B.nelem + TE - 1) / TE;
+    const int grid = need < nsm ? need : nsm;
+    k<<<grid, V * TE * GR + 32, smem, st>>>(B, umap, REC, FIUR, err);
+    return true;
+}
+
 template <typename T>
 int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (V == 5 && B.nsol == 20 && interp_pipe_impl<20, 5, 40, 10, 64, 2>(B, U, REC, FIUR, err, nsm, st)) return 0;
+        if (V == 5 && B.nsol == 35 && interp_pipe_impl<35, 5, 60, 20, 32, 4>(B, U, REC, FIUR, err, nsm, st)) return 0;
+        if (V == 1 && B.nsol == 20 && interp_pipe_impl<20, 1, 40, 10, 64, 4>(B, U, REC, FIUR, err, nsm, st)) return 0;
+        if (V == 1 && B.nsol == 35 && interp_pipe_impl<35, 1, 60, 20, 64, 4>(B, U, REC, FIUR, err, nsm, st)) return 0;
+    }
     if (V == 5 && B.nsol == 20) interp_rec_impl<T, 20, 5, 40, 10>(B, U, REC, FIUR, err, nsm, st);
     else if (V == 5 && B.nsol == 35) interp_rec_impl<T, 35, 5, 60, 20>(B, U, REC, FIUR, err, nsm, st);
     else if (V == 1 && B.nsol == 20) interp_rec_impl<T, 20, 1, 40, 10>(B, U, REC, FIUR, err, nsm, st);
