@@ -81,6 +81,14 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// 16-byte shared-memory load of data that is constant for the kernel's life
+// (no memory clobber: the compiler may move it across other shared stores).
+__device__ __forceinline__ float4 lds128_const(const float* p) {
+    float4 r;
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(smem_u32(p)));
+    return r;
+}
+
 // 2D tensor copy (TMA) of one box at (x, y) of the tensor map into shared memory,
 // completing on bar.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -312,20 +320,23 @@ __global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __r
 // Consumer thread (e, v, g) copies the NS values of variable v of element e
 // to registers, releases the stage (empty[s]) and computes the rows
 // j = g, g + GR, ... of [u_fe; u_fiu] = [M0; M12] U (Eqs.
-// "interpolation_procedure"), four rows at a time, with every lane of a warp
-// reading the same operator rows from shared memory (broadcast).  The results
+// "interpolation_procedure"), with every lane of a warp reading the same
+// operator rows from shared memory (broadcast).  With ALLV a thread (e, g)
+// takes all V variables (V times the FMAs per operator load); its warp holds 8
+// elements x 4 row groups, so that the staging stores of a warp fall on 32
+// distinct banks (record stride = 4 mod 8 words apart per element).  The results
 // are assembled into one of two record staging buffers that a single thread
 // writes out with bulk stores while the next tile is computed.  One CTA per
 // SM, persistent.
-template <int NS, int V, int NFE, int NFIU, int TE, int GR>
-__global__ void __launch_bounds__(V * TE * GR + 32, 1) k_interp_pipe(KBlock<float> B,
+template <int NS, int V, int NFE, int NFIU, int TE, int GR, bool ALLV>
+__global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, 1) k_interp_pipe(KBlock<float> B,
                                                                      const __grid_constant__ CUtensorMap umap,
                                                                      float* __restrict__ REC,
                                                                      float* __restrict__ FIUR, int* __restrict__ err) {
     constexpr int NROW = NS * V;                      // rows (rho, v) of a U tile
     constexpr int MI = NFE + NFIU;
     constexpr int NSP = (NS + 7) / 8 * 8;             // operator row stride (= B.Md_pad)
-    constexpr int NC = V * TE * GR;                   // consumer threads
+    constexpr int NC = (ALLV ? 1 : V) * TE * GR;      // consumer threads
     static_assert(NC % 32 == 0 && TE % 32 == 0, "tile layout");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* As = reinterpret_cast<float*>(smem_raw);                            // [Mir][NSP]
@@ -371,19 +382,30 @@ __global__ void __launch_bounds__(V * TE * GR + 32, 1) k_interp_pipe(KBlock<floa
     }
 
     // Consumers.
-    const int el = tid % TE;
-    const int v = (tid / TE) % V;
-    const int g = tid / (TE * V);
+    int el, v, g;
+    if constexpr (ALLV) {
+        static_assert(GR == 4, "8 elements x 4 row groups per warp");
+        el = (tid >> 5) * 8 + (lane >> 2);
+        v = 0;
+        g = lane & 3;
+    } else {
+        el = tid % TE;
+        v = (tid / TE) % V;
+        g = tid / (TE * V);
+    }
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
         const int s = k & 1;
         const int e0 = t * TE;
         const int n = min(TE, B.nelem - e0);
         if (!mbar_wait(&bar[s], (k >> 1) & 1)) *err = 2;
-        float u[NS];
+        constexpr int UV = ALLV ? V : 1;          // variables held by a thread
+        float u[UV][NS];
         const float* us = Ub + (size_t)s * NROW * TE + (size_t)v * TE + el;
         #pragma unroll
-        for (int r = 0; r < NS; ++r) u[r] = us[(size_t)r * V * TE];
+        for (int w = 0; w < UV; ++w)
+            #pragma unroll
+            for (int r = 0; r < NS; ++r) u[w][r] = us[(size_t)(r * V + w) * TE];
         fence_proxy_async();            // these reads precede the producer's next copies into the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar[2 + s]);
@@ -393,40 +415,79 @@ __global__ void __launch_bounds__(V * TE * GR + 32, 1) k_interp_pipe(KBlock<floa
         if (tid == 0) bulk_wait_read1();
         consumer_sync(NC);
         const bool store = el < n;
-        // All of this thread's rows j = g + i GR are accumulated in registers
-        // first and stored afterwards: with shared-memory stores between them
-        // the operator-row loads of the next rows could not be issued early.
-        constexpr int NR = (MI + GR - 1) / GR;   // rows per thread (some past MI for g > 0)
-        constexpr int RB = 4;                    // rows per pass: independent accumulation chains
-        float acc[NR];
-        #pragma unroll
-        for (int i0 = 0; i0 < NR; i0 += RB) {
-            #pragma unroll
-            for (int i = i0; i < i0 + RB && i < NR; ++i) acc[i] = 0.f;
-            #pragma unroll
-            for (int r = 0; r < NS; r += 4) {
-                float4 x[RB];
+        if constexpr (ALLV) {
+            // Rows j = g + GR i two at a time, stored right away (the operator
+            // loads are free to move across the stores).
+            #pragma unroll 1
+            for (int j = g; j < MI; j += 2 * GR) {
+                const int j2 = j + GR;
+                const int jb = j2 < MI ? j2 : j;
+                float acc[2][UV];
                 #pragma unroll
-                for (int i = 0; i < RB; ++i) {
-                    const int j = min(g + (i0 + i) * GR, MI - 1);   // rows past the end: computed, not stored
-                    x[i] = *reinterpret_cast<const float4*>(As + (size_t)j * NSP + r);
-                }
+                for (int w = 0; w < UV; ++w) acc[0][w] = acc[1][w] = 0.f;
                 #pragma unroll
-                for (int i = 0; i < RB; ++i) {
-                    if (i0 + i >= NR) break;
-                    const float xa[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
+                for (int r = 0; r < NS; r += 4) {
+                    const float4 x0 = lds128_const(As + (size_t)j * NSP + r);
+                    const float4 x1 = lds128_const(As + (size_t)jb * NSP + r);
+                    const float xa[4] = {x0.x, x0.y, x0.z, x0.w};
+                    const float xb[4] = {x1.x, x1.y, x1.z, x1.w};
                     #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (r + q < NS) acc[i0 + i] = fmaf(xa[q], u[r + q], acc[i0 + i]);
+                        if (r + q < NS) {
+                            #pragma unroll
+                            for (int w = 0; w < UV; ++w) {
+                                acc[0][w] = fmaf(xa[q], u[w][r + q], acc[0][w]);
+                                acc[1][w] = fmaf(xb[q], u[w][r + q], acc[1][w]);
+                            }
+                        }
+                }
+                if (store) {
+                    #pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int jj = i == 0 ? j : j2;
+                        if (jj >= MI) break;
+                        float* dst = jj < NFE ? rs + (size_t)el * B.ers + roff[jj]
+                                              : fs + (size_t)el * B.frs + (jj - NFE) * V;
+                        #pragma unroll
+                        for (int w = 0; w < UV; ++w) dst[w] = acc[i][w];
+                    }
                 }
             }
-        }
-        if (store) {
+        } else {
+            // All of this thread's rows j = g + i GR are accumulated in registers
+            // first and stored afterwards.
+            constexpr int NR = (MI + GR - 1) / GR;   // rows per thread (some past MI for g > 0)
+            constexpr int RB = 4;                    // rows per pass: independent accumulation chains
+            float acc[NR];
             #pragma unroll
-            for (int i = 0; i < NR; ++i) {
-                const int j = g + i * GR;
-                if (j < NFE) rs[(size_t)el * B.ers + roff[j] + v] = acc[i];
-                else if (j < MI) fs[(size_t)el * B.frs + (j - NFE) * V + v] = acc[i];
+            for (int i0 = 0; i0 < NR; i0 += RB) {
+                #pragma unroll
+                for (int i = i0; i < i0 + RB && i < NR; ++i) acc[i] = 0.f;
+                #pragma unroll
+                for (int r = 0; r < NS; r += 4) {
+                    float4 x[RB];
+                    #pragma unroll
+                    for (int i = 0; i < RB; ++i) {
+                        const int j = min(g + (i0 + i) * GR, MI - 1);   // rows past the end: computed, not stored
+                        x[i] = lds128_const(As + (size_t)j * NSP + r);
+                    }
+                    #pragma unroll
+                    for (int i = 0; i < RB; ++i) {
+                        if (i0 + i >= NR) break;
+                        const float xa[4] = {x[i].x, x[i].y, x[i].z, x[i].w};
+                        #pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (r + q < NS) acc[i0 + i] = fmaf(xa[q], u[0][r + q], acc[i0 + i]);
+                    }
+                }
+            }
+            if (store) {
+                #pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    const int j = g + i * GR;
+                    if (j < NFE) rs[(size_t)el * B.ers + roff[j] + v] = acc[i];
+                    else if (j < MI) fs[(size_t)el * B.frs + (j - NFE) * V + v] = acc[i];
+                }
             }
         }
         fence_proxy_async();         // every writer orders its staging stores before the bulk stores
@@ -860,7 +921,7 @@ static bool encode_state_map(CUtensorMap* map, const float* base, uint64_t ld, u
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NS, int V, int NFE, int NFIU, int TE, int GR>
+template <int NS, int V, int NFE, int NFIU, int TE, int GR, bool ALLV>
 static bool interp_pipe_impl(const KBlock<float>& B, const float* U, float* REC, float* FIUR, int* err, int nsm,
                              cudaStream_t st) {
     constexpr int NSP = (NS + 7) / 8 * 8;
@@ -874,21 +935,29 @@ static bool interp_pipe_impl(const KBlock<float>& B, const float* U, float* REC,
     smem = a16(smem + 2 * (size_t)TE * (B.ers + B.frs) * 4);
     smem = a16(smem + NFE * 4) + 4 * 8;
     if (smem > 227 * 1024) return false;
-    auto k = k_interp_pipe<NS, V, NFE, NFIU, TE, GR>;
+    auto k = k_interp_pipe<NS, V, NFE, NFIU, TE, GR, ALLV>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int need = (B.nelem + TE - 1) / TE;
     const int grid = need < nsm ? need : nsm;
-    k<<<grid, V * TE * GR + 32, smem, st>>>(B, umap, REC, FIUR, err);
+    k<<<grid, (ALLV ? 1 : V) * TE * GR + 32, smem, st>>>(B, umap, REC, FIUR, err);
     return true;
 }
 
 template <typename T>
 int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) {
-        if (V == 5 && B.nsol == 20 && interp_pipe_impl<20, 5, 40, 10, 64, 2>(B, U, REC, FIUR, err, nsm, st)) return 0;
-        if (V == 5 && B.nsol == 35 && interp_pipe_impl<35, 5, 60, 20, 32, 4>(B, U, REC, FIUR, err, nsm, st)) return 0;
-        if (V == 1 && B.nsol == 20 && interp_pipe_impl<20, 1, 40, 10, 64, 4>(B, U, REC, FIUR, err, nsm, st)) return 0;
-        if (V == 1 && B.nsol == 35 && interp_pipe_impl<35, 1, 60, 20, 64, 4>(B, U, REC, FIUR, err, nsm, st)) return 0;
+        if (V == 5 && B.nsol == 20 &&
+            interp_pipe_impl<20, 5, 40, 10, 64, 4, true>(B, U, REC, FIUR, err, nsm, st))
+            return 0;
+        if (V == 5 && B.nsol == 35 &&
+            interp_pipe_impl<35, 5, 60, 20, 32, 4, false>(B, U, REC, FIUR, err, nsm, st))
+            return 0;
+        if (V == 1 && B.nsol == 20 &&
+            interp_pipe_impl<20, 1, 40, 10, 64, 4, false>(B, U, REC, FIUR, err, nsm, st))
+            return 0;
+        if (V == 1 && B.nsol == 35 &&
+            interp_pipe_impl<35, 1, 60, 20, 64, 4, false>(B, U, REC, FIUR, err, nsm, st))
+            return 0;
     }
     if (V == 5 && B.nsol == 20) interp_rec_impl<T, 20, 5, 40, 10>(B, U, REC, FIUR, err, nsm, st);
     else if (V == 5 && B.nsol == 35) interp_rec_impl<T, 35, 5, 60, 20>(B, U, REC, FIUR, err, nsm, st);
