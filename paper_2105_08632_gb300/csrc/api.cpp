@@ -89,11 +89,17 @@ struct Mesh {
     std::vector<double> sol_xyz;
     DevBuf ufe, dufe, ustage, uacc, uhost_dev, rec, drec, fiur, dfiur;
     DevBuf qfe, dqfe, qfiu, dqfiu;    // viscous: flux-point gradients (kargs.hpp layout)
+    // Block tables of the generic kernels (one launch per kernel kind walks
+    // every block): host copies and the device array, in the mesh precision.
+    std::vector<KBlock<float>> kb_f;
+    std::vector<KBlock<double>> kb_d;
+    DevBuf kb_dev;
     // RK4 graph cache
     cudaGraphExec_t graph = nullptr;
     const void* graph_u = nullptr;
     double graph_dt = 0;
     std::vector<int> graph_slots;     // timing slots recorded inside the graph
+    int64_t graph_launches = 0;       // kernel launches in one replay
     bool warmed = false;
     ~Mesh() {
         if (graph) cudaGraphExecDestroy(graph);
@@ -282,7 +288,24 @@ KBlock<T> make_kblock(const EType& et, const MBlock& b) {
     K.pfr = b.pfr.as<int>();
     K.perm = b.perm.as<unsigned char>();
     K.recoff = b.recoff.as<int>();
+    K.te_interp = 32;
+    K.te_res = b.tile;
+    K.te_res_dual = b.tile_dual;
+    K.te_grad = b.gtile;
+    K.te_grad_dual = b.gtile_dual;
+    K.te_vjp = b.vtile;
     return K;
+}
+
+template <typename T>
+KSet<T> kset(const Mesh& m);
+template <>
+KSet<float> kset<float>(const Mesh& m) {
+    return {m.kb_f.data(), m.kb_dev.as<KBlock<float>>(), (int)m.kb_f.size()};
+}
+template <>
+KSet<double> kset<double>(const Mesh& m) {
+    return {m.kb_d.data(), m.kb_dev.as<KBlock<double>>(), (int)m.kb_d.size()};
 }
 
 template <typename T>
@@ -295,11 +318,6 @@ KPhys<T> make_phys(const sdrt_physics& p) {
     P.beta = (T)p.beta;
     P.eta = (T)p.eta;
     return P;
-}
-
-int grid_for(const sdrt_ctx* ctx, const MBlock& b, int TE, int per_sm) {
-    const int ntiles = (b.nelem + TE - 1) / TE;
-    return std::max(1, std::min(ntiles, ctx->nsm * per_sm));
 }
 
 // Residual-type evaluation of the whole mesh: interpolation of every block,
@@ -367,49 +385,38 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
         if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
         return SDRT_OK;
     }
-    for (auto& bp : m.blocks) {
-        const EType& et = *ctx->etypes[bp->etype];
-        KBlock<T> K = make_kblock<T>(et, *bp);
-        int s = prof_begin(ctx, KIND_INTERP);
-        launch_interp_ext<T>(K, m.nvar, U, ufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
+    // Generic path: one launch per kernel kind, each walking the tiles of every block.
+    const KSet<T> ks = kset<T>(m);
+    int s = prof_begin(ctx, KIND_INTERP);
+    launch_interp_ext<T>(ks, m.nvar, U, ufe, m.Ftot, ctx->nsm, ctx->stream);
+    prof_end(ctx, s);
+    ++ctx->launches;
+    if (dU) {
+        s = prof_begin(ctx, KIND_INTERP);
+        launch_interp_ext<T>(ks, m.nvar, dU, dufe, m.Ftot, ctx->nsm, ctx->stream);
         prof_end(ctx, s);
         ++ctx->launches;
-        if (dU) {
-            s = prof_begin(ctx, KIND_INTERP);
-            launch_interp_ext<T>(K, m.nvar, dU, dufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
-            prof_end(ctx, s);
-            ++ctx->launches;
-        }
     }
     KVisc<T> Q{};
     if (viscous(m)) {
         // Flux-point gradients of every block (they read every block's u_fe).
         Q = {m.qfe.as<T>(), dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr};
-        for (auto& bp : m.blocks) {
-            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
-            const int TE = dU ? bp->gtile_dual : bp->gtile;
-            if (TE == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
-            const int s = prof_begin(ctx, KIND_GRAD);
-            int r = launch_grad<T>(K, sys, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, m.qfe.as<T>(),
-                                   dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr, TE,
-                                   grid_for(ctx, *bp, TE, 2), ctx->stream);
-            prof_end(ctx, s);
-            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
-            ++ctx->launches;
-        }
-    }
-    for (auto& bp : m.blocks) {
-        const EType& et = *ctx->etypes[bp->etype];
-        KBlock<T> K = make_kblock<T>(et, *bp);
-        const int TE = dU ? bp->tile_dual : bp->tile;
-        if (TE == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
-        const int s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
-        int r = launch_residual<T>(K, sys, m.phys.riemann, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, E, Q, TE,
-                                   grid_for(ctx, *bp, TE, 2), ctx->stream);
+        s = prof_begin(ctx, KIND_GRAD);
+        int r = launch_grad<T>(ks, sys, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, m.qfe.as<T>(),
+                               dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr, ctx->nsm,
+                               ctx->stream);
         prof_end(ctx, s);
-        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
+        if (r == -2) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
         ++ctx->launches;
     }
+    s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
+    int r = launch_residual<T>(ks, sys, m.phys.riemann, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, E, Q, ctx->nsm,
+                               ctx->stream);
+    prof_end(ctx, s);
+    if (r == -2) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
+    if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
+    ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SDRT_OK;
@@ -422,25 +429,21 @@ int run_vjp(sdrt_ctx* ctx, Mesh& m, const T* U, const T* W, T* out) {
     const KPhys<T> P = make_phys<T>(m.phys);
     T* ufe = m.ufe.as<T>();
     T* gs = m.dufe.as<T>();
-    for (auto& bp : m.blocks)
-        if (bp->vtile == 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP tile does not fit in shared memory for this element type");
-    for (auto& bp : m.blocks) {
-        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
-        const int s = prof_begin(ctx, KIND_INTERP);
-        launch_interp_ext<T>(K, m.nvar, U, ufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
+    const KSet<T> ks = kset<T>(m);
+    if (!ks.all_tiled(TK_VJP))
+        return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP tile does not fit in shared memory for this element type");
+    int s = prof_begin(ctx, KIND_INTERP);
+    launch_interp_ext<T>(ks, m.nvar, U, ufe, m.Ftot, ctx->nsm, ctx->stream);
+    prof_end(ctx, s);
+    ++ctx->launches;
+    for (int pass = 0; pass < 2; ++pass) {
+        s = prof_begin(ctx, KIND_JVP);
+        int r = launch_vjp<T>(ks, pass, m.phys.system, m.phys.riemann, m.nd, U, W, ufe, gs, m.Ftot, P, out,
+                              ctx->flag.as<int>(), ctx->nsm, ctx->stream);
         prof_end(ctx, s);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported by the VJP");
         ++ctx->launches;
     }
-    for (int pass = 0; pass < 2; ++pass)
-        for (auto& bp : m.blocks) {
-            KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
-            const int s = prof_begin(ctx, KIND_JVP);
-            int r = launch_vjp<T>(K, pass, m.phys.system, m.phys.riemann, m.nd, U, W, ufe, gs, m.Ftot, P, out,
-                                  ctx->flag.as<int>(), bp->vtile, grid_for(ctx, *bp, bp->vtile, 2), ctx->stream);
-            prof_end(ctx, s);
-            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported by the VJP");
-            ++ctx->launches;
-        }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SDRT_OK;
@@ -977,6 +980,16 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
             mb.vtile = vsmem_of(TE) <= 220 * 1024 ? TE : 0;
         }
     }
+    // Block tables of the generic kernels (tile widths are final here).
+    for (auto& bp : m->blocks) {
+        const EType& et = *ctx->etypes[bp->etype];
+        if (f32) m->kb_f.push_back(make_kblock<float>(et, *bp));
+        else m->kb_d.push_back(make_kblock<double>(et, *bp));
+    }
+    if (!ctx->host_only) {
+        if (f32) SDRT_CUDA(upload(m->kb_dev, m->kb_f));
+        else SDRT_CUDA(upload(m->kb_dev, m->kb_d));
+    }
     ctx->meshes.push_back(std::move(m));
     *mesh_id = (int)ctx->meshes.size() - 1;
     return SDRT_OK;
@@ -1085,6 +1098,7 @@ int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
         r = rk4_eager(ctx, m, U, dt);
         ctx->capture_slots = nullptr;
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        m.graph_launches = ctx->launches - before;   // kernel nodes of one RK4 step
         ctx->launches = before;
         if (r) return r;
         if (ce != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -1094,10 +1108,9 @@ int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
         m.graph_u = U;
         m.graph_dt = dt;
     }
-    const int per_step = (int)m.blocks.size() * 8;
     for (; s < nsteps; ++s) {
         SDRT_CUDA(cudaGraphLaunch(m.graph, ctx->stream));
-        ctx->launches += per_step;
+        ctx->launches += m.graph_launches;
     }
     // Events inside the graph hold the timings of its last replay.
     if (ctx->prof) ctx->pending.insert(ctx->pending.end(), m.graph_slots.begin(), m.graph_slots.end());
@@ -1224,18 +1237,13 @@ int residual_into(sdrt_ctx* ctx, Mesh& m, const T* U, T* R, T* ufe) {
     E.mode = EPI_STORE;
     E.out = R;
     E.flag = ctx->flag.as<int>();
-    for (auto& bp : m.blocks) {
-        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
-        launch_interp_ext<T>(K, m.nvar, U, ufe, m.Ftot, 32, grid_for(ctx, *bp, 32, 4), ctx->stream);
-        ++ctx->launches;
-    }
-    for (auto& bp : m.blocks) {
-        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
-        int r = launch_residual<T>(K, m.phys.system, m.phys.riemann, m.nd, U, nullptr, ufe, nullptr, m.Ftot, P, E,
-                                   KVisc<T>{}, bp->tile, grid_for(ctx, *bp, bp->tile, 2), ctx->stream);
-        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
-        ++ctx->launches;
-    }
+    const KSet<T> ks = kset<T>(m);
+    launch_interp_ext<T>(ks, m.nvar, U, ufe, m.Ftot, ctx->nsm, ctx->stream);
+    ++ctx->launches;
+    int r = launch_residual<T>(ks, m.phys.system, m.phys.riemann, m.nd, U, nullptr, ufe, nullptr, m.Ftot, P, E,
+                               KVisc<T>{}, ctx->nsm, ctx->stream);
+    if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
+    ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SDRT_OK;

@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "device_math.cuh"
 #include "kargs.hpp"
@@ -162,18 +163,39 @@ __device__ __forceinline__ void load_tile(const KBlock<T>& B, const T* U, const 
     }
 }
 
+// Block and tile of the global tile g of a work table (false past the last
+// tile).  Every thread of a CTA gets the same answer for the same g.
+template <typename T>
+__device__ __forceinline__ bool locate(const KTable<T>& tab, int kind, int g, int& b, int& tile) {
+    for (int i = 0; i < tab.nblocks; ++i) {
+        const KBlock<T>& B = tab.blocks[i];
+        const int te = tile_width(B, kind);
+        const int n = (B.nelem + te - 1) / te;
+        if (g < n) {
+            b = i;
+            tile = g;
+            return true;
+        }
+        g -= n;
+    }
+    return false;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// u_fe = M0 U for every element of the block, written to UFE.
+// u_fe = M0 U for every element of every block of the table, written to UFE.
 template <typename T, int V>
-__global__ void __launch_bounds__(256) k_interp_ext(KBlock<T> B, const T* __restrict__ U, T* __restrict__ UFE,
-                                                    int64_t Ftot, int TE) {
+__global__ void __launch_bounds__(256) k_interp_ext(KTable<T> tab, const T* __restrict__ U, T* __restrict__ UFE,
+                                                    int64_t Ftot) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Us = reinterpret_cast<T*>(smem_raw);
-    const int ntiles = (B.nelem + TE - 1) / TE;
-    const int NCOL = V * TE;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int gt = blockIdx.x;; gt += gridDim.x) {
+        int bi, tile;
+        if (!locate(tab, TK_INTERP, gt, bi, tile)) break;
+        const KBlock<T>& B = tab.blocks[bi];
+        const int TE = B.te_interp;
+        const int NCOL = V * TE;
         const int e0 = tile * TE;
         __syncthreads();
         load_tile<T, T, V>(B, U, nullptr, e0, TE, Us);
@@ -320,16 +342,22 @@ __device__ __forceinline__ void load_grad(const T* Q, const T* dQ, size_t base, 
 // Full residual of one block (S = T: value; S = Dual<T>: JVP).  Viscous systems
 // read the physical gradients at the flux points from Q (written by k_grad).
 template <typename S, typename T, int V, int ND, int SYS, int RIE>
-__global__ void __launch_bounds__(256) k_residual(KBlock<T> B, const T* __restrict__ U, const T* __restrict__ dU,
+__global__ void __launch_bounds__(256) k_residual(KTable<T> tab, const T* __restrict__ U, const T* __restrict__ dU,
                                                   const T* __restrict__ UFE, const T* __restrict__ dUFE, int64_t Ftot,
-                                                  KPhys<T> P, KEpi<T> E, int TE, int rowsA, KVisc<T> Q) {
+                                                  KPhys<T> P, KEpi<T> E, KVisc<T> Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int NCOL = V * TE;
-    S* RA = reinterpret_cast<S*>(smem_raw);            // U tile, then internal F~ (rowsA rows)
-    S* RB = RA + (size_t)rowsA * NCOL;                  // [u_fe; u_fiu], F~_fe in place of u_fe
-    const int ntiles = (B.nelem + TE - 1) / TE;
     constexpr int ND2 = ND * ND;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    constexpr bool dual = !std::is_same<S, T>::value;
+    constexpr int kind = dual ? TK_RES_DUAL : TK_RES;
+    for (int gt = blockIdx.x;; gt += gridDim.x) {
+        int bi, tile;
+        if (!locate(tab, kind, gt, bi, tile)) break;
+        const KBlock<T>& B = tab.blocks[bi];
+        const int TE = tile_width(B, kind);
+        const int NCOL = V * TE;
+        const int rowsA = B.nsol > B.nfi ? B.nsol : B.nfi;
+        S* RA = reinterpret_cast<S*>(smem_raw);         // U tile, then internal F~ (rowsA rows)
+        S* RB = RA + (size_t)rowsA * NCOL;               // [u_fe; u_fiu], F~_fe in place of u_fe
         const int e0 = tile * TE;
         __syncthreads();
         load_tile<S, T, V>(B, U, dU, e0, TE, RA);
@@ -435,12 +463,12 @@ __global__ void __launch_bounds__(256) k_residual(KBlock<T> B, const T* __restri
 
 // Launch of one k_residual instantiation (host side).
 template <typename S, typename T, int V, int ND, int SYS, int RIE>
-inline void launch_res_impl(const KBlock<T>& B, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
-                            const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int TE, int rowsA, int smem,
-                            int grid, cudaStream_t st) {
+inline void launch_res_impl(const KTable<T>& tab, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
+                            const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int smem, int grid,
+                            cudaStream_t st) {
     auto k = k_residual<S, T, V, ND, SYS, RIE>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k<<<grid, 256, smem, st>>>(B, U, dU, UFE, dUFE, Ftot, P, E, TE, rowsA, Q);
+    k<<<grid, 256, smem, st>>>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q);
 }
 
 }  // namespace sdrt

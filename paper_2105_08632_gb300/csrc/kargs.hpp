@@ -56,7 +56,34 @@ struct KBlock {
     const int* pfr;      // [nelem][nfaces] REC offset of the partner's face record
     const unsigned char* perm;  // [nelem][pstride] local index, in the partner's face record, of each external point
     const int* recoff;   // [nfe] offset of external point j in the element record
+    // Tile widths (elements per tile) of the generic kernels for this block.
+    int te_interp, te_res, te_res_dual, te_grad, te_grad_dual, te_vjp;
 };
+
+// The blocks of a mesh as one work table for the generic kernels: global tile
+// g belongs to the first block b whose tile count (ceil(nelem / TE_b), TE_b
+// the kernel's tile width) exceeds g minus the tiles of the blocks before it.
+// One launch walks the tiles of every block (blocks: device array).
+template <typename T>
+struct KTable {
+    const KBlock<T>* blocks;
+    int nblocks;
+};
+
+// Which tile width a generic kernel uses.
+enum TileKind { TK_INTERP = 0, TK_RES = 1, TK_RES_DUAL = 2, TK_GRAD = 3, TK_GRAD_DUAL = 4, TK_VJP = 5 };
+
+template <typename T>
+__host__ __device__ inline int tile_width(const KBlock<T>& B, int kind) {
+    switch (kind) {
+        case TK_INTERP: return B.te_interp;
+        case TK_RES: return B.te_res;
+        case TK_RES_DUAL: return B.te_res_dual;
+        case TK_GRAD: return B.te_grad;
+        case TK_GRAD_DUAL: return B.te_grad_dual;
+        default: return B.te_vjp;
+    }
+}
 
 // Physical gradients of the viscous systems at the flux points.
 //   QFE  [ND][V][F_tot]: gradient at external points (UFE indexing), component d

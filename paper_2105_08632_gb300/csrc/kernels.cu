@@ -10,19 +10,20 @@ namespace sdrt {
 // Host launchers.
 
 template <typename T>
-static int smem_interp(const KBlock<T>& B, int V, int TE) {
-    return B.nsol * V * TE * (int)sizeof(T);
-}
-
-template <typename T>
-void launch_interp_ext(const KBlock<T>& B, int V, const T* U, T* UFE, int64_t Ftot, int TE, int grid,
-                       cudaStream_t st) {
-    const int smem = smem_interp(B, V, TE);
+void launch_interp_ext(const KSet<T>& ks, int V, const T* U, T* UFE, int64_t Ftot, int nsm, cudaStream_t st) {
+    int smem = 0;
+    for (int i = 0; i < ks.n; ++i) {
+        const int b = ks.host[i].nsol * V * ks.host[i].te_interp * (int)sizeof(T);
+        smem = b > smem ? b : smem;
+    }
+    const int tiles = ks.tiles(TK_INTERP);
+    const int grid = tiles < 4 * nsm ? (tiles > 0 ? tiles : 1) : 4 * nsm;
+    const KTable<T> tab = ks.table();
     switch (V) {
 #define SDRT_CASE(VV)                                                                                   \
     case VV:                                                                                            \
         cudaFuncSetAttribute(k_interp_ext<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
-        k_interp_ext<T, VV><<<grid, 256, smem, st>>>(B, U, UFE, Ftot, TE);                               \
+        k_interp_ext<T, VV><<<grid, 256, smem, st>>>(tab, U, UFE, Ftot);                                 \
         break;
         SDRT_CASE(1)
         SDRT_CASE(4)
@@ -40,17 +41,25 @@ int residual_smem(const KBlock<T>& B, int V, int TE, bool dual, int* rowsA) {
 }
 
 template <typename T>
-int launch_residual(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU, const T* UFE,
-                    const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int TE,
-                    int grid, cudaStream_t st) {
+int launch_residual(const KSet<T>& ks, int system, int riemann, int nd, const T* U, const T* dU, const T* UFE,
+                    const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int nsm,
+                    cudaStream_t st) {
     if (system == SYS_ADVDIFF || system == SYS_NS)
-        return launch_residual_visc<T>(B, system, riemann, nd, U, dU, UFE, dUFE, Ftot, P, E, Q, TE, grid, st);
+        return launch_residual_visc<T>(ks, system, riemann, nd, U, dU, UFE, dUFE, Ftot, P, E, Q, nsm, st);
     const bool dual = dU != nullptr;
-    int rowsA = 0;
+    const int kind = dual ? TK_RES_DUAL : TK_RES;
+    if (!ks.all_tiled(kind)) return -2;
     const int V = (system == SYS_ADVECTION) ? 1 : nd + 2;
-    const int smem = residual_smem(B, V, TE, dual, &rowsA);
+    int smem = 0;
+    for (int i = 0; i < ks.n; ++i) {
+        const int b = residual_smem(ks.host[i], V, tile_width(ks.host[i], kind), dual, nullptr);
+        smem = b > smem ? b : smem;
+    }
+    const int tiles = ks.tiles(kind);
+    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
+    const KTable<T> tab = ks.table();
 #define SDRT_DISPATCH(SS, VV, NDD, SYSS, RIEE) \
-    launch_res_impl<SS, T, VV, NDD, SYSS, RIEE>(B, U, dU, UFE, dUFE, Ftot, P, E, Q, TE, rowsA, smem, grid, st)
+    launch_res_impl<SS, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, grid, st)
     if (system == SYS_ADVECTION) {
         if (nd == 2) {
             if (dual) SDRT_DISPATCH(Dual<T>, 1, 2, SYS_ADVECTION, RIE_UPWIND);
@@ -85,16 +94,15 @@ int launch_residual(const KBlock<T>& B, int system, int riemann, int nd, const T
     return -1;
 }
 
-template void launch_interp_ext<float>(const KBlock<float>&, int, const float*, float*, int64_t, int, int,
-                                       cudaStream_t);
-template void launch_interp_ext<double>(const KBlock<double>&, int, const double*, double*, int64_t, int, int,
+template void launch_interp_ext<float>(const KSet<float>&, int, const float*, float*, int64_t, int, cudaStream_t);
+template void launch_interp_ext<double>(const KSet<double>&, int, const double*, double*, int64_t, int,
                                         cudaStream_t);
-template int launch_residual<float>(const KBlock<float>&, int, int, int, const float*, const float*, const float*,
+template int launch_residual<float>(const KSet<float>&, int, int, int, const float*, const float*, const float*,
                                     const float*, int64_t, const KPhys<float>&, const KEpi<float>&,
-                                    const KVisc<float>&, int, int, cudaStream_t);
-template int launch_residual<double>(const KBlock<double>&, int, int, int, const double*, const double*,
+                                    const KVisc<float>&, int, cudaStream_t);
+template int launch_residual<double>(const KSet<double>&, int, int, int, const double*, const double*,
                                      const double*, const double*, int64_t, const KPhys<double>&,
-                                     const KEpi<double>&, const KVisc<double>&, int, int, cudaStream_t);
+                                     const KEpi<double>&, const KVisc<double>&, int, cudaStream_t);
 template int residual_smem<float>(const KBlock<float>&, int, int, bool, int*);
 template int residual_smem<double>(const KBlock<double>&, int, int, bool, int*);
 

@@ -10,10 +10,11 @@
 //   [q_fe; q_fiu] = [M0; M12] q                  written to QFE / QFIU
 // after which k_residual (generic.cuh) adds the LDG viscous common flux at the
 // external points and the viscous part of the transformed flux at the
-// internal DOFs.  One evaluation is three launches per block: k_interp_ext,
-// k_grad (after every block's interpolation) and k_residual (after every
-// block's gradient).
+// internal DOFs.  One evaluation is three launches, each walking the tiles of
+// every block: k_interp_ext, k_grad (after the interpolation) and k_residual
+// (after the gradients).
 #include <cstdint>
+#include <type_traits>
 
 #include "generic.cuh"
 #include "launch.hpp"
@@ -35,19 +36,23 @@ __device__ __forceinline__ void store_state(T* X, T* dX, size_t i, Dual<T> v) {
 // Shared memory: RU = U tile (nsol rows), RC = C (nfe rows), both of V * TE
 // columns (v, te); RQ = q (nsol rows of ND * V * TE columns (d, v, te)).
 template <typename S, typename T, int V, int ND>
-__global__ void __launch_bounds__(256) k_grad(KBlock<T> B, const T* __restrict__ U, const T* __restrict__ dU,
+__global__ void __launch_bounds__(256) k_grad(KTable<T> tab, const T* __restrict__ U, const T* __restrict__ dU,
                                               const T* __restrict__ UFE, const T* __restrict__ dUFE, int64_t Ftot,
                                               KPhys<T> P, T* __restrict__ QFE, T* __restrict__ dQFE,
-                                              T* __restrict__ QFIU, T* __restrict__ dQFIU, int TE) {
+                                              T* __restrict__ QFIU, T* __restrict__ dQFIU) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int NCOL = V * TE;
-    const int QCOL = ND * NCOL;
-    S* RU = reinterpret_cast<S*>(smem_raw);
-    S* RC = RU + (size_t)B.nsol * NCOL;
-    S* RQ = RC + (size_t)B.nfe * NCOL;
-    const int ntiles = (B.nelem + TE - 1) / TE;
     constexpr int ND2 = ND * ND;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    constexpr int kind = std::is_same<S, T>::value ? TK_GRAD : TK_GRAD_DUAL;
+    for (int gt = blockIdx.x;; gt += gridDim.x) {
+        int bi, tile;
+        if (!locate(tab, kind, gt, bi, tile)) break;
+        const KBlock<T>& B = tab.blocks[bi];
+        const int TE = tile_width(B, kind);
+        const int NCOL = V * TE;
+        const int QCOL = ND * NCOL;
+        S* RU = reinterpret_cast<S*>(smem_raw);
+        S* RC = RU + (size_t)B.nsol * NCOL;
+        S* RQ = RC + (size_t)B.nfe * NCOL;
         const int e0 = tile * TE;
         __syncthreads();
         load_tile<S, T, V>(B, U, dU, e0, TE, RU);
@@ -127,29 +132,36 @@ int grad_smem(const KBlock<T>& B, int V, int nd, int TE, bool dual) {
 }
 
 template <typename S, typename T, int V, int ND>
-static void launch_grad_impl(const KBlock<T>& B, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
-                             const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int TE, int smem, int grid,
+static void launch_grad_impl(const KTable<T>& tab, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
+                             const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int smem, int grid,
                              cudaStream_t st) {
     auto k = k_grad<S, T, V, ND>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k<<<grid, 256, smem, st>>>(B, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, TE);
+    k<<<grid, 256, smem, st>>>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU);
 }
 
 template <typename T>
-int launch_grad(const KBlock<T>& B, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
-                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int TE, int grid,
-                cudaStream_t st) {
+int launch_grad(const KSet<T>& ks, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
+                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int nsm, cudaStream_t st) {
     const bool dual = dU != nullptr;
+    const int kind = dual ? TK_GRAD_DUAL : TK_GRAD;
+    if (!ks.all_tiled(kind)) return -2;
     const int V = system == SYS_ADVDIFF ? 1 : nd + 2;
-    const int smem = grad_smem(B, V, nd, TE, dual);
-#define SDRT_GRAD(VV, NDD)                                                                                         \
-    do {                                                                                                           \
-        if (dual)                                                                                                  \
-            launch_grad_impl<Dual<T>, T, VV, NDD>(B, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, TE, smem,  \
-                                                  grid, st);                                                       \
-        else                                                                                                       \
-            launch_grad_impl<T, T, VV, NDD>(B, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, TE, smem, grid,  \
-                                            st);                                                                   \
+    int smem = 0;
+    for (int i = 0; i < ks.n; ++i) {
+        const int b = grad_smem(ks.host[i], V, nd, tile_width(ks.host[i], kind), dual);
+        smem = b > smem ? b : smem;
+    }
+    const int tiles = ks.tiles(kind);
+    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
+    const KTable<T> tab = ks.table();
+#define SDRT_GRAD(VV, NDD)                                                                                          \
+    do {                                                                                                            \
+        if (dual)                                                                                                   \
+            launch_grad_impl<Dual<T>, T, VV, NDD>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, smem,     \
+                                                  grid, st);                                                        \
+        else                                                                                                        \
+            launch_grad_impl<T, T, VV, NDD>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, smem, grid, st); \
     } while (0)
     if (system == SYS_ADVDIFF) {
         if (nd == 2) SDRT_GRAD(1, 2);
@@ -166,21 +178,28 @@ int launch_grad(const KBlock<T>& B, int system, int nd, const T* U, const T* dU,
 }
 
 template <typename T>
-int launch_residual_visc(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU,
+int launch_residual_visc(const KSet<T>& ks, int system, int riemann, int nd, const T* U, const T* dU,
                          const T* UFE, const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E,
-                         const KVisc<T>& Q, int TE, int grid, cudaStream_t st) {
+                         const KVisc<T>& Q, int nsm, cudaStream_t st) {
     const bool dual = dU != nullptr;
-    int rowsA = 0;
+    const int kind = dual ? TK_RES_DUAL : TK_RES;
+    if (!ks.all_tiled(kind)) return -2;
     const int V = system == SYS_ADVDIFF ? 1 : nd + 2;
-    const int smem = residual_smem(B, V, TE, dual, &rowsA);
+    int smem = 0;
+    for (int i = 0; i < ks.n; ++i) {
+        const int b = residual_smem(ks.host[i], V, tile_width(ks.host[i], kind), dual, nullptr);
+        smem = b > smem ? b : smem;
+    }
+    const int tiles = ks.tiles(kind);
+    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
+    const KTable<T> tab = ks.table();
 #define SDRT_RES(VV, NDD, SYSS, RIEE)                                                                             \
     do {                                                                                                          \
         if (dual)                                                                                                 \
-            launch_res_impl<Dual<T>, T, VV, NDD, SYSS, RIEE>(B, U, dU, UFE, dUFE, Ftot, P, E, Q, TE, rowsA, smem, \
-                                                             grid, st);                                           \
+            launch_res_impl<Dual<T>, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, grid,    \
+                                                             st);                                                 \
         else                                                                                                      \
-            launch_res_impl<T, T, VV, NDD, SYSS, RIEE>(B, U, dU, UFE, dUFE, Ftot, P, E, Q, TE, rowsA, smem, grid, \
-                                                       st);                                                       \
+            launch_res_impl<T, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, grid, st);     \
     } while (0)
     if (system == SYS_ADVDIFF) {
         if (nd == 2) SDRT_RES(1, 2, SYS_ADVDIFF, RIE_UPWIND);
@@ -203,17 +222,17 @@ int launch_residual_visc(const KBlock<T>& B, int system, int riemann, int nd, co
 
 template int grad_smem<float>(const KBlock<float>&, int, int, int, bool);
 template int grad_smem<double>(const KBlock<double>&, int, int, int, bool);
-template int launch_grad<float>(const KBlock<float>&, int, int, const float*, const float*, const float*,
-                                const float*, int64_t, const KPhys<float>&, float*, float*, float*, float*, int, int,
+template int launch_grad<float>(const KSet<float>&, int, int, const float*, const float*, const float*,
+                                const float*, int64_t, const KPhys<float>&, float*, float*, float*, float*, int,
                                 cudaStream_t);
-template int launch_grad<double>(const KBlock<double>&, int, int, const double*, const double*, const double*,
+template int launch_grad<double>(const KSet<double>&, int, int, const double*, const double*, const double*,
                                  const double*, int64_t, const KPhys<double>&, double*, double*, double*, double*,
-                                 int, int, cudaStream_t);
-template int launch_residual_visc<float>(const KBlock<float>&, int, int, int, const float*, const float*,
+                                 int, cudaStream_t);
+template int launch_residual_visc<float>(const KSet<float>&, int, int, int, const float*, const float*,
                                          const float*, const float*, int64_t, const KPhys<float>&,
-                                         const KEpi<float>&, const KVisc<float>&, int, int, cudaStream_t);
-template int launch_residual_visc<double>(const KBlock<double>&, int, int, int, const double*, const double*,
+                                         const KEpi<float>&, const KVisc<float>&, int, cudaStream_t);
+template int launch_residual_visc<double>(const KSet<double>&, int, int, int, const double*, const double*,
                                           const double*, const double*, int64_t, const KPhys<double>&,
-                                          const KEpi<double>&, const KVisc<double>&, int, int, cudaStream_t);
+                                          const KEpi<double>&, const KVisc<double>&, int, cudaStream_t);
 
 }  // namespace sdrt

@@ -10,7 +10,7 @@
 //   ub_fe,j  = (dF / du_own)^T H,
 //   ub_fiu,k = sum over the DOFs nu of point k of (d(S_axis . f) / du)^T Fb_nu,
 //   W^T J    = M0^T ub_fe + M12^T ub_fiu.
-// Two launches per block after the forward interpolation k_interp_ext:
+// Two launches (each over every block) after the forward interpolation k_interp_ext:
 //   k_vjp_face : GS_j = s_j G_j for every external point (UFE layout);
 //   k_vjp_elem : the flux Jacobians (V forward-mode dual evaluations per point,
 //                one per input variable, so the branch taken at ties of |.| and
@@ -24,14 +24,17 @@ namespace sdrt {
 
 // GS = s * (-(1/det J) M14^T W) at the external points of a tile.
 template <typename T, int V, int ND>
-__global__ void __launch_bounds__(256) k_vjp_face(KBlock<T> B, const T* __restrict__ W, T* __restrict__ GS,
-                                                  int64_t Ftot, int TE) {
+__global__ void __launch_bounds__(256) k_vjp_face(KTable<T> tab, const T* __restrict__ W, T* __restrict__ GS,
+                                                  int64_t Ftot) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* RW = reinterpret_cast<T*>(smem_raw);
-    const int NCOL = V * TE;
-    const int ntiles = (B.nelem + TE - 1) / TE;
     constexpr int ND2 = ND * ND;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int gt = blockIdx.x;; gt += gridDim.x) {
+        int bi, tile;
+        if (!locate(tab, TK_VJP, gt, bi, tile)) break;
+        const KBlock<T>& B = tab.blocks[bi];
+        const int TE = B.te_vjp;
+        const int NCOL = V * TE;
         const int e0 = tile * TE;
         __syncthreads();
         load_tile<T, T, V>(B, W, nullptr, e0, TE, RW);
@@ -56,20 +59,23 @@ __global__ void __launch_bounds__(256) k_vjp_face(KBlock<T> B, const T* __restri
 // Shared memory (columns (v, te)): RA = U, then W (nsol rows); RB = u_fiu,
 // then ub_fiu (nfiu rows); RC = Fb (nfi rows); RD = ub_fe (nfe rows).
 template <typename T, int V, int ND, int SYS, int RIE>
-__global__ void __launch_bounds__(256) k_vjp_elem(KBlock<T> B, const T* __restrict__ U, const T* __restrict__ W,
+__global__ void __launch_bounds__(256) k_vjp_elem(KTable<T> tab, const T* __restrict__ U, const T* __restrict__ W,
                                                   const T* __restrict__ UFE, const T* __restrict__ GS, int64_t Ftot,
-                                                  KPhys<T> P, T* __restrict__ out, int* flag, int TE) {
+                                                  KPhys<T> P, T* __restrict__ out, int* flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using D = Dual<T>;
-    const int NCOL = V * TE;
-    T* RA = reinterpret_cast<T*>(smem_raw);
-    T* RB = RA + (size_t)B.nsol * NCOL;
-    T* RC = RB + (size_t)B.nfiu * NCOL;
-    T* RD = RC + (size_t)B.nfi * NCOL;
-    const int ntiles = (B.nelem + TE - 1) / TE;
     constexpr int ND2 = ND * ND;
-    const int nfe_pad = (B.nfe + kMR - 1) / kMR * kMR;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int gt = blockIdx.x;; gt += gridDim.x) {
+        int bi, tile;
+        if (!locate(tab, TK_VJP, gt, bi, tile)) break;
+        const KBlock<T>& B = tab.blocks[bi];
+        const int TE = B.te_vjp;
+        const int NCOL = V * TE;
+        T* RA = reinterpret_cast<T*>(smem_raw);
+        T* RB = RA + (size_t)B.nsol * NCOL;
+        T* RC = RB + (size_t)B.nfiu * NCOL;
+        T* RD = RC + (size_t)B.nfi * NCOL;
+        const int nfe_pad = (B.nfe + kMR - 1) / kMR * kMR;
         const int e0 = tile * TE;
         __syncthreads();
         load_tile<T, T, V>(B, U, nullptr, e0, TE, RA);
@@ -195,33 +201,35 @@ int vjp_smem(const KBlock<T>& B, int V, int TE) {
     return (B.nsol + B.nfiu + B.nfi + B.nfe) * V * TE * (int)sizeof(T);
 }
 
-template <typename T, int V, int ND>
-static void launch_vjp_face_impl(const KBlock<T>& B, const T* W, T* GS, int64_t Ftot, int TE, int grid,
-                                 cudaStream_t st) {
-    const int sf = B.nsol * V * TE * (int)sizeof(T);
-    auto kf = k_vjp_face<T, V, ND>;
-    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
-    kf<<<grid, 256, sf, st>>>(B, W, GS, Ftot, TE);
-}
-
 template <typename T, int V, int ND, int SYS, int RIE>
-static void launch_vjp_elem_impl(const KBlock<T>& B, const T* U, const T* W, const T* UFE, const T* GS,
-                                 int64_t Ftot, const KPhys<T>& P, T* out, int* flag, int TE, int grid,
-                                 cudaStream_t st) {
-    const int se = vjp_smem(B, V, TE);
-    auto ke = k_vjp_elem<T, V, ND, SYS, RIE>;
-    cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
-    ke<<<grid, 256, se, st>>>(B, U, W, UFE, GS, Ftot, P, out, flag, TE);
+static void launch_vjp_pass(const KSet<T>& ks, int pass, const T* U, const T* W, const T* UFE, T* GS, int64_t Ftot,
+                            const KPhys<T>& P, T* out, int* flag, int nsm, cudaStream_t st) {
+    const int tiles = ks.tiles(TK_VJP);
+    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
+    const KTable<T> tab = ks.table();
+    int smem = 0;
+    for (int i = 0; i < ks.n; ++i) {
+        const int b = pass == 0 ? ks.host[i].nsol * V * ks.host[i].te_vjp * (int)sizeof(T)
+                                : vjp_smem(ks.host[i], V, ks.host[i].te_vjp);
+        smem = b > smem ? b : smem;
+    }
+    if (pass == 0) {
+        auto kf = k_vjp_face<T, V, ND>;
+        cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        kf<<<grid, 256, smem, st>>>(tab, W, GS, Ftot);
+    } else {
+        auto ke = k_vjp_elem<T, V, ND, SYS, RIE>;
+        cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        ke<<<grid, 256, smem, st>>>(tab, U, W, UFE, GS, Ftot, P, out, flag);
+    }
 }
 
 template <typename T>
-int launch_vjp(const KBlock<T>& B, int pass, int system, int riemann, int nd, const T* U, const T* W, const T* UFE,
-               T* GS, int64_t Ftot, const KPhys<T>& P, T* out, int* flag, int TE, int grid, cudaStream_t st) {
-#define SDRT_VJP(VV, NDD, SYSS, RIEE)                                                                           \
-    do {                                                                                                        \
-        if (pass == 0) launch_vjp_face_impl<T, VV, NDD>(B, W, GS, Ftot, TE, grid, st);                        \
-        else launch_vjp_elem_impl<T, VV, NDD, SYSS, RIEE>(B, U, W, UFE, GS, Ftot, P, out, flag, TE, grid, st); \
-    } while (0)
+int launch_vjp(const KSet<T>& ks, int pass, int system, int riemann, int nd, const T* U, const T* W, const T* UFE,
+               T* GS, int64_t Ftot, const KPhys<T>& P, T* out, int* flag, int nsm, cudaStream_t st) {
+    if (!ks.all_tiled(TK_VJP)) return -2;
+#define SDRT_VJP(VV, NDD, SYSS, RIEE) \
+    launch_vjp_pass<T, VV, NDD, SYSS, RIEE>(ks, pass, U, W, UFE, GS, Ftot, P, out, flag, nsm, st)
     if (system == SYS_ADVECTION) {
         if (nd == 2) SDRT_VJP(1, 2, SYS_ADVECTION, RIE_UPWIND);
         else SDRT_VJP(1, 3, SYS_ADVECTION, RIE_UPWIND);
@@ -243,10 +251,10 @@ int launch_vjp(const KBlock<T>& B, int pass, int system, int riemann, int nd, co
 
 template int vjp_smem<float>(const KBlock<float>&, int, int);
 template int vjp_smem<double>(const KBlock<double>&, int, int);
-template int launch_vjp<float>(const KBlock<float>&, int, int, int, int, const float*, const float*, const float*,
-                               float*, int64_t, const KPhys<float>&, float*, int*, int, int, cudaStream_t);
-template int launch_vjp<double>(const KBlock<double>&, int, int, int, int, const double*, const double*,
-                                const double*, double*, int64_t, const KPhys<double>&, double*, int*, int, int,
+template int launch_vjp<float>(const KSet<float>&, int, int, int, int, const float*, const float*, const float*,
+                               float*, int64_t, const KPhys<float>&, float*, int*, int, cudaStream_t);
+template int launch_vjp<double>(const KSet<double>&, int, int, int, int, const double*, const double*,
+                                const double*, double*, int64_t, const KPhys<double>&, double*, int*, int,
                                 cudaStream_t);
 
 }  // namespace sdrt

@@ -9,42 +9,65 @@
 
 namespace sdrt {
 
-// u_fe = M0 U for one block (V variables), written to UFE.
+// The blocks of a mesh for the generic kernels, which walk all blocks' tiles
+// in one launch per kernel kind: host copies (tile counts, shared-memory
+// sizes) and the same array in device memory.
 template <typename T>
-void launch_interp_ext(const KBlock<T>& B, int V, const T* U, T* UFE, int64_t Ftot, int TE, int grid,
-                       cudaStream_t st);
+struct KSet {
+    const KBlock<T>* host;
+    const KBlock<T>* dev;
+    int n;
+    KTable<T> table() const { return {dev, n}; }
+    int tiles(int kind) const {
+        int t = 0;
+        for (int i = 0; i < n; ++i) {
+            const int te = tile_width(host[i], kind);
+            if (te > 0) t += (host[i].nelem + te - 1) / te;
+        }
+        return t;
+    }
+    bool all_tiled(int kind) const {
+        for (int i = 0; i < n; ++i)
+            if (tile_width(host[i], kind) <= 0) return false;
+        return true;
+    }
+};
 
-// Residual of one block with a fused epilogue.  dU / dUFE non-null: JVP mode
-// (tangent of the residual written to E.out, E.mode must be EPI_STORE).
-// Returns -1 for an unsupported (system, riemann, nd) combination.
+// u_fe = M0 U for every block (V variables), written to UFE.  One launch.
+template <typename T>
+void launch_interp_ext(const KSet<T>& ks, int V, const T* U, T* UFE, int64_t Ftot, int nsm, cudaStream_t st);
+
+// Residual of every block with a fused epilogue, one launch.  dU / dUFE
+// non-null: JVP mode (tangent of the residual written to E.out, E.mode must be
+// EPI_STORE).  Returns -1 for an unsupported (system, riemann, nd)
+// combination, -2 if a block has no tile width for the mode.
 // Viscous systems read the flux-point gradients from Q (written by launch_grad).
 template <typename T>
-int launch_residual(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU, const T* UFE,
-                    const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int TE,
-                    int grid, cudaStream_t st);
+int launch_residual(const KSet<T>& ks, int system, int riemann, int nd, const T* U, const T* dU, const T* UFE,
+                    const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int nsm,
+                    cudaStream_t st);
 
 // The viscous instantiations of launch_residual (kernels_visc.cu).
 template <typename T>
-int launch_residual_visc(const KBlock<T>& B, int system, int riemann, int nd, const T* U, const T* dU,
+int launch_residual_visc(const KSet<T>& ks, int system, int riemann, int nd, const T* U, const T* dU,
                          const T* UFE, const T* dUFE, int64_t Ftot, const KPhys<T>& P, const KEpi<T>& E,
-                         const KVisc<T>& Q, int TE, int grid, cudaStream_t st);
+                         const KVisc<T>& Q, int nsm, cudaStream_t st);
 
-// Physical gradients of a viscous system at the flux points of one block
+// Physical gradients of a viscous system at the flux points of every block
 // (UFE must hold u_fe of every block): QFE / QFIU (kargs.hpp layout), and with
-// dU / dUFE non-null also their tangents dQFE / dQFIU.  Returns -1 for an
-// unsupported (system, nd) combination.
+// dU / dUFE non-null also their tangents dQFE / dQFIU.  One launch.  Returns
+// -1 for an unsupported (system, nd) combination, -2 without tile widths.
 template <typename T>
-int launch_grad(const KBlock<T>& B, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
-                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int TE, int grid,
-                cudaStream_t st);
+int launch_grad(const KSet<T>& ks, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
+                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int nsm, cudaStream_t st);
 
-// Vector-Jacobian product of the inviscid residual for one block (kernels_vjp.cu).
-// pass 0: GS (UFE layout) = s G at the block's external points from W;
-// pass 1 (after pass 0 of every block): out = W^T dR/dU, with UFE = u_fe of
-// every block.  Returns -1 for an unsupported combination.
+// Vector-Jacobian product of the inviscid residual, every block in one launch
+// per pass (kernels_vjp.cu).  pass 0: GS (UFE layout) = s G at the external
+// points from W; pass 1: out = W^T dR/dU, with UFE = u_fe of every block.
+// Returns -1 for an unsupported combination, -2 without tile widths.
 template <typename T>
-int launch_vjp(const KBlock<T>& B, int pass, int system, int riemann, int nd, const T* U, const T* W, const T* UFE,
-               T* GS, int64_t Ftot, const KPhys<T>& P, T* out, int* flag, int TE, int grid, cudaStream_t st);
+int launch_vjp(const KSet<T>& ks, int pass, int system, int riemann, int nd, const T* U, const T* W, const T* UFE,
+               T* GS, int64_t Ftot, const KPhys<T>& P, T* out, int* flag, int nsm, cudaStream_t st);
 template <typename T>
 int vjp_smem(const KBlock<T>& B, int V, int TE);
 
