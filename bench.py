@@ -456,6 +456,12 @@ def main():
     U = torch.from_numpy(host).to(f"cuda:{local}")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
     dt = spec.dt
+    infos = [sdrt.sdrt_get_etype_info(ctx.ptr, et) for et in M.etypes]
+    rec = record_path(infos, spec.system, spec.riemann)
+    if not rec:
+        M.autotune(U, reps=3)          # tile widths of the generic kernels, per block (untimed)
+    tiles = {f"{b['shape']}_p{p}_{i}": {k: v for k, v in t.items() if k in ("residual", "gradient")}
+             for i, (b, p, t) in enumerate(zip(spec.mesh["blocks"], spec.degrees, M.tiles()))}
 
     for i in range(args.warmup):
         flush.fill_(float(i))
@@ -491,8 +497,6 @@ def main():
     # Roofline of the dominant kernel kind (live CUDA-event durations inside the
     # timed region against its algorithmic bytes).
     s = 4 if args.precision == "fp32" else 8
-    infos = [sdrt.sdrt_get_etype_info(ctx.ptr, et) for et in M.etypes]
-    rec = record_path(infos, spec.system, spec.riemann)
     viscous = spec.system in ("advdiff", "ns")
     names = dict(KERNEL_NAMES[rec])
     if rec and args.tc_div and args.precision == "fp32":
@@ -559,6 +563,7 @@ def main():
                            "system": spec.system, "riemann": spec.riemann, "nvar": spec.nvar, "ndof": ndof,
                            "dt": dt, "residuals_per_step": 4, "precision": args.precision,
                            "path": "record" if rec else "generic",
+                           "tiles": None if rec else tiles,
                            "tc_divergence": args.tc_div, "tc_interpolation": args.tc_interp,
                            "l2": "flushed between timed steps (256 MiB write, untimed)",
                            "parallelism": f"replicas x{world}"},

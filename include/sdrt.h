@@ -229,6 +229,22 @@ int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* V_dev, v
  * mesh's face-state buffers (allocated on first use). */
 int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* W_dev, void* JTW_dev);
 
+/* Tile autotuner of the generic kernels (every element type other than the
+ * register-blocked tetrahedra of degree 3 and 4, which have fixed tiles): for
+ * each block in turn, times `reps` residual evaluations of the whole mesh at
+ * U_dev (device state, not modified) for tile widths of 4..64 elements that
+ * fit in shared memory, and keeps the fastest (the residual kernel's tile,
+ * and for the viscous systems the gradient kernel's).  Results are bit-for-bit
+ * the same for every tile width (tiles only partition the elements).  Drops
+ * the mesh's captured RK4 graph.  Synchronises the stream; allocates a
+ * temporary residual array. */
+int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U_dev, int reps);
+
+/* Tile widths (elements per CTA tile) of one block's generic kernels:
+ * out[6] = {interpolation, residual, residual JVP, gradient, gradient JVP,
+ * VJP}; 0 = not available for this block. */
+int sdrt_get_tiles(sdrt_ctx* ctx, int mesh_id, int block, int32_t* out);
+
 /* Synchronise the context's stream; returns SDRT_ERR_NONFINITE (and clears the
  * flag) if a kernel wrote NaN / Inf into a residual since the last sync. */
 int sdrt_sync(sdrt_ctx* ctx);

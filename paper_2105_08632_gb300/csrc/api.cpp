@@ -490,6 +490,23 @@ int check_compute(sdrt_ctx* ctx, int mesh_id) {
     return SDRT_OK;
 }
 
+// (Re)builds the block tables of the generic kernels from the mesh blocks.
+int refresh_tables(sdrt_ctx* ctx, Mesh& m) {
+    m.kb_f.clear();
+    m.kb_d.clear();
+    const bool f32 = m.phys.precision == SDRT_FP32;
+    for (auto& bp : m.blocks) {
+        const EType& et = *ctx->etypes[bp->etype];
+        if (f32) m.kb_f.push_back(make_kblock<float>(et, *bp));
+        else m.kb_d.push_back(make_kblock<double>(et, *bp));
+    }
+    if (!ctx->host_only) {
+        if (f32) SDRT_CUDA(upload(m.kb_dev, m.kb_f));
+        else SDRT_CUDA(upload(m.kb_dev, m.kb_d));
+    }
+    return SDRT_OK;
+}
+
 int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
     const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
     if (!m.ufe.p) SDRT_CUDA(m.ufe.alloc((size_t)m.nvar * m.Ftot * es));
@@ -981,15 +998,7 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
         }
     }
     // Block tables of the generic kernels (tile widths are final here).
-    for (auto& bp : m->blocks) {
-        const EType& et = *ctx->etypes[bp->etype];
-        if (f32) m->kb_f.push_back(make_kblock<float>(et, *bp));
-        else m->kb_d.push_back(make_kblock<double>(et, *bp));
-    }
-    if (!ctx->host_only) {
-        if (f32) SDRT_CUDA(upload(m->kb_dev, m->kb_f));
-        else SDRT_CUDA(upload(m->kb_dev, m->kb_d));
-    }
+    if (int rt = refresh_tables(ctx, *m)) return rt;
     ctx->meshes.push_back(std::move(m));
     *mesh_id = (int)ctx->meshes.size() - 1;
     return SDRT_OK;
@@ -1205,6 +1214,88 @@ int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW
                               static_cast<float*>(JTW));
     return run_vjp<double>(ctx, m, static_cast<const double*>(U), static_cast<const double*>(W),
                            static_cast<double*>(JTW));
+}
+
+int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (!U || reps < 1) return fail(ctx, SDRT_ERR_ARG, "null state or reps < 1");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (m.fast) return SDRT_OK;                 // the record-path kernels have fixed tiles
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
+    DevBuf R;
+    SDRT_CUDA(R.alloc((size_t)m.state_len * es));
+    cudaEvent_t a, b;
+    SDRT_CUDA(cudaEventCreate(&a));
+    SDRT_CUDA(cudaEventCreate(&b));
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    // Time `reps` residual evaluations of the whole mesh (ms per evaluation).
+    auto timed = [&](float* ms) -> int {
+        int rr;
+        if ((rr = sdrt_residual(ctx, mesh_id, U, R.p))) return rr;    // warm-up (and attribute setup)
+        SDRT_CUDA(cudaEventRecord(a, ctx->stream));
+        for (int i = 0; i < reps; ++i)
+            if ((rr = sdrt_residual(ctx, mesh_id, U, R.p))) return rr;
+        SDRT_CUDA(cudaEventRecord(b, ctx->stream));
+        SDRT_CUDA(cudaEventSynchronize(b));
+        SDRT_CUDA(cudaEventElapsedTime(ms, a, b));
+        *ms /= reps;
+        return SDRT_OK;
+    };
+    const bool visc = viscous(m);
+    int rc = SDRT_OK;
+    // Coordinate descent over the blocks: residual tile, then (viscous) gradient tile.
+    for (auto& bp : m.blocks) {
+        const RefElement& RE = ctx->etypes[bp->etype]->R;
+        const EType& et = *ctx->etypes[bp->etype];
+        for (int which = 0; which < (visc ? 2 : 1) && rc == SDRT_OK; ++which) {
+            int& tile = which == 0 ? bp->tile : bp->gtile;
+            const int keep = tile;
+            int best = keep;
+            float best_ms = 1e30f;
+            for (int te : {4, 8, 16, 32, 64}) {
+                const size_t smem = which == 0
+                                        ? (size_t)(std::max(RE.nsol, RE.nfi) + et.Mi) * m.nvar * te * es
+                                        : (size_t)(RE.nsol + RE.nfe + m.nd * RE.nsol) * m.nvar * te * es;
+                if (smem > 220 * 1024) continue;
+                tile = te;
+                if ((rc = refresh_tables(ctx, m))) break;
+                float ms = 0;
+                if ((rc = timed(&ms))) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = te;
+                }
+            }
+            tile = rc == SDRT_OK ? best : keep;
+            if (int rt = refresh_tables(ctx, m)) rc = rc ? rc : rt;
+        }
+        if (rc) break;
+    }
+    ctx->prof = prof;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (m.graph) {
+        cudaGraphExecDestroy(m.graph);
+        m.graph = nullptr;
+    }
+    // Non-finite values of the tuning state are not the caller's concern.
+    cudaStreamSynchronize(ctx->stream);
+    cudaMemset(ctx->flag.p, 0, sizeof(int));
+    return rc;
+}
+
+int sdrt_get_tiles(sdrt_ctx* ctx, int mesh_id, int block, int32_t* out) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    const Mesh& m = *ctx->meshes[mesh_id];
+    if (!out || block < 0 || block >= (int)m.blocks.size()) return fail(ctx, SDRT_ERR_ARG, "bad block or output");
+    const MBlock& b = *m.blocks[block];
+    const int32_t v[6] = {32, b.tile, b.tile_dual, b.gtile, b.gtile_dual, b.vtile};
+    for (int i = 0; i < 6; ++i) out[i] = v[i];
+    return SDRT_OK;
 }
 
 int sdrt_sync(sdrt_ctx* ctx) {

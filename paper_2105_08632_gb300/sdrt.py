@@ -25,7 +25,8 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_get_etype_info", "sdrt_get_operator", "sdrt_setup_mesh", "sdrt_get_mesh_info",
             "sdrt_get_block_layout", "sdrt_get_sol_points", "sdrt_get_face_map", "sdrt_residual",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
-            "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option"]
+            "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option",
+            "sdrt_autotune", "sdrt_get_tiles"]
 
 
 class SdrtError(RuntimeError):
@@ -108,6 +109,8 @@ def lib():
         "sdrt_profile_collect": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "sdrt_residual_noalloc": (I, [P, I, P, P]),
         "sdrt_set_option": (I, [P, I, I]),
+        "sdrt_autotune": (I, [P, I, P, I]),
+        "sdrt_get_tiles": (I, [P, I, I, ctypes.POINTER(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -262,6 +265,19 @@ def sdrt_launch_count(ctx):
 
 SDRT_OPT_TENSOR_CORES = 0
 SDRT_OPT_TC_DIVERGENCE = 1
+
+
+def sdrt_autotune(ctx, mesh, U, reps=3):
+    _check(ctx, lib().sdrt_autotune(ctx, int(mesh), _ptr(U), int(reps)))
+
+
+TILE_KINDS = ("interp", "residual", "residual_jvp", "gradient", "gradient_jvp", "vjp")
+
+
+def sdrt_get_tiles(ctx, mesh, block):
+    out = (ctypes.c_int32 * 6)()
+    _check(ctx, lib().sdrt_get_tiles(ctx, int(mesh), int(block), out))
+    return dict(zip(TILE_KINDS, list(out)))
 
 
 def sdrt_set_option(ctx, option, value):
@@ -423,6 +439,13 @@ class Mesh:
     def vjp(self, U, W, JTW):
         self._check(U, W, JTW)
         sdrt_vjp(self.ctx.ptr, self.id, U, W, JTW)
+
+    def autotune(self, U, reps=3):
+        self._check(U)
+        sdrt_autotune(self.ctx.ptr, self.id, U, reps)
+
+    def tiles(self):
+        return [sdrt_get_tiles(self.ctx.ptr, self.id, b) for b in range(self.info["nblocks"])]
 
     def sync(self):
         sdrt_sync(self.ctx.ptr)
