@@ -98,6 +98,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+// L2 prefetch of one box of a 2D tensor (no shared memory involved).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -505,7 +512,9 @@ __global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, 1) k_interp_pip
 // Flux and divergence of one tile staged in shared memory (value path).
 template <typename T, int V, int ND, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW>
 __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __restrict__ REC,
-                                                      const T* __restrict__ FIUR, KPhys<T> P, KEpi<T> E) {
+                                                      const T* __restrict__ FIUR, KPhys<T> P, KEpi<T> E,
+                                                      const __grid_constant__ CUtensorMap u0map,
+                                                      const __grid_constant__ CUtensorMap accmap, int prefetch) {
     static_assert(NFE % G == 0, "external points must split evenly across the G threads");
     constexpr int EPW = 32 / G;
     constexpr int TE = NW * EPW;
@@ -571,6 +580,9 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
             bulk_g2s(fiu, FIUR + B.fiur_base + (size_t)e0 * B.frs, (uint32_t)(n * B.frs * sizeof(T)), bar);
             bulk_g2s(met, B.maos + (size_t)e0 * B.nmp, (uint32_t)(n * B.nmp * sizeof(T)), bar);
             bulk_g2s(prm, B.perm + (size_t)e0 * B.pstride, (uint32_t)(n * B.pstride), bar);
+            // The stage-update inputs of this tile's epilogue, into L2 while the fluxes are computed.
+            if (prefetch & 1) tma_prefetch_2d(&u0map, e0, 0);
+            if (prefetch & 2) tma_prefetch_2d(&accmap, e0, 0);
         }
         for (int t = threadIdx.x; t < n * NFACE; t += blockDim.x) {
             const int le = t / NFACE, f = t % NFACE;
@@ -806,6 +818,41 @@ __global__ void __launch_bounds__(32 * V, 4) k_flux_rec_dual(KBlock<T> B, const 
 
 namespace {
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of one block's state matrix: rows (rho, v), columns the padded
+// elements (ld); boxes of te x nrow.
+template <typename T>
+static bool encode_state_map(CUtensorMap* map, const T* base, uint64_t ld, uint64_t nrow, uint32_t te) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * sizeof(T)) % 16 != 0 || nrow > 256 ||
+        te > 256 || (te * sizeof(T)) % 16 != 0)
+        return false;
+    const cuuint64_t dims[2] = {ld, nrow};
+    const cuuint64_t strides[1] = {ld * sizeof(T)};
+    const cuuint32_t box[2] = {te, (cuuint32_t)nrow};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapDataType dt =
+        sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return enc(map, dt, 2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename K>
 int blocks_per_sm(K kernel, int threads, int smem) {
     int n = 0;
@@ -854,7 +901,16 @@ void flux_rec_impl(const KBlock<T>& B, const T* REC, const T* FIUR, const KPhys<
     const int per = blocks_per_sm(k, 32 * NW, (int)smem);
     const int need = (B.nelem + TE - 1) / TE;
     const int grid = need < nsm * per ? need : nsm * per;
-    k<<<grid, 32 * NW, smem, st>>>(B, REC, FIUR, P, E);
+    // L2 prefetch maps of the epilogue's stage inputs (u0 in stages 1-3, uacc in 2-4).
+    CUtensorMap u0map{}, accmap{};
+    int prefetch = 0;
+    const uint64_t nrow = (uint64_t)NS * V;
+    if ((E.mode == EPI_RK_FIRST || E.mode == EPI_RK_MID) && encode_state_map(&u0map, E.u0 + B.u_off, B.ld, nrow, TE))
+        prefetch |= 1;
+    if ((E.mode == EPI_RK_MID || E.mode == EPI_RK_LAST) &&
+        encode_state_map(&accmap, (const T*)E.uacc + B.u_off, B.ld, nrow, TE))
+        prefetch |= 2;
+    k<<<grid, 32 * NW, smem, st>>>(B, REC, FIUR, P, E, u0map, accmap, prefetch);
 }
 
 template <typename T>
@@ -889,36 +945,6 @@ bool fast_path_available(int shape, int nsol, int nd, int system, int riemann) {
     if (nsol != 20 && nsol != 35) return false;
     if (system == SYS_ADVECTION) return true;
     return system == SYS_EULER && riemann == RIE_RUSANOV;
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// dependency on the driver library).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// Tensor map of one block's FP32 state matrix: rows (rho, v), columns the
-// padded elements (ld); boxes of te x nrow.
-static bool encode_state_map(CUtensorMap* map, const float* base, uint64_t ld, uint64_t nrow, uint32_t te) {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld * sizeof(float)) % 16 != 0) return false;
-    const cuuint64_t dims[2] = {ld, nrow};
-    const cuuint64_t strides[1] = {ld * sizeof(float)};
-    const cuuint32_t box[2] = {te, (cuuint32_t)nrow};
-    const cuuint32_t estr[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int NS, int V, int NFE, int NFIU, int TE, int GR, bool ALLV>
