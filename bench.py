@@ -499,6 +499,8 @@ def main():
     s = 4 if args.precision == "fp32" else 8
     viscous = spec.system in ("advdiff", "ns")
     names = dict(KERNEL_NAMES[rec])
+    if rec and args.precision == "fp32":
+        names["interp_ext"] = "k_interp_pipe"       # TMA-fed pipeline (FP32); FP64 keeps k_interp_rec
     if rec and args.tc_div and args.precision == "fp32":
         names["residual"] = "k_flux_tc"
     if rec and args.tc_interp and args.precision == "fp32":
