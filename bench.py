@@ -260,14 +260,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Sources the record-path kernels (k_interp_pipe, k_flux_rec) and their
+# record layouts are built from; a change to any of them makes the committed
+# ncu counters stale.
+RECORD_PATH_SOURCES = ("api.cpp", "device_math.cuh", "flux_rec.cuh", "kargs.hpp", "kernels_fast.cu", "launch.hpp")
+
+
 def kernel_sources_sha():
-    """Hash of every CUDA source of the library (identifies the kernel build)."""
+    """Hash of the record-path kernel sources (identifies the profiled build)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2105_08632_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".hpp")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in RECORD_PATH_SOURCES:
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
