@@ -209,6 +209,97 @@ __device__ __forceinline__ void epi_block(const KEpi<T>& E, const T (&acc)[RS][V
     if (bad) *E.flag = 1;
 }
 
+// Divergence accumulators of one thread: RS rows x V variables.
+template <typename T, int RS, int V>
+struct ScalarAcc {
+    T a[RS][V];
+    __device__ __forceinline__ void zero() {
+        #pragma unroll
+        for (int i = 0; i < RS; ++i)
+            #pragma unroll
+            for (int v = 0; v < V; ++v) a[i][v] = T(0);
+    }
+    // a[i][v] += x[i] F[v]
+    __device__ __forceinline__ void add(const T* x, const T* F) {
+        #pragma unroll
+        for (int i = 0; i < RS; ++i)
+            #pragma unroll
+            for (int v = 0; v < V; ++v) a[i][v] = fma(x[i], F[v], a[i][v]);
+    }
+    __device__ __forceinline__ T get(int i, int v) const { return a[i][v]; }
+};
+
+// The same sums on the paired FP32 FMA of sm_100 and later (__ffma2_rn: two
+// IEEE round-to-nearest fmas per instruction, so every sum is bit-identical to
+// the scalar one).  Row pairs (r0, r1) = (2p, 2p+1) and variable pairs (v, v+1)
+// are accumulated crosswise, D = (r0 v, r1 v+1) += (x_r0, x_r1) (F_v, F_v+1) and
+// X = (r0 v+1, r1 v) += (x_r0, x_r1) (F_v+1, F_v), so that both operands are
+// plain register pairs; an odd last variable or row takes a broadcast pair.
+template <int RS, int V>
+struct PairAcc {
+    static constexpr int RP = RS / 2, VP = V / 2;
+    static constexpr bool ODD_R = RS % 2 != 0, ODD_V = V % 2 != 0;
+    static constexpr int RPX = RP > 0 ? RP : 1, VPX = VP > 0 ? VP : 1;
+    float2 d[RPX][VPX], x[RPX][VPX];
+    float2 dl[RPX];      // odd V: (r0 V-1, r1 V-1)
+    float2 rl[VPX];      // odd RS: (RS-1 v, RS-1 v+1)
+    float rll;           // odd RS and odd V
+    __device__ __forceinline__ void zero() {
+        const float2 z = make_float2(0.f, 0.f);
+        #pragma unroll
+        for (int p = 0; p < RPX; ++p) {
+            dl[p] = z;
+            #pragma unroll
+            for (int w = 0; w < VPX; ++w) d[p][w] = x[p][w] = z;
+        }
+        #pragma unroll
+        for (int w = 0; w < VPX; ++w) rl[w] = z;
+        rll = 0.f;
+    }
+    __device__ __forceinline__ void add(const float* xr, const float* F) {
+        float2 P[VPX], Q[VPX];
+        #pragma unroll
+        for (int w = 0; w < VP; ++w) {
+            P[w] = make_float2(F[2 * w], F[2 * w + 1]);
+            Q[w] = make_float2(F[2 * w + 1], F[2 * w]);
+        }
+        #pragma unroll
+        for (int p = 0; p < RP; ++p) {
+            const float2 X = make_float2(xr[2 * p], xr[2 * p + 1]);
+            #pragma unroll
+            for (int w = 0; w < VP; ++w) {
+                d[p][w] = __ffma2_rn(X, P[w], d[p][w]);
+                x[p][w] = __ffma2_rn(X, Q[w], x[p][w]);
+            }
+            if constexpr (ODD_V) dl[p] = __ffma2_rn(X, make_float2(F[V - 1], F[V - 1]), dl[p]);
+        }
+        if constexpr (ODD_R) {
+            const float2 X = make_float2(xr[RS - 1], xr[RS - 1]);
+            #pragma unroll
+            for (int w = 0; w < VP; ++w) rl[w] = __ffma2_rn(X, P[w], rl[w]);
+            if constexpr (ODD_V) rll = fmaf(xr[RS - 1], F[V - 1], rll);
+        }
+    }
+    // Called with indices known at compile time (fully unrolled loops).
+    __device__ __forceinline__ float get(int i, int v) const {
+        if (i < 2 * RP) {
+            const int p = i >> 1;
+            const bool r0 = (i & 1) == 0;
+            if (v < 2 * VP) {
+                const int w = v >> 1;
+                if ((v & 1) == 0) return r0 ? d[p][w].x : x[p][w].y;
+                return r0 ? x[p][w].x : d[p][w].y;
+            }
+            return r0 ? dl[p].x : dl[p].y;
+        }
+        if (v < 2 * VP) return (v & 1) == 0 ? rl[v >> 1].x : rl[v >> 1].y;
+        return rll;
+    }
+};
+
+template <typename T, int RS, int V> struct DivAcc { using type = ScalarAcc<T, RS, V>; };
+template <int RS, int V> struct DivAcc<float, RS, V> { using type = PairAcc<RS, V>; };
+
 // 16-byte shared-memory vector of T.
 template <typename T> struct Vec16;
 template <> struct Vec16<float> {
@@ -601,24 +692,14 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
         const T* part_e = part + (size_t)le * B.ers;
         const T* met_e = met + (size_t)le * B.nmp;
         const unsigned char* prm_e = prm + (size_t)le * B.pstride;
-        T acc[RS][V];
-        #pragma unroll
-        for (int i = 0; i < RS; ++i)
-            #pragma unroll
-            for (int v = 0; v < V; ++v) acc[i][v] = T(0);
+        typename DivAcc<T, RS, V>::type acc;
+        acc.zero();
         auto accumulate = [&](int j, const T* F) {
             const VT* a = reinterpret_cast<const VT*>(As + ((size_t)j * G + h) * RSP);
+            T x[RSP];
             #pragma unroll
-            for (int r = 0; r < RSP; r += VN) {
-                T x[VN];
-                Vec16<T>::get(a[r / VN], x);
-                #pragma unroll
-                for (int q = 0; q < VN; ++q)
-                    if (r + q < RS) {
-                        #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[r + q][v] = fma(x[q], F[v], acc[r + q][v]);
-                    }
-            }
+            for (int r = 0; r < RSP; r += VN) Vec16<T>::get(a[r / VN], x + r);
+            acc.add(x, F);
         };
         // Accumulate the G fluxes of one round: thread h holds the flux of point
         // base + h; the value of thread h ^ m arrives with one xor-shuffle and
@@ -712,7 +793,12 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
         if (valid) {
             const int e = e0 + el;
             const T inv = -met_e[0];
-            epi_block<RS, V>(E, acc, inv, (size_t)B.u_off + e, B.ld, h * RS, NS);
+            T out[RS][V];
+            #pragma unroll
+            for (int i = 0; i < RS; ++i)
+                #pragma unroll
+                for (int v = 0; v < V; ++v) out[i][v] = acc.get(i, v);
+            epi_block<RS, V>(E, out, inv, (size_t)B.u_off + e, B.ld, h * RS, NS);
         }
         fence_proxy_async();  // this thread's reads of the tile precede the next tile's async copies
         __syncthreads();      // the tile buffers are free for the next tile's copies
