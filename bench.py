@@ -187,16 +187,19 @@ def record_path(infos, system, riemann):
     return ok_sys and all(i["ndim"] == 3 and i["nfaces"] == 4 and i["nsol"] in (20, 35) for i in infos)
 
 
-def algorithmic_bytes(info, nelem, nvar, s, record, viscous):
-    """Algorithmic bytes of one RK4 stage per kernel kind for one block
-    (padding excluded; the stage update is averaged over the 4 stages in
-    state volumes N_s V s: stage 1 reads u0 and writes two arrays = 3, stages
-    2-3 read two and write two = 4, stage 4 reads one and writes one = 2 ->
-    13 / 4 = 3.25).
+def algorithmic_bytes(info, nelem, nvar, s, record, viscous, fused=False):
+    """Algorithmic bytes of one RK4 step per kernel kind for one block
+    (padding excluded).  Stage updates in state volumes N_s V s: stage 1 reads
+    u0 and writes uacc and the next state = 3, stages 2-3 read u0, uacc and
+    write two = 4, stage 4 reads uacc and writes U = 2 -> 13 per step.
 
-    record path   k_interp_rec : read U, write external + internal point states
+    record path   k_interp_*   : read U, write external + internal point states
                   k_flux_rec   : own + partner external states, internal states,
                                  metric, permutation, partner offsets, stage update
+                  fused        : one interpolation per step; stages 1-3 keep the
+                                 next state on chip (no write of it: 10 volumes
+                                 per step) and write its external + internal
+                                 point states instead
     generic path  k_interp_ext : read U, write external point states
                   k_grad       : read U, own + partner external states, write the
                                  physical gradients at all flux points (viscous)
@@ -207,15 +210,19 @@ def algorithmic_bytes(info, nelem, nvar, s, record, viscous):
     ns, nfe, nfiu, nf, nd = info["nsol"], info["nfe"], info["nfiu"], info["nfaces"], info["ndim"]
     V = nvar
     metric = (1 + nd * nd + nf * (nd + 1)) * s
-    upd = 3.25 * ns * V * s
+    vol = ns * V * s
     if record:
-        return {"interp_ext": (ns + nfe + nfiu) * V * s * nelem,
-                "residual": ((2 * nfe + nfiu) * V * s + metric + nfe + 4 * nf + upd) * nelem}
-    out = {"interp_ext": (ns + nfe) * V * s * nelem,
-           "residual": ((ns + nfe) * V * s + metric + 4 * nfe + upd) * nelem}
+        points = (ns + nfe + nfiu) * V * s
+        flux = (2 * nfe + nfiu) * V * s + metric + nfe + 4 * nf
+        if fused:
+            return {"interp_ext": points * nelem,
+                    "residual": (4 * flux + 10 * vol + 3 * (nfe + nfiu) * V * s) * nelem}
+        return {"interp_ext": 4 * points * nelem, "residual": (4 * flux + 13 * vol) * nelem}
+    out = {"interp_ext": 4 * (ns + nfe) * V * s * nelem,
+           "residual": (4 * ((ns + nfe) * V * s + metric + 4 * nfe) + 13 * vol) * nelem}
     if viscous:
-        out["residual"] += (2 * nd * nfe + nd * nfiu) * V * s * nelem
-        out["gradient"] = ((ns + 2 * nfe) * V * s + nd * (nfe + nfiu) * V * s + metric + 4 * nfe) * nelem
+        out["residual"] += 4 * (2 * nd * nfe + nd * nfiu) * V * s * nelem
+        out["gradient"] = 4 * ((ns + 2 * nfe) * V * s + nd * (nfe + nfiu) * V * s + metric + 4 * nfe) * nelem
     return out
 
 
@@ -472,17 +479,37 @@ def main():
         flush.fill_(float(i))
         M.rk4_step(U, dt, 1)
     M.sync()
-    sdrt.sdrt_profile_enable(ctx.ptr, True)
     sampler = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     launches0 = sdrt.sdrt_launch_count(ctx.ptr)
-    prof = {k: [0.0, 0] for k in sdrt.KERNEL_KINDS}
-    step_ms = []
+    events = []
     for i in range(args.steps):
         flush.fill_(float(i))                      # evict L2 (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        M.rk4_step(U, dt, 1)
+        e1.record(stream)
+        events.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = sdrt.sdrt_launch_count(ctx.ptr) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    total_ms, ms_per_step, value = aggregate(float(np.sum(step_ms)), args.steps, ndof, dist, f"cuda:{local}")
+
+    # Per-kernel durations: the same number of steps again with an event pair
+    # around every launch inside the step's graph.  Event-record nodes between
+    # the kernels lengthen the step, so `value` comes from the pass above.
+    sdrt.sdrt_profile_enable(ctx.ptr, True)
+    flush.fill_(0.0)
+    M.rk4_step(U, dt, 1)                           # graph capture with the event nodes (untimed)
+    sdrt.sdrt_profile_collect(ctx.ptr)
+    prof = {k: [0.0, 0] for k in sdrt.KERNEL_KINDS}
+    inst_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -491,13 +518,12 @@ def main():
         for k, (ms, n) in sdrt.sdrt_profile_collect(ctx.ptr).items():   # synchronises
             prof[k][0] += ms
             prof[k][1] += n
-        step_ms.append(e0.elapsed_time(e1))
+        inst_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
-    launches = sdrt.sdrt_launch_count(ctx.ptr) - launches0
     clocks = sampler.stop()
     sdrt.sdrt_profile_enable(ctx.ptr, False)
     M.sync()
-    total_ms, ms_per_step, value = aggregate(float(np.sum(step_ms)), args.steps, ndof, dist, f"cuda:{local}")
+    inst_total = float(np.sum(inst_ms))
 
     # Roofline of the dominant kernel kind (live CUDA-event durations inside the
     # timed region against its algorithmic bytes).
@@ -510,20 +536,23 @@ def main():
         names["residual"] = "k_flux_tc"
     if rec and args.tc_interp and args.precision == "fp32":
         names["interp_ext"] = "k_interp_tc"
-    per_stage = {}
+    # One interpolation launch per block and step: the RK4 stages interpolate
+    # the next stage's state in their update (SDRT_OPT_FUSED_RK).
+    fused = bool(rec and prof["interp_ext"][1] == args.steps * len(M.layouts))
+    per_step = {}
     for info, lay in zip(infos, M.layouts):
-        for k, b in algorithmic_bytes(info, lay["nelem"], spec.nvar, s, rec, viscous).items():
-            per_stage[k] = per_stage.get(k, 0.0) + b
+        for k, b in algorithmic_bytes(info, lay["nelem"], spec.nvar, s, rec, viscous, fused).items():
+            per_step[k] = per_step.get(k, 0.0) + b
     peak, peak_kind = peaks()
-    stages = 4 * args.steps
     kinds = {}
-    for k, b in per_stage.items():
+    for k, b in per_step.items():
         ms_k, n_k = prof[k]
-        kinds[names[k]] = {"algorithmic_bytes_per_stage": b, "launches": n_k, "total_ms": ms_k,
+        kinds[names[k]] = {"algorithmic_bytes_per_step": b, "launches": n_k, "total_ms": ms_k,
                            "avg_launch_ms": ms_k / max(n_k, 1),
-                           "achieved_gbs": b * stages / (ms_k / 1e3) / 1e9 if n_k else None,
-                           "step_share": ms_k / max(total_ms, 1e-9) if not dist else None}
-    dom = max(per_stage, key=lambda k: prof[k][0])
+                           "algorithmic_bytes_per_launch": b * args.steps / max(n_k, 1),
+                           "achieved_gbs": b * args.steps / (ms_k / 1e3) / 1e9 if n_k else None,
+                           "step_share": ms_k / max(inst_total, 1e-9)}
+    dom = max(per_step, key=lambda k: prof[k][0])
     dk = kinds[names[dom]]
     achieved = dk["achieved_gbs"]
     traffic = ncu_traffic() if (args.workload == "euler" and not args.ncell and rec and not args.tc_div) else None
@@ -531,11 +560,15 @@ def main():
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                                 else "of fallback"),
-                "algorithmic_bytes_per_launch": dk["algorithmic_bytes_per_stage"] / max(len(M.layouts), 1),
+                "algorithmic_bytes_per_launch": dk["algorithmic_bytes_per_launch"],
                 "avg_launch_ms": dk["avg_launch_ms"],
                 "kernel_sources_sha256_16": kernel_sources_sha(),
                 "kernels": kinds,
-                "step_hbm_frac": (sum(per_stage.values()) * 4 / (ms_per_step / 1e3) / 1e9) / peak}
+                "timing": "kernel durations from a second pass of the same steps with per-launch events "
+                          "inside the graph (ms_per_step there: %.4f); value and ms_per_step from the pass "
+                          "without them" % (inst_total / max(args.steps, 1)),
+                "fused_rk_stages": fused,
+                "step_hbm_frac": (sum(per_step.values()) / (ms_per_step / 1e3) / 1e9) / peak}
 
     # End to end through the host-buffer entry point (pinned memory).
     pin_in = torch.from_numpy(host).pin_memory()

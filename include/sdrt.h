@@ -204,7 +204,11 @@ int sdrt_residual_noalloc(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R
 
 /* nsteps classical RK4 steps of size dt, in place on U_dev (device).  Each
  * stage is one residual evaluation fused with its stage update (paper Sec. 2.1
- * explicit RK; RK4 stability polynomial Eq. "rk_exponential"). */
+ * explicit RK; RK4 stability polynomial Eq. "rk_exponential").  With
+ * SDRT_OPT_FUSED_RK on (default) and an FP32 Euler mesh of degree-3
+ * tetrahedra, stages 1-3 also interpolate the next stage's state to the flux
+ * points in their epilogue, so one step is one interpolation and four flux
+ * kernels and the stage states stay on chip. */
 int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U_dev, double dt, int nsteps);
 
 /* Same as sdrt_rk4_step with host buffers: copies U_in_host to the device,
@@ -265,6 +269,11 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     divergence [M14 | M13] F~ on the tensor cores (tcgen05, 3xTF32, FP32
  *     accumulation in tensor memory); 0 = CUDA-core FMA accumulation. */
 #define SDRT_OPT_TC_DIVERGENCE 1
+/*   SDRT_OPT_FUSED_RK (default 1): 1 = RK4 steps on FP32 Euler meshes of
+ *     degree-3 tetrahedra (CUDA-core kernels) interpolate each next stage's
+ *     state inside the previous stage's update; 0 = one interpolation kernel
+ *     per stage.  Same operations either way: the results are bit-identical. */
+#define SDRT_OPT_FUSED_RK 2
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 
 /* Per-launch device timing with CUDA events recorded on the context's stream

@@ -88,6 +88,7 @@ struct Mesh {
     std::vector<uint8_t> is_left;
     std::vector<double> sol_xyz;
     DevBuf ufe, dufe, ustage, uacc, uhost_dev, rec, drec, fiur, dfiur;
+    DevBuf rec2, fiur2;          // second record buffers of the fused RK4 stages
     DevBuf qfe, dqfe, qfiu, dqfiu;    // viscous: flux-point gradients (kargs.hpp layout)
     // Block tables of the generic kernels (one launch per kernel kind walks
     // every block): host copies and the device array, in the mesh precision.
@@ -115,6 +116,7 @@ struct sdrt_ctx {
     bool host_only = false;       // device == -1: host-side setup only, no compute
     bool use_tc = false;          // tensor-core interpolation where instantiated (SDRT_OPT_TENSOR_CORES)
     bool use_tc_div = false;      // tensor-core divergence where instantiated (SDRT_OPT_TC_DIVERGENCE)
+    bool fuse_rk = true;          // next-stage interpolation in the RK4 stage update (SDRT_OPT_FUSED_RK)
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
     std::vector<std::unique_ptr<Mesh>> meshes;
@@ -449,8 +451,68 @@ int run_vjp(sdrt_ctx* ctx, Mesh& m, const T* U, const T* W, T* out) {
     return SDRT_OK;
 }
 
+// Whether stages 1-3 of RK4 can interpolate the next stage's state in their
+// epilogue (record path, FP32 Euler on tetrahedra of degree 3, CUDA-core kernels).
+bool rk_fusable(sdrt_ctx* ctx, const Mesh& m) {
+    if (!m.fast || m.phys.precision != SDRT_FP32 || ctx->use_tc || ctx->use_tc_div || !m.rec2.p || !m.fiur2.p)
+        return false;
+    for (auto& bp : m.blocks)
+        if (!flux_rec_fusable(make_kblock<float>(*ctx->etypes[bp->etype], *bp), m.nvar, m.phys.system)) return false;
+    return true;
+}
+
+// RK4 with one interpolation per step: the state U is interpolated into the
+// records once, and the epilogues of stages 1-3 interpolate the next stage's
+// state into the other record buffer (the two alternate), so the stage state
+// never goes to global memory.  Stage 4 writes the new U.
+int rk4_stages_fused(sdrt_ctx* ctx, Mesh& m, float* U, double dt) {
+    const KPhys<float> P = make_phys<float>(m.phys);
+    float* recs[2] = {m.rec.as<float>(), m.rec2.as<float>()};
+    float* fiurs[2] = {m.fiur.as<float>(), m.fiur2.as<float>()};
+    for (auto& bp : m.blocks) {
+        KBlock<float> K = make_kblock<float>(*ctx->etypes[bp->etype], *bp);
+        const int s = prof_begin(ctx, KIND_INTERP);
+        const int r = launch_interp_rec<float>(K, m.nvar, U, recs[0], fiurs[0], ctx->flag.as<int>(), ctx->nsm,
+                                               ctx->stream);
+        prof_end(ctx, s);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "record path not instantiated");
+        ++ctx->launches;
+    }
+    KEpi<float> E{};
+    E.flag = ctx->flag.as<int>();
+    E.u0 = U;
+    E.uacc = m.uacc.as<float>();
+    E.unext = m.ustage.as<float>();
+    const float c6 = (float)(dt / 6.0), c3 = (float)(dt / 3.0), c2 = (float)(dt / 2.0), c1 = (float)dt;
+    const int modes[4] = {EPI_RK_FIRST, EPI_RK_MID, EPI_RK_MID, EPI_RK_LAST};
+    const float cacc[4] = {c6, c3, c3, c6};
+    const float cnext[4] = {c2, c2, c1, 0.0f};
+    for (int stage = 0; stage < 4; ++stage) {
+        E.mode = modes[stage];
+        E.cacc = cacc[stage];
+        E.cnext = cnext[stage];
+        E.out = stage == 3 ? U : nullptr;
+        E.rec_next = stage < 3 ? recs[(stage + 1) & 1] : nullptr;
+        E.fiur_next = stage < 3 ? fiurs[(stage + 1) & 1] : nullptr;
+        for (auto& bp : m.blocks) {
+            KBlock<float> K = make_kblock<float>(*ctx->etypes[bp->etype], *bp);
+            const int s = prof_begin(ctx, KIND_RESIDUAL);
+            launch_flux_rec<float>(K, m.phys.system, recs[stage & 1], nullptr, fiurs[stage & 1], nullptr, P, E,
+                                   ctx->nsm, ctx->stream);
+            prof_end(ctx, s);
+            ++ctx->launches;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
 template <typename T>
 int rk4_stages(sdrt_ctx* ctx, Mesh& m, T* U, double dt) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (ctx->fuse_rk && rk_fusable(ctx, m)) return rk4_stages_fused(ctx, m, U, dt);
+    }
     KEpi<T> E{};
     E.flag = ctx->flag.as<int>();
     T* us = m.ustage.as<T>();
@@ -523,6 +585,10 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
         if (!m.fiur.p) SDRT_CUDA(m.fiur.alloc((size_t)m.fiur_total * es));
         if (need_dual && !m.drec.p) SDRT_CUDA(m.drec.alloc((size_t)m.rec_total * es));
         if (need_dual && !m.dfiur.p) SDRT_CUDA(m.dfiur.alloc((size_t)m.fiur_total * es));
+    }
+    if (need_rk && m.fast && m.phys.precision == SDRT_FP32) {
+        if (!m.rec2.p) SDRT_CUDA(m.rec2.alloc((size_t)m.rec_total * es));
+        if (!m.fiur2.p) SDRT_CUDA(m.fiur2.alloc((size_t)m.fiur_total * es));
     }
     if (need_rk && !m.ustage.p) {
         SDRT_CUDA(m.ustage.alloc((size_t)m.state_len * es));
@@ -1130,6 +1196,7 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     if (!ctx) return SDRT_ERR_ARG;
     if (option == SDRT_OPT_TENSOR_CORES) ctx->use_tc = value != 0;
     else if (option == SDRT_OPT_TC_DIVERGENCE) ctx->use_tc_div = value != 0;
+    else if (option == SDRT_OPT_FUSED_RK) ctx->fuse_rk = value != 0;
     else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {

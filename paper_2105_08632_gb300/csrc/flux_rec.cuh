@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace sdrt {
 namespace {
 
@@ -32,9 +34,51 @@ __device__ __forceinline__ void prim_rec(const T* u, T gamma, T& inv, T* v, T& p
     p = (gamma - T(1)) * fma(T(-0.5), ke, u[ND + 1]);
 }
 
+// FP32: the primitive variables, normal velocities and sound speeds of the
+// left and right states as the two lanes of float2 pairs on the paired FP32
+// instructions of sm_100 and later (__fmul2_rn / __ffma2_rn: IEEE
+// round-to-nearest per lane), in the same operations and order as the scalar
+// code below, so the results are bit-identical.
+template <int ND>
+__device__ __forceinline__ void rusanov_rec_pair(const float* uL, const float* uR, const float* n, float gamma, float s,
+                                                 float* F) {
+    constexpr int V = ND + 2;
+    float2 u[V];
+    #pragma unroll
+    for (int v = 0; v < V; ++v) u[v] = make_float2(uL[v], uR[v]);
+    float2 inv = make_float2(__fdividef(1.0f, u[0].x), __fdividef(1.0f, u[0].y));
+    inv = __ffma2_rn(inv, __ffma2_rn(make_float2(-u[0].x, -u[0].y), inv, make_float2(1.f, 1.f)), inv);
+    float2 vv[ND];
+    float2 ke = make_float2(0.f, 0.f);
+    #pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        vv[d] = __fmul2_rn(u[1 + d], inv);
+        ke = __ffma2_rn(u[1 + d], vv[d], ke);
+    }
+    const float g1 = gamma - 1.0f;
+    const float2 p = __fmul2_rn(make_float2(g1, g1), __ffma2_rn(make_float2(-0.5f, -0.5f), ke, u[V - 1]));
+    float2 vn = __fmul2_rn(vv[0], make_float2(n[0], n[0]));
+    #pragma unroll
+    for (int d = 1; d < ND; ++d) vn = __ffma2_rn(vv[d], make_float2(n[d], n[d]), vn);
+    const float2 c2 = __fmul2_rn(__fmul2_rn(make_float2(gamma, gamma), p), inv);
+    const float cL = c2.x * rsqrtf(c2.x), cR = c2.y * rsqrtf(c2.y);
+    const float phi = fmaxf(fabsf(vn.x) + cL, fabsf(vn.y) + cR);
+    const float hs = 0.5f * s;
+    F[0] = hs * fmaf(phi, u[0].x - u[0].y, fmaf(u[0].x, vn.x, u[0].y * vn.y));
+    const float pp = p.x + p.y;
+    #pragma unroll
+    for (int i = 0; i < ND; ++i)
+        F[1 + i] = hs * fmaf(phi, u[1 + i].x - u[1 + i].y, fmaf(pp, n[i], fmaf(u[1 + i].x, vn.x, u[1 + i].y * vn.y)));
+    F[V - 1] = hs * fmaf(phi, u[V - 1].x - u[V - 1].y, fmaf(u[V - 1].x + p.x, vn.x, (u[V - 1].y + p.y) * vn.y));
+}
+
 // s F_Rusanov(u_L, u_R, n): F = (n.f_L + n.f_R)/2 + phi/2 (u_L - u_R).
 template <typename T, int ND>
 __device__ __forceinline__ void rusanov_rec(const T* uL, const T* uR, const T* n, T gamma, T s, T* F) {
+    if constexpr (std::is_same<T, float>::value) {
+        rusanov_rec_pair<ND>(uL, uR, n, gamma, s, F);
+        return;
+    }
     constexpr int V = ND + 2;
     T iL, iR, vL[ND], vR[ND], pL, pR;
     prim_rec<T, ND>(uL, gamma, iL, vL, pL);

@@ -120,6 +120,11 @@ struct KEpi {
     T* unext;
     T cacc, cnext;
     int* flag;           // set to 1 when a non-finite value is produced
+    // Non-null (record path, stages 1-3 of RK4): the next stage's state
+    // u0 + cnext R is not stored but interpolated right away into these record
+    // buffers (the layouts of REC and FIUR).
+    T* rec_next;
+    T* fiur_next;
 };
 
 }  // namespace sdrt

@@ -209,6 +209,76 @@ __device__ __forceinline__ void epi_block(const KEpi<T>& E, const T (&acc)[RS][V
     if (bad) *E.flag = 1;
 }
 
+// Stage update of stages 1-3 with the next stage's state kept on chip: uacc
+// goes to global memory, u0 + cnext R into this element's shared-memory state
+// tile ut ([NS][8]: solution point, variable).
+template <int RS, int V, typename T>
+__device__ __forceinline__ void epi_block_next(const KEpi<T>& E, const T (&acc)[RS][V], T inv, size_t base, int ld,
+                                               int r0, int nrows, T* ut) {
+    T a[RS][V], b[RS][V];
+    const bool mid = E.mode == EPI_RK_MID;
+    #pragma unroll
+    for (int i = 0; i < RS; ++i)
+        #pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const size_t idx = base + (size_t)((r0 + i) * V + v) * ld;
+            const bool ok = r0 + i < nrows;
+            a[i][v] = ok ? __ldg(E.u0 + idx) : T(0);
+            b[i][v] = (ok && mid) ? E.uacc[idx] : T(0);
+        }
+    bool bad = false;
+    #pragma unroll
+    for (int i = 0; i < RS; ++i) {
+        if (r0 + i >= nrows) continue;
+        #pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const size_t idx = base + (size_t)((r0 + i) * V + v) * ld;
+            const T r = acc[i][v] * inv;
+            bad |= !isfinite(r);
+            E.uacc[idx] = fma(E.cacc, r, mid ? b[i][v] : a[i][v]);
+            ut[(r0 + i) * 8 + v] = fma(E.cnext, r, a[i][v]);
+        }
+    }
+    if (bad) *E.flag = 1;
+}
+
+// Rows j = h + G i (i < NRT) of [M0; M12] u for one element whose state tile
+// ut ([NS][8]) is in shared memory; A is the row-major operator in global
+// memory (rows of nsp values, read through the L1 cache).  Rows past MI are
+// computed from row MI - 1 and not used.
+template <int NRT, int NS, int V, int G>
+__device__ __forceinline__ void interp_rows_tile(const float* __restrict__ A, int nsp, int h, int MI, const float* ut,
+                                                 float (&res)[NRT][V]) {
+    static_assert(NS % 4 == 0 && V == 5, "four solution points per operator load; five variables");
+    #pragma unroll
+    for (int i = 0; i < NRT; ++i)
+        #pragma unroll
+        for (int v = 0; v < V; ++v) res[i][v] = 0.f;
+    #pragma unroll
+    for (int r = 0; r < NS; r += 4) {
+        float u[4][V];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(ut + (r + q) * 8);
+            u[q][0] = t.x;
+            u[q][1] = t.y;
+            u[q][2] = t.z;
+            u[q][3] = t.w;
+            u[q][4] = ut[(r + q) * 8 + 4];
+        }
+        #pragma unroll
+        for (int i = 0; i < NRT; ++i) {
+            const int j = min(h + G * i, MI - 1);
+            const float4 x = __ldg(reinterpret_cast<const float4*>(A + (size_t)j * nsp + r));
+            const float xq[4] = {x.x, x.y, x.z, x.w};
+            #pragma unroll
+            for (int q = 0; q < 4; ++q)
+                #pragma unroll
+                for (int v = 0; v < V; ++v) res[i][v] = fmaf(xq[q], u[q][v], res[i][v]);
+        }
+    }
+}
+
 // Divergence accumulators of one thread: RS rows x V variables.
 template <typename T, int RS, int V>
 struct ScalarAcc {
@@ -412,9 +482,9 @@ __global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __r
 // ---------------------------------------------------------------------------
 // Interpolation to the flux points as a producer / consumer pipeline (FP32).
 //
-// Warp NC / 32 (the last one) is the producer: for each of the CTA's tiles it
-// streams the tile's solution values U[rho][v][e0 .. e0+TE) (one bulk copy per
-// (rho, v) row) into a two-stage shared-memory ring, completing on full[s].
+// Warp NC / 32 (the last one) is the producer: for each of the CTA's tiles one
+// lane streams the tile's solution values U[rho][v][e0 .. e0+TE) (one 2D tensor
+// copy) into a two-stage shared-memory ring, completing on full[s].
 // Consumer thread (e, v, g) copies the NS values of variable v of element e
 // to registers, releases the stage (empty[s]) and computes the rows
 // j = g, g + GR, ... of [u_fe; u_fiu] = [M0; M12] U (Eqs.
@@ -424,10 +494,10 @@ __global__ void __launch_bounds__(2 * TE) k_interp_rec(KBlock<T> B, const T* __r
 // elements x 4 row groups, so that the staging stores of a warp fall on 32
 // distinct banks (record stride = 4 mod 8 words apart per element).  The results
 // are assembled into one of two record staging buffers that a single thread
-// writes out with bulk stores while the next tile is computed.  One CTA per
-// SM, persistent.
+// writes out with bulk stores while the next tile is computed.  Persistent:
+// one CTA per SM, two for tiles of at most 32 elements.
 template <int NS, int V, int NFE, int NFIU, int TE, int GR, bool ALLV>
-__global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, 1) k_interp_pipe(KBlock<float> B,
+__global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, TE <= 32 ? 2 : 1) k_interp_pipe(KBlock<float> B,
                                                                      const __grid_constant__ CUtensorMap umap,
                                                                      float* __restrict__ REC,
                                                                      float* __restrict__ FIUR, int* __restrict__ err) {
@@ -601,8 +671,8 @@ __global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, 1) k_interp_pip
 
 // ---------------------------------------------------------------------------
 // Flux and divergence of one tile staged in shared memory (value path).
-template <typename T, int V, int ND, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW>
-__global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __restrict__ REC,
+template <typename T, int V, int ND, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW, bool FUSE = false>
+__global__ void __launch_bounds__(32 * NW, FUSE ? 3 : 1) k_flux_rec(KBlock<T> B, const T* __restrict__ REC,
                                                       const T* __restrict__ FIUR, KPhys<T> P, KEpi<T> E,
                                                       const __grid_constant__ CUtensorMap u0map,
                                                       const __grid_constant__ CUtensorMap accmap, int prefetch) {
@@ -790,18 +860,66 @@ __global__ void __launch_bounds__(32 * NW) k_flux_rec(KBlock<T> B, const T* __re
                 }
             }
         }
-        if (valid) {
-            const int e = e0 + el;
-            const T inv = -met_e[0];
-            T out[RS][V];
-            #pragma unroll
-            for (int i = 0; i < RS; ++i)
+        if constexpr (FUSE) {
+            // Stages 1-3 of RK4: the next stage's state goes to this element's
+            // own-record slot (read by this warp only), its interpolation to the
+            // element's partner-record and internal-record slots, and the tile's
+            // new records out with two bulk stores.
+            static_assert(std::is_same<T, float>::value && V == 5 && G == 4, "fused interpolation: FP32 Euler");
+            constexpr int MI = NFE + NFIU;
+            constexpr int NRT = (MI + G - 1) / G;
+            float* ut = own + (size_t)le * B.ers;
+            __syncwarp();         // the warp's reads of its own records are complete
+            if (valid) {
+                const T inv = -met_e[0];
+                T out[RS][V];
                 #pragma unroll
-                for (int v = 0; v < V; ++v) out[i][v] = acc.get(i, v);
-            epi_block<RS, V>(E, out, inv, (size_t)B.u_off + e, B.ld, h * RS, NS);
+                for (int i = 0; i < RS; ++i)
+                    #pragma unroll
+                    for (int v = 0; v < V; ++v) out[i][v] = acc.get(i, v);
+                epi_block_next<RS, V>(E, out, inv, (size_t)B.u_off + e0 + el, B.ld, h * RS, NS, ut);
+            }
+            __syncwarp();         // the element's state tile is complete
+            if (valid) {
+                float res[NRT][V];
+                interp_rows_tile<NRT, NS, V, G>(B.Air, B.Md_pad, h, MI, ut, res);
+                float* rs = part + (size_t)le * B.ers;
+                float* fs = fiu + (size_t)le * B.frs;
+                #pragma unroll
+                for (int i = 0; i < NRT; ++i) {
+                    const int j = h + G * i;
+                    if (j >= MI) break;
+                    float* dst = j < NFE ? rs + roff[j] : fs + (j - NFE) * V;
+                    #pragma unroll
+                    for (int v = 0; v < V; ++v) dst[v] = res[i][v];
+                }
+            }
+            fence_proxy_async();  // staging writes (and this thread's reads) before the bulk copies
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bulk_s2g(E.rec_next + B.rec_base + (size_t)e0 * B.ers, part, (uint32_t)(n * B.ers * sizeof(T)));
+                bulk_s2g(E.fiur_next + B.fiur_base + (size_t)e0 * B.frs, fiu, (uint32_t)(n * B.frs * sizeof(T)));
+                bulk_commit();
+                bulk_wait_read0();    // the staging slots may be refilled once the stores have read them
+            }
+            __syncthreads();
+        } else {
+            if (valid) {
+                const int e = e0 + el;
+                const T inv = -met_e[0];
+                T out[RS][V];
+                #pragma unroll
+                for (int i = 0; i < RS; ++i)
+                    #pragma unroll
+                    for (int v = 0; v < V; ++v) out[i][v] = acc.get(i, v);
+                epi_block<RS, V>(E, out, inv, (size_t)B.u_off + e, B.ld, h * RS, NS);
+            }
+            fence_proxy_async();  // this thread's reads of the tile precede the next tile's async copies
+            __syncthreads();      // the tile buffers are free for the next tile's copies
         }
-        fence_proxy_async();  // this thread's reads of the tile precede the next tile's async copies
-        __syncthreads();      // the tile buffers are free for the next tile's copies
+    }
+    if constexpr (FUSE) {
+        if (threadIdx.x == 0) bulk_wait0();   // record stores complete before the kernel ends
     }
 }
 
@@ -968,10 +1086,10 @@ void interp_rec_impl(const KBlock<T>& B, const T* U, T* REC, T* FIUR, int* err, 
     else interp_rec_tile<T, NS, V, NFE, NFIU, 32>(B, U, REC, FIUR, err, nsm, st, smem_of(32));
 }
 
-template <typename T, int V, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW>
+template <typename T, int V, int SYS, int RIE, int NS, int G, int NFE, int NFIU, int NW, bool FUSE = false>
 void flux_rec_impl(const KBlock<T>& B, const T* REC, const T* FIUR, const KPhys<T>& P, const KEpi<T>& E, int nsm,
                    cudaStream_t st) {
-    auto k = k_flux_rec<T, V, 3, SYS, RIE, NS, G, NFE, NFIU, NW>;
+    auto k = k_flux_rec<T, V, 3, SYS, RIE, NS, G, NFE, NFIU, NW, FUSE>;
     constexpr int TE = NW * (32 / G);
     constexpr int RSP = ((NS + G - 1) / G + 3) / 4 * 4;
     auto a16 = [](size_t x) { return (x + 15) / 16 * 16; };
@@ -1050,7 +1168,8 @@ static bool interp_pipe_impl(const KBlock<float>& B, const float* U, float* REC,
     auto k = k_interp_pipe<NS, V, NFE, NFIU, TE, GR, ALLV>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int need = (B.nelem + TE - 1) / TE;
-    const int grid = need < nsm ? need : nsm;
+    const int slots = (TE <= 32 ? 2 : 1) * nsm;     // CTAs resident per SM (shared memory)
+    const int grid = need < slots ? need : slots;
     k<<<grid, (ALLV ? 1 : V) * TE * GR + 32, smem, st>>>(B, umap, REC, FIUR, err);
     return true;
 }
@@ -1059,7 +1178,7 @@ template <typename T>
 int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, int* err, int nsm, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value) {
         if (V == 5 && B.nsol == 20 &&
-            interp_pipe_impl<20, 5, 40, 10, 64, 4, true>(B, U, REC, FIUR, err, nsm, st))
+            interp_pipe_impl<20, 5, 40, 10, 32, 4, true>(B, U, REC, FIUR, err, nsm, st))
             return 0;
         if (V == 5 && B.nsol == 35 &&
             interp_pipe_impl<35, 5, 60, 20, 32, 4, false>(B, U, REC, FIUR, err, nsm, st))
@@ -1079,6 +1198,11 @@ int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, in
     return 0;
 }
 
+bool flux_rec_fusable(const KBlock<float>& B, int V, int system) {
+    return system == SYS_EULER && V == 5 && B.nsol == 20 && B.Air != nullptr && B.Md_pad % 4 == 0 &&
+           B.Mir >= 50 && B.ers >= 20 * 8;
+}
+
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,
                     const KPhys<T>& P, const KEpi<T>& E, int nsm, cudaStream_t st) {
@@ -1086,7 +1210,12 @@ int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC,
     if (system == SYS_EULER) {
         if (B.nsol == 20) {
             if (dual) flux_rec_dual_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20>(B, REC, dREC, FIUR, dFIUR, P, E, nsm, st);
-            else flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20, 4, 40, 10, 4>(B, REC, FIUR, P, E, nsm, st);
+            else if constexpr (std::is_same<T, float>::value) {
+                if (E.rec_next)
+                    flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20, 4, 40, 10, 4, true>(B, REC, FIUR, P, E, nsm, st);
+                else
+                    flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20, 4, 40, 10, 4>(B, REC, FIUR, P, E, nsm, st);
+            } else flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 20, 4, 40, 10, 4>(B, REC, FIUR, P, E, nsm, st);
         } else {
             if (dual) flux_rec_dual_impl<T, 5, SYS_EULER, RIE_RUSANOV, 35>(B, REC, dREC, FIUR, dFIUR, P, E, nsm, st);
             else flux_rec_impl<T, 5, SYS_EULER, RIE_RUSANOV, 35, 4, 60, 20, 2>(B, REC, FIUR, P, E, nsm, st);

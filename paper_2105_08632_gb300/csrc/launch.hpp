@@ -107,6 +107,10 @@ bool tc_flux_available(int shape, int nsol, int nvar, int system, int riemann);
 int launch_flux_tc(const KBlock<float>& B, const float* REC, const float* FIUR, const KPhys<float>& P,
                    const KEpi<float>& E, int nsm, cudaStream_t st);
 
+// Whether launch_flux_rec can interpolate the next RK stage's state in its
+// epilogue (E.rec_next / E.fiur_next non-null; FP32 Euler, tetrahedra of degree 3).
+bool flux_rec_fusable(const KBlock<float>& B, int V, int system);
+
 // Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,

@@ -265,6 +265,7 @@ def sdrt_launch_count(ctx):
 
 SDRT_OPT_TENSOR_CORES = 0
 SDRT_OPT_TC_DIVERGENCE = 1
+SDRT_OPT_FUSED_RK = 2
 
 
 def sdrt_autotune(ctx, mesh, U, reps=3):

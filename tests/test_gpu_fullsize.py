@@ -115,3 +115,33 @@ def test_full_size_benchmark_workload(ctx, div_tc):
     part, left = M.face_map()
     assert np.array_equal(part.astype(np.int64), geom.partner)
     assert np.array_equal(left.astype(bool), geom.is_left)
+
+
+@pytest.mark.parametrize("ncell", [(3, 3, 3), (24, 24, 24)])
+def test_fused_rk_stages_match_the_unfused_sequence(ctx, ncell):
+    """RK4 with the next stage's interpolation in the stage update
+    (SDRT_OPT_FUSED_RK, one interpolation and four flux kernels per step)
+    against one interpolation kernel per stage: the same FP32 operations in
+    the same order, so the states after three steps agree bit for bit.
+    162 tetrahedra: five full tiles of 32 and a ragged one of 2; 82,944: the
+    benchmark workload."""
+    from paper_2105_08632_gb300 import sdrt
+    mesh = meshes.box_mesh("tet", ncell, [-5.0] * 3, [5.0] * 3)
+    M = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
+    X = M.sol_points()[0]
+    u = fields.isentropic_vortex(X.reshape(-1, 3), gamma=1.4, mach=0.5).reshape(X.shape[0], X.shape[1], 5)
+    u = u * (1 + fields.uniform_noise(u.shape, 7, 1e-2))
+    U0 = M.pack([np.ascontiguousarray(u.transpose(1, 2, 0))])
+    out = {}
+    try:
+        for fused in (1, 0):
+            sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_FUSED_RK, fused)
+            Ud = torch.from_numpy(U0.copy()).to("cuda")
+            M.rk4_step(Ud, 1e-3, 3)
+            M.sync()
+            out[fused] = Ud.cpu().numpy()
+    finally:
+        sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_FUSED_RK, 1)
+    assert np.isfinite(out[1]).all()
+    assert not np.array_equal(out[1], U0)
+    assert np.array_equal(out[1], out[0])
