@@ -157,6 +157,49 @@ int sdrt_get_operator(sdrt_ctx* ctx, int etype_id, int which, double* host_out, 
 int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
                     int64_t nfaces, const sdrt_face* faces, int* mesh_id);
 int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out);
+
+/* One partition of a mesh whose residual is distributed over processes or
+ * devices.  Elements couple only through the common flux at shared faces
+ * (paper Sec. 2.1, Eq. "flux_advection" and the common fluxes), so a
+ * partition needs, once per residual evaluation, the external-point states of
+ * the faces it shares with other partitions, and nothing else.
+ * blocks / faces as for sdrt_setup_mesh; ghost[b] = 1 marks blocks that hold
+ * copies of OTHER partitions' elements sharing a face with this partition's
+ * elements (their vertices pair the face points; their other faces stay
+ * unglued; no residual is computed for them).  Ghost blocks come after the
+ * owned ones; faces keep the L / R order of the whole mesh.  The state arrays
+ * of the partition hold the owned blocks only.  Record path only: tetrahedra
+ * of degree 3 or 4 with Euler / Rusanov or advection / upwind, one face-record
+ * size (else SDRT_ERR_UNSUPPORTED).  Whole-mesh calls (sdrt_residual,
+ * sdrt_rk4_step, sdrt_jvp, sdrt_vjp, ...) return SDRT_ERR_STATE on a
+ * partition.  Host inputs are copied. */
+int sdrt_setup_partition(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                         const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id);
+
+/* Exchange lists of a partition, host int32 triplets (block, element, local
+ * face) in the numbering of sdrt_setup_partition: send[i] names the i-th
+ * face record this partition packs (an owned element's face), recv[i] the
+ * ghost face that the i-th received record fills.  Partition q's send list
+ * towards p must list the faces in the order of p's receive list from q.
+ * SDRT_ERR_ARG for a triplet outside the owned (send) or ghost (recv) blocks. */
+int sdrt_set_exchange(sdrt_ctx* ctx, int mesh_id, int64_t nsend, const int32_t* send, int64_t nrecv,
+                      const int32_t* recv);
+/* Counts of the exchange lists (-1 before sdrt_set_exchange) and the values per
+ * face record (points per face x nvar, padded to a multiple of 4). */
+int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record);
+
+/* Partitioned residual, first half: interpolation of the owned blocks to
+ * their flux points (Eq. "interpolation_procedure"), then the send buffer
+ * send_dev (device, nsend x face_record values, caller owned) packed in the
+ * order of the send list.  Asynchronous on the context's stream. */
+int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* send_dev);
+/* Second half, after the caller has moved every partition's send buffer
+ * segments into the receive buffers (NCCL, device copies, ...): recv_dev
+ * (device, nrecv x face_record values) fills the ghost faces, then the common
+ * and internal fluxes and the divergence of the owned blocks give R_dev =
+ * dU/dt (owned state layout).  Same values as sdrt_residual on the whole
+ * mesh, element by element. */
+int sdrt_residual_end(sdrt_ctx* ctx, int mesh_id, const void* recv_dev, void* R_dev);
 int sdrt_get_block_layout(sdrt_ctx* ctx, int mesh_id, int block, sdrt_block_layout* out);
 
 /* Physical coordinates of the solution points, host FP64, blocks in order,

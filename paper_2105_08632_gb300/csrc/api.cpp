@@ -102,6 +102,14 @@ struct Mesh {
     std::vector<int> graph_slots;     // timing slots recorded inside the graph
     int64_t graph_launches = 0;       // kernel launches in one replay
     bool warmed = false;
+    // Partition (sdrt_setup_partition): ghost blocks are copies of other
+    // partitions' elements that share faces with this one; only their face
+    // records are used, filled from the received exchange buffer.
+    bool partition = false;
+    std::vector<std::unique_ptr<MBlock>> ghosts;
+    int xfrec = 0;                    // values per exchanged face record
+    int64_t nsend = -1, nrecv = -1;   // -1: no exchange lists yet
+    DevBuf xsend_off, xrecv_off;      // REC offsets of the sent / received face records
     ~Mesh() {
         if (graph) cudaGraphExecDestroy(graph);
     }
@@ -552,6 +560,15 @@ int check_compute(sdrt_ctx* ctx, int mesh_id) {
     return SDRT_OK;
 }
 
+// Whole-mesh computations: not on a partition (its ghost records come from the exchange).
+int check_whole(sdrt_ctx* ctx, int mesh_id) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    if (ctx->meshes[mesh_id]->partition)
+        return fail(ctx, SDRT_ERR_STATE, "partition mesh: use sdrt_residual_begin / sdrt_residual_end");
+    return SDRT_OK;
+}
+
 // (Re)builds the block tables of the generic kernels from the mesh blocks.
 int refresh_tables(sdrt_ctx* ctx, Mesh& m) {
     m.kb_f.clear();
@@ -596,6 +613,56 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
         SDRT_CUDA(cudaMemset(m.ustage.p, 0, m.ustage.bytes));
         SDRT_CUDA(cudaMemset(m.uacc.p, 0, m.uacc.bytes));
     }
+    return SDRT_OK;
+}
+
+// Partitioned residual, first half: interpolation of the owned blocks into
+// the records, then the packed face records to send.
+template <typename T>
+int residual_begin_impl(sdrt_ctx* ctx, Mesh& m, const T* U, T* send) {
+    T* rec = m.rec.as<T>();
+    T* fiur = m.fiur.as<T>();
+    for (auto& bp : m.blocks) {
+        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+        const int s = prof_begin(ctx, KIND_INTERP);
+        const int r = launch_interp_rec<T>(K, m.nvar, U, rec, fiur, ctx->flag.as<int>(), ctx->nsm, ctx->stream);
+        prof_end(ctx, s);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "record path not instantiated");
+        ++ctx->launches;
+    }
+    if (m.nsend > 0) {
+        launch_face_records<T>(rec, send, m.xsend_off.as<int>(), m.nsend, m.xfrec, false, ctx->nsm, ctx->stream);
+        ++ctx->launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+// Second half: the received face records into the ghost slots, then fluxes
+// and divergence of the owned blocks.
+template <typename T>
+int residual_end_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* R) {
+    T* rec = m.rec.as<T>();
+    T* fiur = m.fiur.as<T>();
+    if (m.nrecv > 0) {
+        launch_face_records<T>(recv, rec, m.xrecv_off.as<int>(), m.nrecv, m.xfrec, true, ctx->nsm, ctx->stream);
+        ++ctx->launches;
+    }
+    const KPhys<T> P = make_phys<T>(m.phys);
+    KEpi<T> E{};
+    E.mode = EPI_STORE;
+    E.out = R;
+    E.flag = ctx->flag.as<int>();
+    for (auto& bp : m.blocks) {
+        KBlock<T> K = make_kblock<T>(*ctx->etypes[bp->etype], *bp);
+        const int s = prof_begin(ctx, KIND_RESIDUAL);
+        launch_flux_rec<T>(K, m.phys.system, rec, nullptr, fiur, nullptr, P, E, ctx->nsm, ctx->stream);
+        prof_end(ctx, s);
+        ++ctx->launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SDRT_OK;
 }
 
@@ -759,10 +826,32 @@ int sdrt_get_operator(sdrt_ctx* ctx, int id, int which, double* out, int64_t n) 
     return SDRT_OK;
 }
 
+static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                           const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id);
+
 int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks, int64_t nfaces,
                     const sdrt_face* faces, int* mesh_id) {
+    return setup_mesh_impl(ctx, phys, nblocks, blocks, nullptr, nfaces, faces, mesh_id);
+}
+
+int sdrt_setup_partition(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                         const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id) {
+    if (!ghost) return fail(ctx, SDRT_ERR_ARG, "null ghost flags");
+    return setup_mesh_impl(ctx, phys, nblocks, blocks, ghost, nfaces, faces, mesh_id);
+}
+
+static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                           const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id) {
     if (!ctx || !phys || !blocks || !mesh_id || nblocks <= 0 || (nfaces > 0 && !faces))
         return fail(ctx, SDRT_ERR_ARG, "null or empty argument");
+    int nown = nblocks;
+    if (ghost) {
+        nown = 0;
+        while (nown < nblocks && !ghost[nown]) ++nown;
+        for (int b = nown; b < nblocks; ++b)
+            if (!ghost[b]) return fail(ctx, SDRT_ERR_ARG, "ghost blocks must follow the owned blocks");
+        if (nown == 0) return fail(ctx, SDRT_ERR_ARG, "a partition needs an owned block");
+    }
     if (phys->ndim != 2 && phys->ndim != 3) return fail(ctx, SDRT_ERR_ARG, "ndim must be 2 or 3");
     if (phys->precision != SDRT_FP32 && phys->precision != SDRT_FP64) return fail(ctx, SDRT_ERR_ARG, "bad precision");
     if (phys->system < SDRT_ADVECTION || phys->system > SDRT_NAVIER_STOKES) return fail(ctx, SDRT_ERR_ARG, "bad system");
@@ -827,6 +916,14 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
         }
     }
     if (canon >= INT32_MAX || m->Ftot >= INT32_MAX) return fail(ctx, SDRT_ERR_UNSUPPORTED, "mesh too large for int32 maps");
+    if (ghost) {
+        if (!m->fast)
+            return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions need the record path (tetrahedra of degree 3 or 4, "
+                                                   "Euler / Rusanov or advection / upwind)");
+        for (int b = 1; b < nblocks; ++b)
+            if (m->blocks[b]->frec != m->blocks[0]->frec)
+                return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions need one face-record size");
+    }
 
     // Metrics, physical points.
     struct HostBlk {
@@ -953,12 +1050,12 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
         hb[F.blk_l].metric[(size_t)(NDD + F.face_l * (nd + 1) + nd) * bl.ld + F.elem_l] = magL;
         hb[F.blk_r].metric[(size_t)(NDD + F.face_r * (nd + 1) + nd) * br.ld + F.elem_r] = -magR;
     }
-    for (int b = 0; b < nblocks; ++b)
+    for (int b = 0; b < nown; ++b)     // ghost elements keep their other faces unglued
         for (uint8_t g : hb[b].glued)
             if (!g) return fail(ctx, SDRT_ERR_MESH, "mesh has an unglued face (only closed / periodic meshes)");
 
-    // Device copies.
-    for (int b = 0; b < nblocks; ++b) {
+    // Device copies (ghost blocks need none: only their face records are read).
+    for (int b = 0; b < nown; ++b) {
         MBlock& mb = *m->blocks[b];
         const RefElement& R = ctx->etypes[mb.etype]->R;
         std::vector<int> dmap((size_t)R.nfe * mb.ld, 0);
@@ -1063,6 +1160,23 @@ int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const 
             mb.vtile = vsmem_of(TE) <= 220 * 1024 ? TE : 0;
         }
     }
+    if (ghost) {
+        // The state arrays and every kernel cover the owned blocks; the ghost
+        // blocks keep their face-record slots (after the owned records).
+        int64_t gsol = 0;
+        for (int b = nown; b < nblocks; ++b) {
+            MBlock& g = *m->blocks[b];
+            const RefElement& R = ctx->etypes[g.etype]->R;
+            m->ndof -= (int64_t)R.nsol * m->nvar * g.nelem;
+            gsol += (int64_t)g.nelem * R.nsol * nd;
+        }
+        m->state_len = m->blocks[nown]->u_off;
+        m->sol_xyz.resize(m->sol_xyz.size() - (size_t)gsol);
+        for (int b = nown; b < nblocks; ++b) m->ghosts.push_back(std::move(m->blocks[b]));
+        m->blocks.resize(nown);
+        m->partition = true;
+        m->xfrec = m->blocks[0]->frec;
+    }
     // Block tables of the generic kernels (tile widths are final here).
     if (int rt = refresh_tables(ctx, *m)) return rt;
     ctx->meshes.push_back(std::move(m));
@@ -1116,7 +1230,7 @@ int sdrt_get_face_map(sdrt_ctx* ctx, int mesh_id, int32_t* partner, uint8_t* is_
 }
 
 int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U, void* R) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !R || U == R) return fail(ctx, SDRT_ERR_ARG, "U and R must be distinct device arrays");
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1135,13 +1249,88 @@ int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U, void* R) {
     return run_residual<double>(ctx, m, static_cast<const double*>(U), nullptr, E);
 }
 
+int sdrt_set_exchange(sdrt_ctx* ctx, int mesh_id, int64_t nsend, const int32_t* send, int64_t nrecv,
+                      const int32_t* recv) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (!m.partition) return fail(ctx, SDRT_ERR_STATE, "not a partition mesh");
+    if (nsend < 0 || nrecv < 0 || (nsend > 0 && !send) || (nrecv > 0 && !recv))
+        return fail(ctx, SDRT_ERR_ARG, "bad exchange lists");
+    const int nown = (int)m.blocks.size();
+    auto offsets = [&](int64_t n, const int32_t* t, bool ghosts, std::vector<int>& out) -> bool {
+        out.resize(n);
+        for (int64_t i = 0; i < n; ++i) {
+            const int b = t[3 * i], e = t[3 * i + 1], f = t[3 * i + 2];
+            const MBlock* q = nullptr;
+            if (!ghosts && b >= 0 && b < nown) q = m.blocks[b].get();
+            if (ghosts && b >= nown && b < nown + (int)m.ghosts.size()) q = m.ghosts[b - nown].get();
+            if (!q || e < 0 || e >= q->nelem || f < 0 || f >= ctx->etypes[q->etype]->R.nfaces) return false;
+            out[i] = (int)(q->rec_base + (int64_t)e * q->ers + (int64_t)f * q->frec);
+        }
+        return true;
+    };
+    std::vector<int> so, ro;
+    if (!offsets(nsend, send, false, so)) return fail(ctx, SDRT_ERR_ARG, "send list: not an owned (block, element, face)");
+    if (!offsets(nrecv, recv, true, ro)) return fail(ctx, SDRT_ERR_ARG, "receive list: not a ghost (block, element, face)");
+    if (!ctx->host_only) {
+        if (nsend > 0) SDRT_CUDA(upload(m.xsend_off, so));
+        if (nrecv > 0) SDRT_CUDA(upload(m.xrecv_off, ro));
+    }
+    m.nsend = nsend;
+    m.nrecv = nrecv;
+    return SDRT_OK;
+}
+
+int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record) {
+    int r = check_mesh(ctx, mesh_id);
+    if (r) return r;
+    const Mesh& m = *ctx->meshes[mesh_id];
+    if (!m.partition) return fail(ctx, SDRT_ERR_STATE, "not a partition mesh");
+    if (nsend) *nsend = m.nsend;
+    if (nrecv) *nrecv = m.nrecv;
+    if (face_record) *face_record = m.xfrec;
+    return SDRT_OK;
+}
+
+static int check_partition(sdrt_ctx* ctx, int mesh_id) {
+    int r = check_compute(ctx, mesh_id);
+    if (r) return r;
+    const Mesh& m = *ctx->meshes[mesh_id];
+    if (!m.partition) return fail(ctx, SDRT_ERR_STATE, "not a partition mesh");
+    if (m.nsend < 0) return fail(ctx, SDRT_ERR_STATE, "no exchange lists (sdrt_set_exchange)");
+    return SDRT_OK;
+}
+
+int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U, void* send) {
+    int r = check_partition(ctx, mesh_id);
+    if (r) return r;
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (!U || (m.nsend > 0 && !send)) return fail(ctx, SDRT_ERR_ARG, "null array");
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if (m.phys.precision == SDRT_FP32)
+        return residual_begin_impl<float>(ctx, m, static_cast<const float*>(U), static_cast<float*>(send));
+    return residual_begin_impl<double>(ctx, m, static_cast<const double*>(U), static_cast<double*>(send));
+}
+
+int sdrt_residual_end(sdrt_ctx* ctx, int mesh_id, const void* recv, void* R) {
+    int r = check_partition(ctx, mesh_id);
+    if (r) return r;
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (!R || (m.nrecv > 0 && !recv)) return fail(ctx, SDRT_ERR_ARG, "null array");
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if (m.phys.precision == SDRT_FP32)
+        return residual_end_impl<float>(ctx, m, static_cast<const float*>(recv), static_cast<float*>(R));
+    return residual_end_impl<double>(ctx, m, static_cast<const double*>(recv), static_cast<double*>(R));
+}
+
 static int rk4_eager(sdrt_ctx* ctx, Mesh& m, void* U, double dt) {
     if (m.phys.precision == SDRT_FP32) return rk4_stages<float>(ctx, m, static_cast<float*>(U), dt);
     return rk4_stages<double>(ctx, m, static_cast<double*>(U), dt);
 }
 
 int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || nsteps < 0 || !(std::isfinite(dt))) return fail(ctx, SDRT_ERR_ARG, "bad argument");
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1236,7 +1425,7 @@ int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out) {
 }
 
 int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* Uin, void* Uout, double dt, int nsteps) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!Uin || !Uout) return fail(ctx, SDRT_ERR_ARG, "null host buffer");
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1250,7 +1439,7 @@ int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* Uin, void* Uout, 
 }
 
 int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* V, void* JV) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !V || !JV || JV == U || JV == V) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1270,7 +1459,7 @@ int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* V, void* JV)
 }
 
 int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !W || !JTW || JTW == U || JTW == W) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1284,7 +1473,7 @@ int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW
 }
 
 int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || reps < 1) return fail(ctx, SDRT_ERR_ARG, "null state or reps < 1");
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1417,7 +1606,7 @@ int internal_fail(sdrt_ctx* ctx, int code, const char* msg) { return fail(ctx, c
 
 int internal_residual_with_scratch(sdrt_ctx* ctx, int mesh_id, const void* U, void* R, void* scratch,
                                    size_t scratch_bytes) {
-    int r = check_compute(ctx, mesh_id);
+    int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !R || U == R || !scratch) return fail(ctx, SDRT_ERR_ARG, "U and R must be distinct device arrays");
     Mesh& m = *ctx->meshes[mesh_id];

@@ -1198,6 +1198,32 @@ int launch_interp_rec(const KBlock<T>& B, int V, const T* U, T* REC, T* FIUR, in
     return 0;
 }
 
+// Face records between the record array and a packed exchange buffer (one
+// thread per value, records of len values; consecutive threads walk a record).
+template <typename T>
+__global__ void k_face_records(const T* __restrict__ src, T* __restrict__ dst, const int* __restrict__ off,
+                               int64_t n, int len, int scatter) {
+    const int64_t total = n * len;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / len;
+        const int k = (int)(i - r * len);
+        if (scatter) dst[(int64_t)off[r] + k] = src[i];
+        else dst[i] = src[(int64_t)off[r] + k];
+    }
+}
+
+template <typename T>
+void launch_face_records(const T* src, T* dst, const int* off, int64_t n, int len, bool scatter, int nsm,
+                         cudaStream_t st) {
+    const int64_t total = n * len;
+    if (total <= 0) return;
+    int64_t grid = (total + 255) / 256;
+    if (grid > 8 * (int64_t)nsm) grid = 8 * (int64_t)nsm;
+    k_face_records<T><<<(int)grid, 256, 0, st>>>(src, dst, off, n, len, scatter ? 1 : 0);
+}
+template void launch_face_records<float>(const float*, float*, const int*, int64_t, int, bool, int, cudaStream_t);
+template void launch_face_records<double>(const double*, double*, const int*, int64_t, int, bool, int, cudaStream_t);
+
 bool flux_rec_fusable(const KBlock<float>& B, int V, int system) {
     return system == SYS_EULER && V == 5 && B.nsol == 20 && B.Air != nullptr && B.Md_pad % 4 == 0 &&
            B.Mir >= 50 && B.ers >= 20 * 8;

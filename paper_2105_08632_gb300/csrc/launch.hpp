@@ -111,6 +111,12 @@ int launch_flux_tc(const KBlock<float>& B, const float* REC, const float* FIUR, 
 // epilogue (E.rec_next / E.fiur_next non-null; FP32 Euler, tetrahedra of degree 3).
 bool flux_rec_fusable(const KBlock<float>& B, int V, int system);
 
+// n face records of len values between the record array and a packed buffer:
+// gather (buf[i len + k] = rec[off[i] + k]) or scatter (rec[off[i] + k] = buf[i len + k]).
+template <typename T>
+void launch_face_records(const T* src, T* dst, const int* off, int64_t n, int len, bool scatter, int nsm,
+                         cudaStream_t st);
+
 // Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,

@@ -111,6 +111,12 @@ def lib():
         "sdrt_set_option": (I, [P, I, I]),
         "sdrt_autotune": (I, [P, I, P, I]),
         "sdrt_get_tiles": (I, [P, I, I, ctypes.POINTER(ctypes.c_int32)]),
+        "sdrt_setup_partition": (I, [P, ctypes.POINTER(Physics), I, ctypes.POINTER(Block), ctypes.POINTER(ctypes.c_uint8),
+                                     I64, ctypes.POINTER(Face), ctypes.POINTER(I)]),
+        "sdrt_set_exchange": (I, [P, I, I64, ctypes.POINTER(ctypes.c_int32), I64, ctypes.POINTER(ctypes.c_int32)]),
+        "sdrt_get_exchange_info": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32)]),
+        "sdrt_residual_begin": (I, [P, I, P, P]),
+        "sdrt_residual_end": (I, [P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -181,9 +187,10 @@ def sdrt_get_operator(ctx, etype, name):
     return out
 
 
-def sdrt_setup_mesh(ctx, physics, blocks, faces):
+def sdrt_setup_mesh(ctx, physics, blocks, faces, ghost=None):
     """physics: Physics struct; blocks: list of (etype_id, verts float64 (E, nv, ND));
-    faces: int array (F, 6) and shift array (F, ND) as a tuple."""
+    faces: int array (F, 6) and shift array (F, ND) as a tuple.  ghost: per-block
+    flags (uint8) -> sdrt_setup_partition."""
     nb = len(blocks)
     barr = (Block * nb)()
     keep = []
@@ -199,8 +206,42 @@ def sdrt_setup_mesh(ctx, physics, blocks, faces):
         s = list(shift[i]) + [0.0] * (3 - len(shift[i]))
         farr[i] = Face(int(r[0]), int(r[1]), int(r[2]), int(r[3]), int(r[4]), int(r[5]), (ctypes.c_double * 3)(*s))
     out = ctypes.c_int()
-    _check(ctx, lib().sdrt_setup_mesh(ctx, ctypes.byref(physics), nb, barr, nf, farr, ctypes.byref(out)))
+    if ghost is None:
+        _check(ctx, lib().sdrt_setup_mesh(ctx, ctypes.byref(physics), nb, barr, nf, farr, ctypes.byref(out)))
+    else:
+        g = np.ascontiguousarray(ghost, np.uint8)
+        if g.shape != (nb,):
+            raise ValueError("one ghost flag per block")
+        _check(ctx, lib().sdrt_setup_partition(ctx, ctypes.byref(physics), nb, barr,
+                                               g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nf, farr,
+                                               ctypes.byref(out)))
     return out.value
+
+
+def sdrt_setup_partition(ctx, physics, blocks, ghost, faces):
+    return sdrt_setup_mesh(ctx, physics, blocks, faces, ghost=ghost)
+
+
+def sdrt_set_exchange(ctx, mesh, send, recv):
+    """send / recv: int32 arrays (n, 3) of (block, element, face) triplets."""
+    s = np.ascontiguousarray(np.asarray(send, np.int32).reshape(-1, 3))
+    r = np.ascontiguousarray(np.asarray(recv, np.int32).reshape(-1, 3))
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    _check(ctx, lib().sdrt_set_exchange(ctx, int(mesh), len(s), s.ctypes.data_as(P32), len(r), r.ctypes.data_as(P32)))
+
+
+def sdrt_get_exchange_info(ctx, mesh):
+    ns, nr, fr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(ctx, lib().sdrt_get_exchange_info(ctx, int(mesh), ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(fr)))
+    return {"nsend": ns.value, "nrecv": nr.value, "face_record": fr.value}
+
+
+def sdrt_residual_begin(ctx, mesh, U, send):
+    _check(ctx, lib().sdrt_residual_begin(ctx, int(mesh), _ptr(U), _ptr(send)))
+
+
+def sdrt_residual_end(ctx, mesh, recv, R):
+    _check(ctx, lib().sdrt_residual_end(ctx, int(mesh), _ptr(recv), _ptr(R)))
 
 
 def sdrt_get_mesh_info(ctx, mesh):
@@ -314,8 +355,8 @@ class Context:
     """A library context on one CUDA device, bound to torch's current stream."""
 
     def __init__(self, device=0, stream=None):
-        import torch
-        if stream is None:
+        if stream is None and device >= 0:               # device -1: host-only context
+            import torch
             stream = torch.cuda.current_stream(device).cuda_stream
         self.device = device
         self.ptr = sdrt_create(device, stream)
@@ -335,7 +376,7 @@ class Context:
 class Mesh:
     """A mesh set up in a Context: mesh dict from inputs.meshes plus physics."""
 
-    def __init__(self, ctx, mesh, degree, physics):
+    def __init__(self, ctx, mesh, degree, physics, ghost=None):
         self.ctx = ctx
         c = ctx.ptr
         blocks = []
@@ -350,7 +391,7 @@ class Mesh:
             et = sdrt_setup_element_type(c, blk["shape"], p)
             self.etypes.append(et)
             blocks.append((et, blk["verts"]))
-        self.id = sdrt_setup_mesh(c, physics, blocks, (mesh["faces"], mesh["shift"]))
+        self.id = sdrt_setup_mesh(c, physics, blocks, (mesh["faces"], mesh["shift"]), ghost=ghost)
         self.info = sdrt_get_mesh_info(c, self.id)
         self.layouts = [sdrt_get_block_layout(c, self.id, b) for b in range(self.info["nblocks"])]
         self.dtype_np = np.float32 if self.info["precision"] == 1 else np.float64

@@ -1,0 +1,186 @@
+"""Partitions of a mesh for a distributed residual, host side (no GPU): the
+partition plans (owned and ghost elements, faces, exchange lists), their
+set-up in a host-only library context, the error codes, and the exchange of
+packed face records between two processes with torch.distributed (gloo),
+each record tagged with the (global element, face) it carries."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+from inputs import meshes  # noqa: E402
+
+sdrt = pytest.importorskip("paper_2105_08632_gb300.sdrt")
+from paper_2105_08632_gb300 import partition as pt  # noqa: E402
+
+
+def _owners(mesh, scheme, nparts):
+    n = sum(len(b["verts"]) for b in mesh["blocks"])
+    if scheme == "slabs":                        # contiguous runs of elements: z slabs of the box
+        return (np.arange(n) * nparts) // n
+    return np.random.default_rng(5).integers(0, nparts, n)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(sdrt.LIB_PATH):
+        from paper_2105_08632_gb300 import build
+        build.build()
+    return sdrt.lib()
+
+
+@pytest.mark.parametrize("scheme,nparts", [("slabs", 3), ("random", 4)])
+def test_plan_invariants(scheme, nparts):
+    mesh = meshes.box_mesh("tet", (3, 3, 3), [0.0] * 3, [1.0] * 3)
+    owner = _owners(mesh, scheme, nparts)
+    plans = pt.split(mesh, owner, nparts)
+    nglob = len(owner)
+    seen = np.zeros(nglob, int)
+    faces = np.asarray(mesh["faces"]).reshape(-1, 6)
+    off = pt.global_offsets(mesh)
+    gl = off[faces[:, 0]] + faces[:, 1]
+    gr = off[faces[:, 3]] + faces[:, 4]
+    for p, pl in enumerate(plans):
+        for b, ids in pl["owned"]:
+            seen[ids] += 1
+            assert (owner[ids] == p).all()
+        for b, ids in pl["ghosts"]:
+            assert (owner[ids] != p).all()
+        # owned blocks first, then ghosts
+        g = pl["ghost"]
+        assert (np.diff(g.astype(int)) >= 0).all() and g[0] == 0
+        # the partition's faces are the global faces touching its elements, L / R order kept
+        touch = (owner[gl] == p) | (owner[gr] == p)
+        assert len(pl["mesh"]["faces"]) == int(touch.sum())
+        inv = {v: k for k, v in pl["local"].items()}
+        for row, fi in zip(pl["mesh"]["faces"], np.nonzero(touch)[0]):
+            assert inv[(row[0], row[1])] == gl[fi] and inv[(row[3], row[4])] == gr[fi]
+            assert row[2] == faces[fi, 2] and row[5] == faces[fi, 5]
+        # exchange lists agree pairwise and name ghost faces glued to owned elements
+        for q, keys in pl["keys_recv"].items():
+            assert np.array_equal(keys, plans[q]["keys_send"][p])
+            assert (owner[keys[:, 0]] == q).all()
+            for (G, f), (b, e, f2) in zip(keys, pl["recv"][q]):
+                assert g[b] == 1 and inv[(b, e)] == G and f2 == f
+            for (G, f), (b, e, f2) in zip(keys, plans[q]["send"][p]):
+                assert plans[q]["ghost"][b] == 0 and {v: k for k, v in plans[q]["local"].items()}[(b, e)] == G
+        # every face between p and another partition appears once in p's receive keys
+        cross = set()
+        for fi in range(len(faces)):
+            for G, f, H in ((gl[fi], faces[fi, 2], gr[fi]), (gr[fi], faces[fi, 5], gl[fi])):
+                if owner[H] == p and owner[G] != p:
+                    cross.add((int(G), int(f)))
+        got = {tuple(k) for keys in pl["keys_recv"].values() for k in keys.tolist()}
+        assert got == cross
+    assert (seen == 1).all()
+
+
+def test_partition_setup_in_host_context(lib):
+    mesh = meshes.box_mesh("tet", (3, 3, 3), [0.0] * 3, [1.0] * 3)
+    owner = _owners(mesh, "random", 3)
+    plans = pt.split(mesh, owner, 3)
+    ctx = sdrt.Context(-1)
+    try:
+        phys = sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4)
+        total = 0
+        for pl in plans:
+            pm = pt.PartitionMesh(ctx, pl, 3, phys)
+            nown = sum(len(ids) for _, ids in pl["owned"])
+            total += nown
+            assert pm.info["ndof"] == 20 * 5 * nown
+            assert pm.info["nblocks"] == len(pl["owned"])
+            assert pm.state_len == sum(20 * 5 * ((len(ids) + 31) // 32 * 32) for _, ids in pl["owned"])
+            x = pm.xinfo
+            assert x["nsend"] == sum(len(a) for a in pl["send"].values())
+            assert x["nrecv"] == sum(len(a) for a in pl["recv"].values())
+            assert x["face_record"] == 52                     # 10 points x 5 variables, padded to 4
+            with pytest.raises(sdrt.SdrtError):                # no device work in a host-only context
+                pm.residual_begin(1)                           # (a raw pointer reaches the library)
+        assert total == len(owner)
+    finally:
+        ctx.close()
+
+
+def test_partition_errors(lib):
+    ctx = sdrt.sdrt_create(-1)
+    try:
+        mesh = meshes.box_mesh("tet", (2, 2, 2), [0.0] * 3, [1.0] * 3)
+        pl = pt.split(mesh, _owners(mesh, "slabs", 2), 2)[0]
+        phys = sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4)
+        et = sdrt.sdrt_setup_element_type(ctx, "tet", 3)
+        blocks = [(et, b["verts"]) for b in pl["mesh"]["blocks"]]
+        faces = (pl["mesh"]["faces"], pl["mesh"]["shift"])
+        with pytest.raises(sdrt.SdrtError):                    # ghost block before an owned one
+            sdrt.sdrt_setup_partition(ctx, phys, blocks[::-1], pl["ghost"][::-1].copy(), faces)
+        mid = sdrt.sdrt_setup_partition(ctx, phys, blocks, pl["ghost"], faces)
+        with pytest.raises(sdrt.SdrtError):                    # a ghost face in the send list
+            sdrt.sdrt_set_exchange(ctx, mid, pt.concat(pl["recv"]), pt.concat(pl["recv"]))
+        with pytest.raises(sdrt.SdrtError):                    # element out of range
+            sdrt.sdrt_set_exchange(ctx, mid, np.array([[0, 10 ** 6, 0]]), np.zeros((0, 3)))
+        with pytest.raises(sdrt.SdrtError):                    # unglued face on an owned element
+            sdrt.sdrt_setup_partition(ctx, phys, blocks, pl["ghost"],
+                                      (pl["mesh"]["faces"][1:], pl["mesh"]["shift"][1:]))
+        # partitions need the record path: hexahedra are refused
+        hmesh = meshes.box_mesh("hex", (2, 2, 2), [0.0] * 3, [1.0] * 3)
+        hpl = pt.split(hmesh, _owners(hmesh, "slabs", 2), 2)[0]
+        het = sdrt.sdrt_setup_element_type(ctx, "hex", 2)
+        with pytest.raises(sdrt.SdrtError):
+            sdrt.sdrt_setup_partition(ctx, phys, [(het, b["verts"]) for b in hpl["mesh"]["blocks"]], hpl["ghost"],
+                                      (hpl["mesh"]["faces"], hpl["mesh"]["shift"]))
+    finally:
+        sdrt.sdrt_destroy(ctx)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _tag(keys, fr):
+    """Record values carrying (G, f): value k of the record of (G, f) is (8 G + f) * 64 + k."""
+    k = np.arange(fr)
+    return ((8 * keys[:, 0:1] + keys[:, 1:2]) * 64 + k[None, :]).astype(np.float64)
+
+
+def _exchange_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mesh = meshes.box_mesh("tet", (3, 3, 4), [0.0] * 3, [1.0] * 3)
+        n = sum(len(b["verts"]) for b in mesh["blocks"])
+        owner = np.random.default_rng(11).integers(0, world, n)
+        plan = pt.split(mesh, owner, world)[rank]
+        fr = 52
+        send = {q: torch.from_numpy(_tag(k, fr).reshape(-1)) for q, k in plan["keys_send"].items()}
+        recv = {q: torch.zeros(len(k) * fr, dtype=torch.float64) for q, k in plan["keys_recv"].items()}
+        pt.exchange(send, recv)
+        ok = all(np.array_equal(recv[q].numpy(), _tag(k, fr).reshape(-1)) for q, k in plan["keys_recv"].items())
+        nrec = sum(len(k) for k in plan["keys_recv"].values())
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (ok, nrec))
+        if rank == 0:
+            out.put(gathered)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_face_record_exchange_between_two_processes():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_exchange_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for ok, _ in res), res
+    assert all(n > 0 for _, n in res)
