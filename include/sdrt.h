@@ -60,7 +60,23 @@ typedef enum { SDRT_FP64 = 0, SDRT_FP32 = 1 } sdrt_precision;
 typedef struct {
     int32_t shape;   /* sdrt_shape */
     int32_t degree;  /* p >= 1; p <= 4 validated (simplices are unstable for p >= 5, Sec. 3.1.1) */
+    int32_t scheme;  /* SDRT_SCHEME_SDRT (0) or SDRT_SCHEME_FR (1) */
 } sdrt_etype_desc;
+
+/* Schemes of an element type.
+ *   SDRT_SCHEME_SDRT: the spectral difference Raviart-Thomas residual (Sec. 2.1).
+ *   SDRT_SCHEME_FR:   FR-SDRT (Sec. 2.3, Eq. "divergence_fr" with the correction
+ *     field's divergence taken from the RT external-point functions): the
+ *     transformed flux at the solution points, differentiated there, plus
+ *     M14 (F~_fe - (M0 f~) . n~).  It runs on the same kernels as SDRT with the
+ *     internal DOFs at the solution points ((r, d) for solution point r and axis
+ *     d; M12 = I) and the divergence operator M13_FR[s, (r, d)] = (M15 P M12)[(d, s), r],
+ *     which the identities D = M16 M0 + M15 P M12 (exact reference gradient of
+ *     the solution space) and M16[(d, s), j] = n~_jd M14[s, j] turn the FR
+ *     correction into; the viscous gradient operator is the same as SDRT's.
+ *     Generic kernels only (no record path). */
+#define SDRT_SCHEME_SDRT 0
+#define SDRT_SCHEME_FR 1
 
 /* Counts of one element type (paper App. A, Tables "nsolpts_nfpts", "nfpts_extra"). */
 typedef struct {

@@ -666,6 +666,43 @@ int residual_end_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* R) {
     return SDRT_OK;
 }
 
+// FR-SDRT operators from the SDRT ones (Sec. 2.3): internal DOFs at the
+// solution points, nu = r nd + d (point r, reference axis d), M12 = I,
+// M13_FR[s, nu] = (M15 P M12)[(d, s), r], and M15_FR with M15_FR P_FR = M15 P M12
+// (the same viscous gradient operator; the axis-0 DOF of each point carries it).
+RefElement fr_variant(const RefElement& S) {
+    RefElement R = S;
+    const int nd = S.nd, ns = S.nsol;
+    std::vector<double> G((size_t)nd * ns * ns, 0.0);      // M15 P M12: (nd ns) x ns
+    for (int m = 0; m < nd * ns; ++m)
+        for (int mu = 0; mu < S.nfi; ++mu) {
+            const double a = S.M15[(size_t)m * S.nfi + mu];
+            if (a == 0.0) continue;
+            const double* row = &S.M12[(size_t)S.fi_point[mu] * ns];
+            for (int r = 0; r < ns; ++r) G[(size_t)m * ns + r] += a * row[r];
+        }
+    R.nfiu = ns;
+    R.nfi = nd * ns;
+    R.xfiu = S.xs;
+    R.fi_point.resize(R.nfi);
+    R.fi_axis.resize(R.nfi);
+    for (int r = 0; r < ns; ++r)
+        for (int d = 0; d < nd; ++d) {
+            R.fi_point[r * nd + d] = r;
+            R.fi_axis[r * nd + d] = d;
+        }
+    R.M12.assign((size_t)ns * ns, 0.0);
+    for (int r = 0; r < ns; ++r) R.M12[(size_t)r * ns + r] = 1.0;
+    R.M13.assign((size_t)ns * R.nfi, 0.0);
+    R.M15.assign((size_t)nd * ns * R.nfi, 0.0);
+    for (int s = 0; s < ns; ++s)
+        for (int r = 0; r < ns; ++r)
+            for (int d = 0; d < nd; ++d) R.M13[(size_t)s * R.nfi + r * nd + d] = G[((size_t)d * ns + s) * ns + r];
+    for (int m = 0; m < nd * ns; ++m)
+        for (int r = 0; r < ns; ++r) R.M15[(size_t)m * R.nfi + r * nd] = G[(size_t)m * ns + r];
+    return R;
+}
+
 }  // namespace
 
 extern "C" {
@@ -717,8 +754,10 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
     if (!ctx || !d || !etype_id) return fail(ctx, SDRT_ERR_ARG, "null argument");
     if (d->shape < 0 || d->shape > 4) return fail(ctx, SDRT_ERR_ARG, "unknown shape");
     if (d->degree < 1 || d->degree > 6) return fail(ctx, SDRT_ERR_UNSUPPORTED, "degree must be in 1..6");
+    if (d->scheme != SDRT_SCHEME_SDRT && d->scheme != SDRT_SCHEME_FR) return fail(ctx, SDRT_ERR_ARG, "unknown scheme");
     for (size_t i = 0; i < ctx->etypes.size(); ++i)
-        if (ctx->etypes[i]->desc.shape == d->shape && ctx->etypes[i]->desc.degree == d->degree) {
+        if (ctx->etypes[i]->desc.shape == d->shape && ctx->etypes[i]->desc.degree == d->degree &&
+            ctx->etypes[i]->desc.scheme == d->scheme) {
             *etype_id = (int)i;
             return SDRT_OK;
         }
@@ -726,6 +765,7 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
     et->desc = *d;
     try {
         et->R = build_ref_element(d->shape, d->degree);
+        if (d->scheme == SDRT_SCHEME_FR) et->R = fr_variant(et->R);
     } catch (const std::exception& ex) {
         return fail(ctx, SDRT_ERR_UNSUPPORTED, ex.what());
     }
@@ -884,7 +924,9 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         m->Ftot += (int64_t)R.nfe * mb->ld;
         m->ndof += (int64_t)R.nsol * m->nvar * B.nelem;
         canon += (int64_t)R.nfe * B.nelem;
-        if (!fast_path_available(R.shape, R.nsol, nd, phys->system, phys->riemann)) m->fast = false;
+        if (ctx->etypes[B.etype]->desc.scheme != SDRT_SCHEME_SDRT ||
+            !fast_path_available(R.shape, R.nsol, nd, phys->system, phys->riemann))
+            m->fast = false;
         if (phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES) {
             mb->qfiu_off = m->qfiu_total;
             m->qfiu_total += (int64_t)R.nfiu * nd * m->nvar * mb->ld;

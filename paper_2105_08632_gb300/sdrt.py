@@ -36,7 +36,10 @@ class SdrtError(RuntimeError):
 
 
 class EtypeDesc(ctypes.Structure):
-    _fields_ = [("shape", ctypes.c_int32), ("degree", ctypes.c_int32)]
+    _fields_ = [("shape", ctypes.c_int32), ("degree", ctypes.c_int32), ("scheme", ctypes.c_int32)]
+
+
+SCHEMES = {"sdrt": 0, "fr": 1}
 
 
 class EtypeInfo(ctypes.Structure):
@@ -160,9 +163,10 @@ def sdrt_set_stream(ctx, stream):
     _check(ctx, lib().sdrt_set_stream(ctx, stream))
 
 
-def sdrt_setup_element_type(ctx, shape, degree):
+def sdrt_setup_element_type(ctx, shape, degree, scheme="sdrt"):
     out = ctypes.c_int()
-    d = EtypeDesc(SHAPES[shape] if isinstance(shape, str) else int(shape), int(degree))
+    d = EtypeDesc(SHAPES[shape] if isinstance(shape, str) else int(shape), int(degree),
+                  SCHEMES[scheme] if isinstance(scheme, str) else int(scheme))
     _check(ctx, lib().sdrt_setup_element_type(ctx, ctypes.byref(d), ctypes.byref(out)))
     return out.value
 
@@ -376,7 +380,7 @@ class Context:
 class Mesh:
     """A mesh set up in a Context: mesh dict from inputs.meshes plus physics."""
 
-    def __init__(self, ctx, mesh, degree, physics, ghost=None):
+    def __init__(self, ctx, mesh, degree, physics, ghost=None, scheme="sdrt"):
         self.ctx = ctx
         c = ctx.ptr
         blocks = []
@@ -388,7 +392,7 @@ class Mesh:
                 p = degree[i]                  # one degree per block
             else:
                 p = degree[blk["shape"]]       # one degree per element shape
-            et = sdrt_setup_element_type(c, blk["shape"], p)
+            et = sdrt_setup_element_type(c, blk["shape"], p, scheme)
             self.etypes.append(et)
             blocks.append((et, blk["verts"]))
         self.id = sdrt_setup_mesh(c, physics, blocks, (mesh["faces"], mesh["shift"]), ghost=ghost)

@@ -33,13 +33,13 @@ def perturb(U, seed, amp):
 
 
 def build_pair(ctx, kind, n, degree, system="euler", riemann="rusanov", precision="fp64", lo=0.0, hi=1.0,
-               a=(1.0, 0.5, 0.25), **kw):
+               a=(1.0, 0.5, 0.25), scheme="sdrt", **kw):
     """Library Mesh and oracle (geom, physics) for the same seeded box mesh."""
     from paper_2105_08632_gb300 import sdrt
     nd = len(n)
     mesh = meshes.box_mesh(kind, n, [lo] * nd, [hi] * nd)
     phys = sdrt.make_physics(system, nd, riemann, precision, a=a, **kw)
-    M = sdrt.Mesh(ctx, mesh, degree, phys)
+    M = sdrt.Mesh(ctx, mesh, degree, phys, scheme=scheme)
     geom = omesh.build(mesh, degree)
     oph = ophx.Physics(system, nd, riemann, a=tuple(a), mu=kw.get("mu", 0.0), gamma=kw.get("gamma", 1.4),
                        Pr=kw.get("prandtl", 0.72), beta=kw.get("beta", 0.5), eta=kw.get("eta", 0.1))

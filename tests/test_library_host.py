@@ -59,6 +59,34 @@ def test_operators_match_oracle(hctx, shape, p):
         assert np.abs(got - want).max() < tol, (name, np.abs(got - want).max())
 
 
+@pytest.mark.parametrize("shape,p", CASES)
+def test_fr_scheme_operators(hctx, shape, p):
+    """FR-SDRT element types (Sec. 2.3): internal DOFs (r, d) at the solution
+    points, M12 = I, and a divergence operator equal to the oracle's FR form
+    written out with its own differentiation matrices (from the Vandermonde
+    derivatives):  M13_FR[s, (r, d)] = D_d[s, r] - sum_j M14[s, j] M0[j, r] n~_jd."""
+    et = sdrt.sdrt_setup_element_type(hctx, shape, p, "fr")
+    info = sdrt.sdrt_get_etype_info(hctx, et)
+    ref = oops.get(shape, p)
+    nd, ns = ref.nd, ref.n_sol
+    assert (info["nsol"], info["nfe"], info["nfi"], info["nfiu"]) == (ns, ref.n_fe, nd * ns, ns)
+    np.testing.assert_array_equal(sdrt.sdrt_get_operator(hctx, et, "M12"), np.eye(ns))
+    want = np.zeros((ns, ns, nd))
+    for d in range(nd):
+        want[:, :, d] = ref.Dsol[d] - np.einsum("sj,jr,j->sr", ref.M14, ref.M0, ref.nrm_fe[:, d])
+    got = sdrt.sdrt_get_operator(hctx, et, "M13")
+    tol = 1e-11 * max(1.0, np.abs(want).max()) * max(1.0, ref.cond_flux / 1e3)
+    assert np.abs(got - want.reshape(ns, ns * nd)).max() < tol
+    # the viscous gradient operator M15 P M12 is SDRT's
+    sd = sdrt.sdrt_setup_element_type(hctx, shape, p)
+    def grad_op(e, nfi, fi_point):
+        M15 = sdrt.sdrt_get_operator(hctx, e, "M15")
+        M12 = sdrt.sdrt_get_operator(hctx, e, "M12")
+        return M15 @ M12[fi_point]
+    fr_pt = np.repeat(np.arange(ns), nd)
+    np.testing.assert_allclose(grad_op(et, nd * ns, fr_pt), grad_op(sd, ref.n_fi, ref.fi_point), atol=tol)
+
+
 MESHES = [("tri", (5, 3), 2), ("quad", (3, 4), 3), ("tet", (3, 2, 2), 3), ("pri", (2, 3, 2), 2),
           ("hex", (2, 2, 3), 2), ("tet", (2, 2, 2), 4)]
 
