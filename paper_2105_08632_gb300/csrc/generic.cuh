@@ -82,7 +82,7 @@ __device__ __forceinline__ void ld_b(const Dual<T>* p, Dual<T> (&b)[CW]) {
     for (int j = 0; j < CW; ++j) b[j] = p[j];
 }
 
-template <int CW, typename S, typename T, typename Store>
+template <int CW, bool PAIRED, typename S, typename T, typename Store>
 __device__ __forceinline__ void tile_gemm_cw(const T* __restrict__ At, int ldA, int M, int K, const S* B0, int ksplit,
                                              const S* B1, int NCOL, Store store) {
     const int nrb = (M + kMR - 1) / kMR;
@@ -97,16 +97,55 @@ __device__ __forceinline__ void tile_gemm_cw(const T* __restrict__ At, int ldA, 
             #pragma unroll
             for (int j = 0; j < CW; ++j) acc[i][j] = szero<S>();
         const T* a = At + rb * kMR;
-        #pragma unroll 2
-        for (int k = 0; k < K; ++k) {
-            S b[CW];
-            ld_b<CW>((k < ksplit ? B0 + (size_t)k * NCOL : B1 + (size_t)(k - ksplit) * NCOL) + col0, b);
-            T av[kMR];
-            ld_a8(a + (size_t)k * ldA, av, avec);
+        if constexpr (PAIRED && std::is_same<S, float>::value && std::is_same<T, float>::value && CW == 4) {
+            // Paired FP32 FMA (two IEEE fmas per instruction, sm_100+), rows and
+            // columns paired crosswise: D = (r c, r+1 c+1) += (a_r, a_r+1)(b_c, b_c+1),
+            // X = (r c+1, r+1 c) += (a_r, a_r+1)(b_c+1, b_c) -- the same sums, in
+            // the same order, as the scalar loop below.
+            float2 d[kMR / 2][2], x[kMR / 2][2];
             #pragma unroll
-            for (int i = 0; i < kMR; ++i)
+            for (int q = 0; q < kMR / 2; ++q)
                 #pragma unroll
-                for (int j = 0; j < CW; ++j) mac(acc[i][j], av[i], b[j]);
+                for (int w = 0; w < 2; ++w) d[q][w] = x[q][w] = make_float2(0.f, 0.f);
+            #pragma unroll 2
+            for (int k = 0; k < K; ++k) {
+                float b[4];
+                ld_b<4>((k < ksplit ? B0 + (size_t)k * NCOL : B1 + (size_t)(k - ksplit) * NCOL) + col0, b);
+                float av[kMR];
+                ld_a8(a + (size_t)k * ldA, av, avec);
+                const float2 P[2] = {make_float2(b[0], b[1]), make_float2(b[2], b[3])};
+                const float2 Q[2] = {make_float2(b[1], b[0]), make_float2(b[3], b[2])};
+                #pragma unroll
+                for (int q = 0; q < kMR / 2; ++q) {
+                    const float2 A2 = make_float2(av[2 * q], av[2 * q + 1]);
+                    #pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        d[q][w] = __ffma2_rn(A2, P[w], d[q][w]);
+                        x[q][w] = __ffma2_rn(A2, Q[w], x[q][w]);
+                    }
+                }
+            }
+            #pragma unroll
+            for (int q = 0; q < kMR / 2; ++q)
+                #pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    acc[2 * q][2 * w] = d[q][w].x;
+                    acc[2 * q + 1][2 * w + 1] = d[q][w].y;
+                    acc[2 * q][2 * w + 1] = x[q][w].x;
+                    acc[2 * q + 1][2 * w] = x[q][w].y;
+                }
+        } else {
+            #pragma unroll 2
+            for (int k = 0; k < K; ++k) {
+                S b[CW];
+                ld_b<CW>((k < ksplit ? B0 + (size_t)k * NCOL : B1 + (size_t)(k - ksplit) * NCOL) + col0, b);
+                T av[kMR];
+                ld_a8(a + (size_t)k * ldA, av, avec);
+                #pragma unroll
+                for (int i = 0; i < kMR; ++i)
+                    #pragma unroll
+                    for (int j = 0; j < CW; ++j) mac(acc[i][j], av[i], b[j]);
+            }
         }
         #pragma unroll
         for (int j = 0; j < CW; ++j) {
@@ -126,12 +165,16 @@ __device__ __forceinline__ void tile_gemm_cw(const T* __restrict__ At, int ldA, 
 // i.e. kMR x CW FMAs per three loads.  CW = 4 when NCOL is a multiple of 4
 // (B rows then start 16-byte aligned), else 1.  Every thread must call it
 // (no barrier inside); rows >= M of the last block read zero-padded operator
-// entries and are dropped by the store functor.
-template <typename S, typename T, typename Store>
+// entries and are dropped by the store functor.  PAIRED (FP32, CW = 4): the
+// paired FP32 FMA, bit-identical sums; it pays where the GEMM is issue-bound
+// (the interpolation kernel) and not where the tile is latency-bound.
+template <typename S, typename T, bool PAIRED = false, typename Store>
 __device__ __forceinline__ void tile_gemm(const T* __restrict__ At, int ldA, int M, int K, const S* B0, int ksplit,
                                           const S* B1, int NCOL, Store store) {
-    if (NCOL % 4 == 0 && aligned16(B0) && aligned16(B1)) tile_gemm_cw<4>(At, ldA, M, K, B0, ksplit, B1, NCOL, store);
-    else tile_gemm_cw<1>(At, ldA, M, K, B0, ksplit, B1, NCOL, store);
+    if (NCOL % 4 == 0 && aligned16(B0) && aligned16(B1))
+        tile_gemm_cw<4, PAIRED>(At, ldA, M, K, B0, ksplit, B1, NCOL, store);
+    else
+        tile_gemm_cw<1, false>(At, ldA, M, K, B0, ksplit, B1, NCOL, store);
 }
 
 template <typename S, typename T>
@@ -200,7 +243,7 @@ __global__ void __launch_bounds__(256) k_interp_ext(KTable<T> tab, const T* __re
         __syncthreads();
         load_tile<T, T, V>(B, U, nullptr, e0, TE, Us);
         __syncthreads();
-        tile_gemm<T, T>(B.Ai, B.Mi_pad, B.nfe, B.nsol, Us, B.nsol, Us, NCOL,
+        tile_gemm<T, T, true>(B.Ai, B.Mi_pad, B.nfe, B.nsol, Us, B.nsol, Us, NCOL,
                         [&](int m0, int col, const T* acc) {
                             const int v = col / TE, te = col - v * TE, e = e0 + te;
                             if (e >= B.nelem) return;
