@@ -29,6 +29,16 @@ constexpr int kMR = 8;   // rows of a GEMM micro tile
 
 __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Grid of a persistent kernel (256 threads, blocks walking tiles): every CTA
+// that fits on an SM at this shared-memory size, at most one per tile.
+template <typename K>
+inline int persistent_grid(K kernel, int smem, int tiles, int nsm) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, smem) != cudaSuccess || per < 1) per = 1;
+    const int cap = per * nsm;
+    return tiles < 1 ? 1 : (tiles < cap ? tiles : cap);
+}
+
 // 8 consecutive operator entries (16-byte loads when aligned).
 __device__ __forceinline__ void ld_a8(const float* p, float (&a)[8], bool vec) {
     if (vec) {
@@ -507,11 +517,11 @@ __global__ void __launch_bounds__(256) k_residual(KTable<T> tab, const T* __rest
 // Launch of one k_residual instantiation (host side).
 template <typename S, typename T, int V, int ND, int SYS, int RIE>
 inline void launch_res_impl(const KTable<T>& tab, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
-                            const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int smem, int grid,
+                            const KPhys<T>& P, const KEpi<T>& E, const KVisc<T>& Q, int smem, int tiles, int nsm,
                             cudaStream_t st) {
     auto k = k_residual<S, T, V, ND, SYS, RIE>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k<<<grid, 256, smem, st>>>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q);
+    k<<<persistent_grid(k, smem, tiles, nsm), 256, smem, st>>>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q);
 }
 
 }  // namespace sdrt

@@ -17,13 +17,13 @@ void launch_interp_ext(const KSet<T>& ks, int V, const T* U, T* UFE, int64_t Fto
         smem = b > smem ? b : smem;
     }
     const int tiles = ks.tiles(TK_INTERP);
-    const int grid = tiles < 4 * nsm ? (tiles > 0 ? tiles : 1) : 4 * nsm;
     const KTable<T> tab = ks.table();
     switch (V) {
 #define SDRT_CASE(VV)                                                                                   \
     case VV:                                                                                            \
         cudaFuncSetAttribute(k_interp_ext<T, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);   \
-        k_interp_ext<T, VV><<<grid, 256, smem, st>>>(tab, U, UFE, Ftot);                                 \
+        k_interp_ext<T, VV><<<persistent_grid(k_interp_ext<T, VV>, smem, tiles, nsm), 256, smem, st>>>(   \
+            tab, U, UFE, Ftot);                                                                         \
         break;
         SDRT_CASE(1)
         SDRT_CASE(4)
@@ -56,10 +56,9 @@ int launch_residual(const KSet<T>& ks, int system, int riemann, int nd, const T*
         smem = b > smem ? b : smem;
     }
     const int tiles = ks.tiles(kind);
-    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
     const KTable<T> tab = ks.table();
 #define SDRT_DISPATCH(SS, VV, NDD, SYSS, RIEE) \
-    launch_res_impl<SS, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, grid, st)
+    launch_res_impl<SS, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, tiles, nsm, st)
     if (system == SYS_ADVECTION) {
         if (nd == 2) {
             if (dual) SDRT_DISPATCH(Dual<T>, 1, 2, SYS_ADVECTION, RIE_UPWIND);

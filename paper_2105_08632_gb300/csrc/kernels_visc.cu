@@ -133,11 +133,11 @@ int grad_smem(const KBlock<T>& B, int V, int nd, int TE, bool dual) {
 
 template <typename S, typename T, int V, int ND>
 static void launch_grad_impl(const KTable<T>& tab, const T* U, const T* dU, const T* UFE, const T* dUFE, int64_t Ftot,
-                             const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int smem, int grid,
+                             const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int smem, int tiles, int nsm,
                              cudaStream_t st) {
     auto k = k_grad<S, T, V, ND>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k<<<grid, 256, smem, st>>>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU);
+    k<<<persistent_grid(k, smem, tiles, nsm), 256, smem, st>>>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU);
 }
 
 template <typename T>
@@ -153,15 +153,14 @@ int launch_grad(const KSet<T>& ks, int system, int nd, const T* U, const T* dU, 
         smem = b > smem ? b : smem;
     }
     const int tiles = ks.tiles(kind);
-    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
     const KTable<T> tab = ks.table();
 #define SDRT_GRAD(VV, NDD)                                                                                          \
     do {                                                                                                            \
         if (dual)                                                                                                   \
             launch_grad_impl<Dual<T>, T, VV, NDD>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, smem,     \
-                                                  grid, st);                                                        \
+                                                  tiles, nsm, st);                                                        \
         else                                                                                                        \
-            launch_grad_impl<T, T, VV, NDD>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, smem, grid, st); \
+            launch_grad_impl<T, T, VV, NDD>(tab, U, dU, UFE, dUFE, Ftot, P, QFE, dQFE, QFIU, dQFIU, smem, tiles, nsm, st); \
     } while (0)
     if (system == SYS_ADVDIFF) {
         if (nd == 2) SDRT_GRAD(1, 2);
@@ -191,15 +190,14 @@ int launch_residual_visc(const KSet<T>& ks, int system, int riemann, int nd, con
         smem = b > smem ? b : smem;
     }
     const int tiles = ks.tiles(kind);
-    const int grid = tiles < 2 * nsm ? tiles : 2 * nsm;
     const KTable<T> tab = ks.table();
 #define SDRT_RES(VV, NDD, SYSS, RIEE)                                                                             \
     do {                                                                                                          \
         if (dual)                                                                                                 \
-            launch_res_impl<Dual<T>, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, grid,    \
+            launch_res_impl<Dual<T>, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, tiles, nsm,    \
                                                              st);                                                 \
         else                                                                                                      \
-            launch_res_impl<T, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, grid, st);     \
+            launch_res_impl<T, T, VV, NDD, SYSS, RIEE>(tab, U, dU, UFE, dUFE, Ftot, P, E, Q, smem, tiles, nsm, st);     \
     } while (0)
     if (system == SYS_ADVDIFF) {
         if (nd == 2) SDRT_RES(1, 2, SYS_ADVDIFF, RIE_UPWIND);
