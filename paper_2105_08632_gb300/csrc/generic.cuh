@@ -395,7 +395,9 @@ __device__ __forceinline__ void load_grad(const T* Q, const T* dQ, size_t base, 
 // Full residual of one block (S = T: value; S = Dual<T>: JVP).  Viscous systems
 // read the physical gradients at the flux points from Q (written by k_grad).
 template <typename S, typename T, int V, int ND, int SYS, int RIE>
-__global__ void __launch_bounds__(256) k_residual(KTable<T> tab, const T* __restrict__ U, const T* __restrict__ dU,
+__global__ void __launch_bounds__(256, (std::is_same<S, float>::value && (SYS == SYS_EULER || SYS == SYS_ADVECTION))
+                                               ? 3    // inviscid FP32: three CTAs per SM (a few spills; measured faster)
+                                               : 1) k_residual(KTable<T> tab, const T* __restrict__ U, const T* __restrict__ dU,
                                                   const T* __restrict__ UFE, const T* __restrict__ dUFE, int64_t Ftot,
                                                   KPhys<T> P, KEpi<T> E, KVisc<T> Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
