@@ -1,0 +1,38 @@
+"""Host-side pieces of bench.py: the algorithmic byte model (per RK4 step, per
+kernel kind) against the sizes written out by hand for the benchmark element
+(tetrahedron, p = 3, Euler, FP32), and the workload labels."""
+import pytest
+
+bench = pytest.importorskip("bench")
+
+TET3 = {"nsol": 20, "nfe": 40, "nfiu": 10, "nfaces": 4, "ndim": 3}
+
+
+def test_record_path_bytes_per_element():
+    s, V = 4, 5
+    b = bench.algorithmic_bytes(TET3, 1, V, s, record=True, viscous=False)
+    # interpolation: read U (20 x 5), write 40 + 10 point states -> 70 x 5 x 4 B, four per step
+    assert b["interp_ext"] == 4 * 1400
+    # flux per stage: own + partner external states (2 x 40 x 5 x 4 = 1,600), internal
+    # states (200), metric 26 values (104), permutation 40 B, partner offsets 16 B;
+    # stage updates 13 state volumes of 400 B per step
+    assert b["residual"] == 4 * (1600 + 200 + 104 + 40 + 16) + 13 * 400
+
+
+def test_fused_rk_bytes_per_element():
+    s, V = 4, 5
+    unf = bench.algorithmic_bytes(TET3, 1, V, s, record=True, viscous=False)
+    fus = bench.algorithmic_bytes(TET3, 1, V, s, record=True, viscous=False, fused=True)
+    # one interpolation per step instead of four
+    assert fus["interp_ext"] == unf["interp_ext"] / 4
+    # stages 1-3 write the next records (50 point states) instead of the stage state
+    assert fus["residual"] == unf["residual"] - 3 * 400 + 3 * 50 * V * s
+    total_unf = sum(unf.values())
+    total_fus = sum(fus.values())
+    assert total_fus < total_unf
+
+
+def test_workload_labels():
+    assert bench.workload_label("euler") == "euler3d_tet_p3_82944_rk4"
+    assert bench.workload_label("tgv") == "tgv_ns_tet_p4_663552_rk4"
+    assert bench.workload_label("mixed").startswith("mixed_euler_") and bench.workload_label("mixed").endswith("_rk4")
