@@ -34,9 +34,11 @@ def lib():
     return sdrt.lib()
 
 
-@pytest.mark.parametrize("scheme,nparts", [("slabs", 3), ("random", 4)])
-def test_plan_invariants(scheme, nparts):
-    mesh = meshes.box_mesh("tet", (3, 3, 3), [0.0] * 3, [1.0] * 3)
+@pytest.mark.parametrize("kinds,scheme,nparts", [("tet", "slabs", 3), ("tet", "random", 4),
+                                                 (["tet", "pri", "tet"], "random", 3), (["hex", "pri_x"], "slabs", 2)])
+def test_plan_invariants(kinds, scheme, nparts):
+    n = (3, 3, 3) if isinstance(kinds, str) else (3, 2, len(kinds))
+    mesh = meshes.box_mesh(kinds, n, [0.0] * 3, [1.0] * 3)
     owner = _owners(mesh, scheme, nparts)
     plans = pt.split(mesh, owner, nparts)
     nglob = len(owner)
