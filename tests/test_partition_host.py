@@ -186,3 +186,35 @@ def test_face_record_exchange_between_two_processes():
         assert p.exitcode == 0
     assert all(ok for ok, _ in res), res
     assert all(n > 0 for _, n in res)
+
+
+@pytest.mark.parametrize("scheme,nparts", [("slabs", 2), ("random", 3)])
+def test_partition_face_maps_match_the_whole_mesh(lib, scheme, nparts):
+    """The face pairing of every partition (owned points glued to owned or ghost
+    points), mapped back to global (element, point) ids, is the whole mesh's
+    face map bit for bit, L / R sides included."""
+    mesh = meshes.box_mesh("tet", (3, 3, 2), [0.0] * 3, [1.0] * 3)
+    owner = _owners(mesh, scheme, nparts)
+    plans = pt.split(mesh, owner, nparts)
+    ctx = sdrt.Context(-1)
+    try:
+        phys = sdrt.make_physics("euler", 3, "rusanov", "fp64", gamma=1.4)
+        W = sdrt.Mesh(ctx, mesh, 3, phys)
+        wpart, wleft = W.face_map()
+        nfe = 40
+        for pl in plans:
+            pm = pt.PartitionMesh(ctx, pl, 3, phys)
+            part, left = pm.face_map()
+            gid = [ids for _, ids in pl["owned"]] + [ids for _, ids in pl["ghosts"]]
+            base = np.concatenate([[0], np.cumsum([len(i) * nfe for i in gid])])
+            for b in range(len(pl["owned"])):
+                for e, G in enumerate(gid[b]):
+                    for s in range(nfe):
+                        g = base[b] + e * nfe + s
+                        q = int(part[g])
+                        qb = int(np.searchsorted(base, q, side="right") - 1)
+                        qe, qs = divmod(q - int(base[qb]), nfe)
+                        assert (int(gid[qb][qe]) * nfe + qs) == int(wpart[G * nfe + s])
+                        assert left[g] == wleft[G * nfe + s]
+    finally:
+        ctx.close()
