@@ -267,10 +267,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Sources the record-path kernels (k_interp_pipe, k_flux_rec) and their
-# record layouts are built from; a change to any of them makes the committed
-# ncu counters stale.
-RECORD_PATH_SOURCES = ("api.cpp", "device_math.cuh", "flux_rec.cuh", "kargs.hpp", "kernels_fast.cu", "launch.hpp")
+# Sources the record-path kernels (k_interp_pipe, k_flux_rec) are compiled
+# from; a change to any of them makes the committed ncu counters stale.
+RECORD_PATH_SOURCES = ("device_math.cuh", "flux_rec.cuh", "kargs.hpp", "kernels_fast.cu")
 
 
 def kernel_sources_sha():

@@ -184,9 +184,11 @@ int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out);
  * elements (their vertices pair the face points; their other faces stay
  * unglued; no residual is computed for them).  Ghost blocks come after the
  * owned ones; faces keep the L / R order of the whole mesh.  The state arrays
- * of the partition hold the owned blocks only.  Record path only: tetrahedra
- * of degree 3 or 4 with Euler / Rusanov or advection / upwind, one face-record
- * size (else SDRT_ERR_UNSUPPORTED).  Whole-mesh calls (sdrt_residual,
+ * of the partition hold the owned blocks only.  Inviscid systems (advection,
+ * Euler; SDRT_ERR_UNSUPPORTED for the viscous ones), any element types: the
+ * record path (tetrahedra of degree 3 / 4) exchanges whole face records of
+ * its record layout, the generic path the face points' states gathered from
+ * its face-state array.  Whole-mesh calls (sdrt_residual,
  * sdrt_rk4_step, sdrt_jvp, sdrt_vjp, ...) return SDRT_ERR_STATE on a
  * partition.  Host inputs are copied. */
 int sdrt_setup_partition(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
@@ -201,7 +203,8 @@ int sdrt_setup_partition(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, c
 int sdrt_set_exchange(sdrt_ctx* ctx, int mesh_id, int64_t nsend, const int32_t* send, int64_t nrecv,
                       const int32_t* recv);
 /* Counts of the exchange lists (-1 before sdrt_set_exchange) and the values per
- * face record (points per face x nvar, padded to a multiple of 4). */
+ * face record (points per face x nvar, padded to a multiple of 4; on meshes whose
+ * faces differ in point count, sized for the largest face, the rest zero). */
 int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record);
 
 /* Partitioned residual, first half: interpolation of the owned blocks to
@@ -214,7 +217,8 @@ int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* sen
  * (device, nrecv x face_record values) fills the ghost faces, then the common
  * and internal fluxes and the divergence of the owned blocks give R_dev =
  * dU/dt (owned state layout).  Same values as sdrt_residual on the whole
- * mesh, element by element. */
+ * mesh, element by element.  The generic path reads the state passed to
+ * sdrt_residual_begin again here: it must stay valid and unchanged in between. */
 int sdrt_residual_end(sdrt_ctx* ctx, int mesh_id, const void* recv_dev, void* R_dev);
 int sdrt_get_block_layout(sdrt_ctx* ctx, int mesh_id, int block, sdrt_block_layout* out);
 

@@ -109,7 +109,9 @@ struct Mesh {
     std::vector<std::unique_ptr<MBlock>> ghosts;
     int xfrec = 0;                    // values per exchanged face record
     int64_t nsend = -1, nrecv = -1;   // -1: no exchange lists yet
-    DevBuf xsend_off, xrecv_off;      // REC offsets of the sent / received face records
+    DevBuf xsend_off, xrecv_off;      // record path: REC offsets of the sent / received face records
+    DevBuf xsend_idx, xrecv_idx;      // generic path: UFE index of every record value (-1: padding)
+    const void* part_u = nullptr;     // generic path: the state of the last sdrt_residual_begin
     ~Mesh() {
         if (graph) cudaGraphExecDestroy(graph);
     }
@@ -620,6 +622,24 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
 // the records, then the packed face records to send.
 template <typename T>
 int residual_begin_impl(sdrt_ctx* ctx, Mesh& m, const T* U, T* send) {
+    if (!m.fast) {
+        // Generic path: the owned blocks' external-point states into UFE, then the
+        // send buffer gathered from it.
+        T* ufe = m.ufe.as<T>();
+        const KSet<T> ks = kset<T>(m);
+        const int s = prof_begin(ctx, KIND_INTERP);
+        launch_interp_ext<T>(ks, m.nvar, U, ufe, m.Ftot, ctx->nsm, ctx->stream);
+        prof_end(ctx, s);
+        ++ctx->launches;
+        if (m.nsend > 0) {
+            launch_gather_values<T>(ufe, send, m.xsend_idx.as<int>(), m.nsend * m.xfrec, false, ctx->nsm, ctx->stream);
+            ++ctx->launches;
+        }
+        m.part_u = U;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+        return SDRT_OK;
+    }
     T* rec = m.rec.as<T>();
     T* fiur = m.fiur.as<T>();
     for (auto& bp : m.blocks) {
@@ -643,6 +663,29 @@ int residual_begin_impl(sdrt_ctx* ctx, Mesh& m, const T* U, T* send) {
 // and divergence of the owned blocks.
 template <typename T>
 int residual_end_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* R) {
+    if (!m.fast) {
+        T* ufe = m.ufe.as<T>();
+        if (!m.part_u) return fail(ctx, SDRT_ERR_STATE, "sdrt_residual_end before sdrt_residual_begin");
+        if (m.nrecv > 0) {
+            launch_gather_values<T>(recv, ufe, m.xrecv_idx.as<int>(), m.nrecv * m.xfrec, true, ctx->nsm, ctx->stream);
+            ++ctx->launches;
+        }
+        const KPhys<T> P = make_phys<T>(m.phys);
+        KEpi<T> E{};
+        E.mode = EPI_STORE;
+        E.out = R;
+        E.flag = ctx->flag.as<int>();
+        const KSet<T> ks = kset<T>(m);
+        const int s = prof_begin(ctx, KIND_RESIDUAL);
+        const int r = launch_residual<T>(ks, m.phys.system, m.phys.riemann, m.nd, static_cast<const T*>(m.part_u),
+                                         nullptr, ufe, nullptr, m.Ftot, P, E, KVisc<T>{}, ctx->nsm, ctx->stream);
+        prof_end(ctx, s);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
+        ++ctx->launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+        return SDRT_OK;
+    }
     T* rec = m.rec.as<T>();
     T* fiur = m.fiur.as<T>();
     if (m.nrecv > 0) {
@@ -959,12 +1002,15 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
     }
     if (canon >= INT32_MAX || m->Ftot >= INT32_MAX) return fail(ctx, SDRT_ERR_UNSUPPORTED, "mesh too large for int32 maps");
     if (ghost) {
-        if (!m->fast)
-            return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions need the record path (tetrahedra of degree 3 or 4, "
-                                                   "Euler / Rusanov or advection / upwind)");
-        for (int b = 1; b < nblocks; ++b)
-            if (m->blocks[b]->frec != m->blocks[0]->frec)
-                return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions need one face-record size");
+        if (phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES)
+            return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions cover the inviscid systems");
+        if (m->fast) {
+            for (int b = 1; b < nblocks; ++b)
+                if (m->blocks[b]->frec != m->blocks[0]->frec)
+                    return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions need one face-record size");
+        } else if ((int64_t)m->nvar * m->Ftot >= INT32_MAX) {
+            return fail(ctx, SDRT_ERR_UNSUPPORTED, "partition too large for int32 face-state indices");
+        }
     }
 
     // Metrics, physical points.
@@ -1217,7 +1263,20 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         for (int b = nown; b < nblocks; ++b) m->ghosts.push_back(std::move(m->blocks[b]));
         m->blocks.resize(nown);
         m->partition = true;
-        m->xfrec = m->blocks[0]->frec;
+        if (m->fast) {
+            m->xfrec = m->blocks[0]->frec;
+        } else {
+            // Generic path: records of (points per face) x nvar values, padded to the
+            // largest face of the mesh's element types and to a multiple of 4.
+            int npf = 0;
+            for (int b = 0; b < nblocks; ++b) {
+                const MBlock& q = b < nown ? *m->blocks[b] : *m->ghosts[b - nown];
+                const RefElement& R = ctx->etypes[q.etype]->R;
+                std::vector<int> cnt(R.nfaces, 0);
+                for (int k = 0; k < R.nfe; ++k) npf = std::max(npf, ++cnt[R.fe_face[k]]);
+            }
+            m->xfrec = round_up(npf * m->nvar, 4);
+        }
     }
     // Block tables of the generic kernels (tile widths are final here).
     if (int rt = refresh_tables(ctx, *m)) return rt;
@@ -1315,9 +1374,37 @@ int sdrt_set_exchange(sdrt_ctx* ctx, int mesh_id, int64_t nsend, const int32_t* 
     std::vector<int> so, ro;
     if (!offsets(nsend, send, false, so)) return fail(ctx, SDRT_ERR_ARG, "send list: not an owned (block, element, face)");
     if (!offsets(nrecv, recv, true, ro)) return fail(ctx, SDRT_ERR_ARG, "receive list: not a ghost (block, element, face)");
-    if (!ctx->host_only) {
-        if (nsend > 0) SDRT_CUDA(upload(m.xsend_off, so));
-        if (nrecv > 0) SDRT_CUDA(upload(m.xrecv_off, ro));
+    if (m.fast) {
+        if (!ctx->host_only) {
+            if (nsend > 0) SDRT_CUDA(upload(m.xsend_off, so));
+            if (nrecv > 0) SDRT_CUDA(upload(m.xrecv_off, ro));
+        }
+    } else {
+        // Generic path: value k * nvar + v of a record is variable v of the face's
+        // k-th point (local point order) in the face-state array UFE.
+        auto indices = [&](int64_t n, const int32_t* t, std::vector<int>& out) {
+            out.assign((size_t)n * m.xfrec, -1);
+            for (int64_t i = 0; i < n; ++i) {
+                const int b = t[3 * i], e = t[3 * i + 1], f = t[3 * i + 2];
+                const MBlock& q = b < nown ? *m.blocks[b] : *m.ghosts[b - nown];
+                const RefElement& R = ctx->etypes[q.etype]->R;
+                int k = 0;
+                for (int sg = 0; sg < R.nfe; ++sg) {
+                    if (R.fe_face[sg] != f) continue;
+                    for (int v = 0; v < m.nvar; ++v)
+                        out[(size_t)i * m.xfrec + k * m.nvar + v] =
+                            (int)((int64_t)v * m.Ftot + q.fe_base + (int64_t)sg * q.ld + e);
+                    ++k;
+                }
+            }
+        };
+        std::vector<int> si, ri;
+        indices(nsend, send, si);
+        indices(nrecv, recv, ri);
+        if (!ctx->host_only) {
+            if (nsend > 0) SDRT_CUDA(upload(m.xsend_idx, si));
+            if (nrecv > 0) SDRT_CUDA(upload(m.xrecv_idx, ri));
+        }
     }
     m.nsend = nsend;
     m.nrecv = nrecv;

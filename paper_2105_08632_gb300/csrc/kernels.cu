@@ -34,6 +34,29 @@ void launch_interp_ext(const KSet<T>& ks, int V, const T* U, T* UFE, int64_t Fto
 }
 
 template <typename T>
+__global__ void k_gather_values(const T* __restrict__ src, T* __restrict__ dst, const int* __restrict__ idx, int64_t n,
+                                int scatter) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = idx[i];
+        if (scatter) {
+            if (j >= 0) dst[j] = src[i];
+        } else {
+            dst[i] = j >= 0 ? src[j] : T(0);
+        }
+    }
+}
+
+template <typename T>
+void launch_gather_values(const T* src, T* dst, const int* idx, int64_t n, bool scatter, int nsm, cudaStream_t st) {
+    if (n <= 0) return;
+    int64_t grid = (n + 255) / 256;
+    if (grid > 8 * (int64_t)nsm) grid = 8 * (int64_t)nsm;
+    k_gather_values<T><<<(int)grid, 256, 0, st>>>(src, dst, idx, n, scatter ? 1 : 0);
+}
+template void launch_gather_values<float>(const float*, float*, const int*, int64_t, bool, int, cudaStream_t);
+template void launch_gather_values<double>(const double*, double*, const int*, int64_t, bool, int, cudaStream_t);
+
+template <typename T>
 int residual_smem(const KBlock<T>& B, int V, int TE, bool dual, int* rowsA) {
     const int ra = B.nsol > B.nfi ? B.nsol : B.nfi;
     if (rowsA) *rowsA = ra;

@@ -117,6 +117,12 @@ template <typename T>
 void launch_face_records(const T* src, T* dst, const int* off, int64_t n, int len, bool scatter, int nsm,
                          cudaStream_t st);
 
+// n values between an array and a packed buffer through an index list (-1:
+// padding, gathered as zero, not scattered): gather dst[i] = src[idx[i]],
+// scatter dst[idx[i]] = src[i].
+template <typename T>
+void launch_gather_values(const T* src, T* dst, const int* idx, int64_t n, bool scatter, int nsm, cudaStream_t st);
+
 // Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,

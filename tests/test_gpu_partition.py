@@ -33,30 +33,39 @@ def _owners(n, scheme, nparts):
     return np.random.default_rng(9).integers(0, nparts, n)
 
 
-@pytest.mark.parametrize("system,precision,p,scheme,nparts", [
-    ("euler", "fp32", 3, "slabs", 3),
-    ("euler", "fp32", 3, "random", 4),
-    ("euler", "fp64", 3, "random", 3),
-    ("euler", "fp32", 4, "random", 2),
-    ("advection", "fp32", 3, "random", 3),
-    ("advection", "fp64", 4, "slabs", 2),
+@pytest.mark.parametrize("kinds,n,system,precision,p,scheme,nparts", [
+    # record path (tetrahedra of degree 3 / 4)
+    ("tet", (4, 4, 3), "euler", "fp32", 3, "slabs", 3),
+    ("tet", (4, 4, 3), "euler", "fp32", 3, "random", 4),
+    ("tet", (4, 4, 3), "euler", "fp64", 3, "random", 3),
+    ("tet", (4, 4, 3), "euler", "fp32", 4, "random", 2),
+    ("tet", (4, 4, 3), "advection", "fp32", 3, "random", 3),
+    ("tet", (4, 4, 3), "advection", "fp64", 4, "slabs", 2),
+    # generic path: other degrees and element types, mixed meshes, 2D
+    ("tet", (3, 3, 3), "euler", "fp32", 2, "random", 3),
+    ("hex", (3, 3, 3), "euler", "fp64", 2, "random", 4),
+    (["tet", "pri", "pri"], (3, 3, 3), "euler", "fp32", 2, "random", 3),
+    ("tri", (6, 5), "advection", "fp64", 3, "random", 3),
+    ("quad", (5, 4), "euler", "fp32", 3, "slabs", 2),
 ])
-def test_partitioned_residual_equals_whole_mesh(ctx, system, precision, p, scheme, nparts):
+def test_partitioned_residual_equals_whole_mesh(ctx, kinds, n, system, precision, p, scheme, nparts):
     from paper_2105_08632_gb300 import partition as pt
     from paper_2105_08632_gb300 import sdrt
-    mesh = meshes.box_mesh("tet", (4, 4, 3), [-1.0] * 3, [1.0] * 3)
-    kw = {"gamma": 1.4} if system == "euler" else {"a": (1.0, 0.5, 0.25)}
+    nd = len(n)
+    mesh = meshes.box_mesh(kinds, n, [-1.0] * nd, [1.0] * nd)
+    kw = {"gamma": 1.4} if system == "euler" else {"a": (1.0, 0.5, 0.25)[:nd]}
     riemann = "rusanov" if system == "euler" else "upwind"
-    phys = sdrt.make_physics(system, 3, riemann, precision, **kw)
+    phys = sdrt.make_physics(system, nd, riemann, precision, **kw)
     M = sdrt.Mesh(ctx, mesh, p, phys)
-    X = M.sol_points()[0]
     nv = M.nvar
-    if system == "euler":
-        u = gu.smooth_gas(X.reshape(-1, 3)).reshape(X.shape[0], X.shape[1], nv)
-    else:
-        u = np.sin(2 * X[..., :1]) * np.cos(X[..., 1:2] + 0.5 * X[..., 2:3])
-    u = u * (1 + 0.01 * np.random.default_rng(3).uniform(-1, 1, u.shape))
-    Ug = [np.ascontiguousarray(u.transpose(1, 2, 0))]
+    Ug = []
+    for b, X in enumerate(M.sol_points()):
+        if system == "euler":
+            u = gu.smooth_gas(X.reshape(-1, nd)).reshape(X.shape[0], X.shape[1], nv)
+        else:
+            u = np.sin(2 * X[..., :1]) * np.cos(X[..., 1:2] + (0.5 * X[..., 2:3] if nd == 3 else 0.0))
+        u = u * (1 + 0.01 * np.random.default_rng(3 + b).uniform(-1, 1, u.shape))
+        Ug.append(np.ascontiguousarray(u.transpose(1, 2, 0)))
     dt = torch.float32 if precision == "fp32" else torch.float64
     U = torch.from_numpy(M.pack(Ug)).to("cuda")
     R = torch.zeros_like(U)
@@ -64,7 +73,7 @@ def test_partitioned_residual_equals_whole_mesh(ctx, system, precision, p, schem
     M.sync()
     want = M.unpack(R.cpu().numpy())
 
-    owner = _owners(len(X), scheme, nparts)
+    owner = _owners(sum(len(b["verts"]) for b in mesh["blocks"]), scheme, nparts)
     plans = pt.split(mesh, owner, nparts)
     parts = [pt.PartitionMesh(ctx, pl, p, phys) for pl in plans]
     Us = [torch.from_numpy(pm.pack(pt.scatter_state(pl, Ug))).to("cuda") for pm, pl in zip(parts, plans)]
@@ -74,7 +83,8 @@ def test_partitioned_residual_equals_whole_mesh(ctx, system, precision, p, schem
     parts[0].sync()
     got = pt.gather_state(plans, [pm.unpack(r.cpu().numpy()) for pm, r in zip(parts, Rs)], want)
     assert sum(pm.xinfo["nrecv"] for pm in parts) > 0
-    assert np.array_equal(got[0], want[0]), float(np.abs(got[0] - want[0]).max())
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w), float(np.abs(g - w).max())
 
 
 def test_whole_mesh_calls_refuse_a_partition(ctx):

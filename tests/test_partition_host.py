@@ -127,13 +127,10 @@ def test_partition_errors(lib):
         with pytest.raises(sdrt.SdrtError):                    # unglued face on an owned element
             sdrt.sdrt_setup_partition(ctx, phys, blocks, pl["ghost"],
                                       (pl["mesh"]["faces"][1:], pl["mesh"]["shift"][1:]))
-        # partitions need the record path: hexahedra are refused
-        hmesh = meshes.box_mesh("hex", (2, 2, 2), [0.0] * 3, [1.0] * 3)
-        hpl = pt.split(hmesh, _owners(hmesh, "slabs", 2), 2)[0]
-        het = sdrt.sdrt_setup_element_type(ctx, "hex", 2)
+        # partitions cover the inviscid systems: Navier-Stokes is refused
+        nsphys = sdrt.make_physics("ns", 3, "rusanov", "fp32", gamma=1.4, mu=0.01)
         with pytest.raises(sdrt.SdrtError):
-            sdrt.sdrt_setup_partition(ctx, phys, [(het, b["verts"]) for b in hpl["mesh"]["blocks"]], hpl["ghost"],
-                                      (hpl["mesh"]["faces"], hpl["mesh"]["shift"]))
+            sdrt.sdrt_setup_partition(ctx, nsphys, blocks, pl["ghost"], faces)
     finally:
         sdrt.sdrt_destroy(ctx)
 
@@ -216,5 +213,25 @@ def test_partition_face_maps_match_the_whole_mesh(lib, scheme, nparts):
                         qe, qs = divmod(q - int(base[qb]), nfe)
                         assert (int(gid[qb][qe]) * nfe + qs) == int(wpart[G * nfe + s])
                         assert left[g] == wleft[G * nfe + s]
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("kinds,p,frec", [(["tet", "pri"], 2, 48), ("hex", 2, 48), ("tet", 2, 32)])
+def test_generic_partition_setup_in_host_context(lib, kinds, p, frec):
+    """Partitions on the generic path (any element type): face records of the
+    largest face's points x nvar, padded to 4 (prisms: 9-point quadrilateral and
+    6-point triangular faces at p = 2)."""
+    n = (2, 2, 2)
+    mesh = meshes.box_mesh(kinds if isinstance(kinds, str) else kinds, n, [0.0] * 3, [1.0] * 3)
+    owner = _owners(mesh, "random", 3)
+    plans = pt.split(mesh, owner, 3)
+    ctx = sdrt.Context(-1)
+    try:
+        phys = sdrt.make_physics("euler", 3, "rusanov", "fp64", gamma=1.4)
+        for pl in plans:
+            pm = pt.PartitionMesh(ctx, pl, p, phys)
+            assert pm.xinfo["face_record"] == frec
+            assert pm.xinfo["nsend"] == sum(len(a) for a in pl["send"].values())
     finally:
         ctx.close()
