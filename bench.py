@@ -331,6 +331,12 @@ REF_SCALE = {"euler": 5 / 24, "tgv": 3 / 48, "mixed": 0.02}
 REF_BUDGET_S = 150.0
 
 
+# Solution points per element (paper App. A, Table "nsolpts_nfpts").
+N_SOL = {"tri": lambda p: (p + 1) * (p + 2) // 2, "quad": lambda p: (p + 1) ** 2,
+         "tet": lambda p: (p + 1) * (p + 2) * (p + 3) // 6, "pri": lambda p: (p + 1) ** 2 * (p + 2) // 2,
+         "hex": lambda p: (p + 1) ** 3}
+
+
 def run_reference(args):
     """The oracle as the reference arm: one RK4 step of a bounded sample of the
     workload per bench step, warm-up steps untimed; to keep the run within a
@@ -349,13 +355,16 @@ def run_reference(args):
         if steps and time.perf_counter() - t_start > REF_BUDGET_S:
             break
     v = float(np.mean(steps))
+    full = Workload(args.workload, args.ncell, 0)
+    ndof_full = sum(N_SOL[b["shape"]](p) * full.nvar * len(b["verts"]) for b, p in zip(full.mesh["blocks"], full.degrees))
     label = WORKLOAD if (args.workload == "euler" and not args.ncell) else workload_label(args.workload, args.ncell)
     sample = (f"{small.label} ({small.nelem} elements), one RK4 step per bench step; {len(steps)} of "
               f"{args.steps} steps timed within the {REF_BUDGET_S:.0f} s budget; 1 core")
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": label, "sample": sample},
+            "warmup": args.warmup, "ms_per_step": ndof_full * 4 / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": label, "sample": sample,
+                       "ms_per_step": "one full-size RK4 step at the sampled DOF-update rate"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

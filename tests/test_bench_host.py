@@ -36,3 +36,19 @@ def test_workload_labels():
     assert bench.workload_label("euler") == "euler3d_tet_p3_82944_rk4"
     assert bench.workload_label("tgv") == "tgv_ns_tet_p4_663552_rk4"
     assert bench.workload_label("mixed").startswith("mixed_euler_") and bench.workload_label("mixed").endswith("_rk4")
+
+
+def test_solution_point_counts_match_the_paper_table():
+    """bench.N_SOL (used to project the reference arm's step time) against the
+    counts of App. A's table in tests/golden/point_counts.txt."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "point_counts.txt")
+    seen = 0
+    for line in open(path):
+        parts = line.split()
+        if not parts or parts[0].startswith("#") or parts[0] not in bench.N_SOL:
+            continue
+        shape, p, nsol = parts[0], int(parts[1]), int(parts[2])
+        assert bench.N_SOL[shape](p) == nsol, (shape, p)
+        seen += 1
+    assert seen >= 20
