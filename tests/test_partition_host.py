@@ -185,34 +185,44 @@ def test_face_record_exchange_between_two_processes():
     assert all(n > 0 for _, n in res)
 
 
-@pytest.mark.parametrize("scheme,nparts", [("slabs", 2), ("random", 3)])
-def test_partition_face_maps_match_the_whole_mesh(lib, scheme, nparts):
+@pytest.mark.parametrize("kinds,p,scheme,nparts", [("tet", 3, "slabs", 2), ("tet", 3, "random", 3),
+                                                   (["tet", "pri"], 2, "random", 3), ("hex", 2, "random", 2)])
+def test_partition_face_maps_match_the_whole_mesh(lib, kinds, p, scheme, nparts):
     """The face pairing of every partition (owned points glued to owned or ghost
     points), mapped back to global (element, point) ids, is the whole mesh's
-    face map bit for bit, L / R sides included."""
-    mesh = meshes.box_mesh("tet", (3, 3, 2), [0.0] * 3, [1.0] * 3)
+    face map bit for bit, L / R sides included (record and generic paths)."""
+    mesh = meshes.box_mesh(kinds, (3, 3, 2), [0.0] * 3, [1.0] * 3)
     owner = _owners(mesh, scheme, nparts)
     plans = pt.split(mesh, owner, nparts)
+    off = pt.global_offsets(mesh)
     ctx = sdrt.Context(-1)
     try:
         phys = sdrt.make_physics("euler", 3, "rusanov", "fp64", gamma=1.4)
-        W = sdrt.Mesh(ctx, mesh, 3, phys)
+        W = sdrt.Mesh(ctx, mesh, p, phys)
         wpart, wleft = W.face_map()
-        nfe = 40
+        nfe_of = [l["nfe"] for l in W.layouts]
+        wbase = np.concatenate([[0], np.cumsum([len(b["verts"]) * n for b, n in zip(mesh["blocks"], nfe_of)])])
+
+        def wcanon(G, s):                      # global element, local point -> whole-mesh canonical index
+            b = int(np.searchsorted(off, G, side="right") - 1)
+            return int(wbase[b] + (G - off[b]) * nfe_of[b] + s)
+
         for pl in plans:
-            pm = pt.PartitionMesh(ctx, pl, 3, phys)
+            pm = pt.PartitionMesh(ctx, pl, p, phys)
             part, left = pm.face_map()
-            gid = [ids for _, ids in pl["owned"]] + [ids for _, ids in pl["ghosts"]]
-            base = np.concatenate([[0], np.cumsum([len(i) * nfe for i in gid])])
-            for b in range(len(pl["owned"])):
-                for e, G in enumerate(gid[b]):
-                    for s in range(nfe):
-                        g = base[b] + e * nfe + s
+            blocks = pl["owned"] + pl["ghosts"]
+            nfe_l = [nfe_of[b] for b, _ in blocks]
+            base = np.concatenate([[0], np.cumsum([len(ids) * n for (_, ids), n in zip(blocks, nfe_l)])])
+            for lb in range(len(pl["owned"])):
+                ids = blocks[lb][1]
+                for e, G in enumerate(ids):
+                    for s in range(nfe_l[lb]):
+                        g = int(base[lb] + e * nfe_l[lb] + s)
                         q = int(part[g])
                         qb = int(np.searchsorted(base, q, side="right") - 1)
-                        qe, qs = divmod(q - int(base[qb]), nfe)
-                        assert (int(gid[qb][qe]) * nfe + qs) == int(wpart[G * nfe + s])
-                        assert left[g] == wleft[G * nfe + s]
+                        qe, qs = divmod(q - int(base[qb]), nfe_l[qb])
+                        assert wcanon(int(blocks[qb][1][qe]), qs) == int(wpart[wcanon(int(G), s)])
+                        assert left[g] == wleft[wcanon(int(G), s)]
     finally:
         ctx.close()
 
