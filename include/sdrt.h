@@ -185,10 +185,10 @@ int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out);
  * unglued; no residual is computed for them).  Ghost blocks come after the
  * owned ones; faces keep the L / R order of the whole mesh.  The state arrays
  * of the partition hold the owned blocks only.  Inviscid systems (advection,
- * Euler; SDRT_ERR_UNSUPPORTED for the viscous ones), any element types: the
- * record path (tetrahedra of degree 3 / 4) exchanges whole face records of
- * its record layout, the generic path the face points' states gathered from
- * its face-state array.  Whole-mesh calls (sdrt_residual,
+ * Euler) and, with a second exchange of the face points' gradients, the
+ * viscous ones; any element types: the record path (tetrahedra of degree 3 /
+ * 4) exchanges whole face records of its record layout, the generic path the
+ * face points' states gathered from its face-state array.  Whole-mesh calls (sdrt_residual,
  * sdrt_rk4_step, sdrt_jvp, sdrt_vjp, ...) return SDRT_ERR_STATE on a
  * partition.  Host inputs are copied. */
 int sdrt_setup_partition(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
@@ -204,21 +204,35 @@ int sdrt_set_exchange(sdrt_ctx* ctx, int mesh_id, int64_t nsend, const int32_t* 
                       const int32_t* recv);
 /* Counts of the exchange lists (-1 before sdrt_set_exchange) and the values per
  * face record (points per face x nvar, padded to a multiple of 4; on meshes whose
- * faces differ in point count, sized for the largest face, the rest zero). */
-int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record);
+ * faces differ in point count, sized for the largest face, the rest zero) and per
+ * gradient record of the viscous systems (points per face x ndim x nvar, padded
+ * the same way; 0 for the inviscid ones).  Null outputs are skipped. */
+int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record,
+                           int32_t* grad_record);
 
 /* Partitioned residual, first half: interpolation of the owned blocks to
  * their flux points (Eq. "interpolation_procedure"), then the send buffer
  * send_dev (device, nsend x face_record values, caller owned) packed in the
  * order of the send list.  Asynchronous on the context's stream. */
 int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* send_dev);
+/* Viscous systems (advection-diffusion, Navier-Stokes; generic path): the
+ * gradient needs the common value at the faces (Sec. 2.1, LDG), so the
+ * partitioned residual takes a second exchange.  After the face states have
+ * moved: recv_dev (nrecv x face_record) fills the ghost faces, the flux-point
+ * gradients of the owned elements follow (q~ = M16 C + M15 P M12 U, q = J^-T q~),
+ * and send_grad_dev (nsend x grad_record values, the face points' gradients,
+ * component d * nvar + v) is packed.  sdrt_residual_end then takes the received
+ * gradient records.  SDRT_ERR_STATE on an inviscid partition or before begin. */
+int sdrt_residual_gradients(sdrt_ctx* ctx, int mesh_id, const void* recv_dev, void* send_grad_dev);
 /* Second half, after the caller has moved every partition's send buffer
  * segments into the receive buffers (NCCL, device copies, ...): recv_dev
  * (device, nrecv x face_record values) fills the ghost faces, then the common
  * and internal fluxes and the divergence of the owned blocks give R_dev =
  * dU/dt (owned state layout).  Same values as sdrt_residual on the whole
  * mesh, element by element.  The generic path reads the state passed to
- * sdrt_residual_begin again here: it must stay valid and unchanged in between. */
+ * sdrt_residual_begin again here: it must stay valid and unchanged in between.
+ * Viscous systems: recv_dev holds the gradient records (nrecv x grad_record)
+ * of the exchange after sdrt_residual_gradients. */
 int sdrt_residual_end(sdrt_ctx* ctx, int mesh_id, const void* recv_dev, void* R_dev);
 int sdrt_get_block_layout(sdrt_ctx* ctx, int mesh_id, int block, sdrt_block_layout* out);
 

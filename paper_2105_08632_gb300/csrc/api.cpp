@@ -112,6 +112,11 @@ struct Mesh {
     DevBuf xsend_off, xrecv_off;      // record path: REC offsets of the sent / received face records
     DevBuf xsend_idx, xrecv_idx;      // generic path: UFE index of every record value (-1: padding)
     const void* part_u = nullptr;     // generic path: the state of the last sdrt_residual_begin
+    // Viscous partitions: gradient records (flux-point gradients of the face's
+    // points, QFE indices) exchanged between sdrt_residual_gradients and _end.
+    int xgrec = 0;
+    DevBuf xsend_gidx, xrecv_gidx;
+    bool part_grad = false;           // sdrt_residual_gradients ran since the last begin
     ~Mesh() {
         if (graph) cudaGraphExecDestroy(graph);
     }
@@ -636,6 +641,7 @@ int residual_begin_impl(sdrt_ctx* ctx, Mesh& m, const T* U, T* send) {
             ++ctx->launches;
         }
         m.part_u = U;
+        m.part_grad = false;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
         return SDRT_OK;
@@ -666,7 +672,18 @@ int residual_end_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* R) {
     if (!m.fast) {
         T* ufe = m.ufe.as<T>();
         if (!m.part_u) return fail(ctx, SDRT_ERR_STATE, "sdrt_residual_end before sdrt_residual_begin");
-        if (m.nrecv > 0) {
+        KVisc<T> Q{};
+        if (viscous(m)) {
+            // recv holds gradient records: into the ghost faces' flux-point gradients
+            // (the face states arrived with sdrt_residual_gradients).
+            if (!m.part_grad) return fail(ctx, SDRT_ERR_STATE, "viscous partition: sdrt_residual_gradients first");
+            if (m.nrecv > 0) {
+                launch_gather_values<T>(recv, m.qfe.as<T>(), m.xrecv_gidx.as<int>(), m.nrecv * m.xgrec, true,
+                                        ctx->nsm, ctx->stream);
+                ++ctx->launches;
+            }
+            Q = {m.qfe.as<T>(), nullptr, m.qfiu.as<T>(), nullptr};
+        } else if (m.nrecv > 0) {
             launch_gather_values<T>(recv, ufe, m.xrecv_idx.as<int>(), m.nrecv * m.xfrec, true, ctx->nsm, ctx->stream);
             ++ctx->launches;
         }
@@ -678,7 +695,7 @@ int residual_end_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* R) {
         const KSet<T> ks = kset<T>(m);
         const int s = prof_begin(ctx, KIND_RESIDUAL);
         const int r = launch_residual<T>(ks, m.phys.system, m.phys.riemann, m.nd, static_cast<const T*>(m.part_u),
-                                         nullptr, ufe, nullptr, m.Ftot, P, E, KVisc<T>{}, ctx->nsm, ctx->stream);
+                                         nullptr, ufe, nullptr, m.Ftot, P, E, Q, ctx->nsm, ctx->stream);
         prof_end(ctx, s);
         if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported");
         ++ctx->launches;
@@ -704,6 +721,35 @@ int residual_end_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* R) {
         prof_end(ctx, s);
         ++ctx->launches;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+// Viscous partitions, middle step: the received face states into the ghost
+// faces, the flux-point gradients of the owned elements, then the packed
+// gradient records to send.
+template <typename T>
+int residual_gradients_impl(sdrt_ctx* ctx, Mesh& m, const T* recv, T* send_grad) {
+    T* ufe = m.ufe.as<T>();
+    if (m.nrecv > 0) {
+        launch_gather_values<T>(recv, ufe, m.xrecv_idx.as<int>(), m.nrecv * m.xfrec, true, ctx->nsm, ctx->stream);
+        ++ctx->launches;
+    }
+    const KPhys<T> P = make_phys<T>(m.phys);
+    const KSet<T> ks = kset<T>(m);
+    const int s = prof_begin(ctx, KIND_GRAD);
+    const int r = launch_grad<T>(ks, m.phys.system, m.nd, static_cast<const T*>(m.part_u), nullptr, ufe, nullptr,
+                                 m.Ftot, P, m.qfe.as<T>(), nullptr, m.qfiu.as<T>(), nullptr, ctx->nsm, ctx->stream);
+    prof_end(ctx, s);
+    if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
+    ++ctx->launches;
+    if (m.nsend > 0) {
+        launch_gather_values<T>(m.qfe.as<T>(), send_grad, m.xsend_gidx.as<int>(), m.nsend * m.xgrec, false, ctx->nsm,
+                                ctx->stream);
+        ++ctx->launches;
+    }
+    m.part_grad = true;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return SDRT_OK;
@@ -1002,13 +1048,11 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
     }
     if (canon >= INT32_MAX || m->Ftot >= INT32_MAX) return fail(ctx, SDRT_ERR_UNSUPPORTED, "mesh too large for int32 maps");
     if (ghost) {
-        if (phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES)
-            return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions cover the inviscid systems");
         if (m->fast) {
             for (int b = 1; b < nblocks; ++b)
                 if (m->blocks[b]->frec != m->blocks[0]->frec)
                     return fail(ctx, SDRT_ERR_UNSUPPORTED, "partitions need one face-record size");
-        } else if ((int64_t)m->nvar * m->Ftot >= INT32_MAX) {
+        } else if ((int64_t)nd * m->nvar * m->Ftot >= INT32_MAX) {
             return fail(ctx, SDRT_ERR_UNSUPPORTED, "partition too large for int32 face-state indices");
         }
     }
@@ -1276,6 +1320,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
                 for (int k = 0; k < R.nfe; ++k) npf = std::max(npf, ++cnt[R.fe_face[k]]);
             }
             m->xfrec = round_up(npf * m->nvar, 4);
+            if (viscous(*m)) m->xgrec = round_up(npf * nd * m->nvar, 4);
         }
     }
     // Block tables of the generic kernels (tile widths are final here).
@@ -1405,13 +1450,42 @@ int sdrt_set_exchange(sdrt_ctx* ctx, int mesh_id, int64_t nsend, const int32_t* 
             if (nsend > 0) SDRT_CUDA(upload(m.xsend_idx, si));
             if (nrecv > 0) SDRT_CUDA(upload(m.xrecv_idx, ri));
         }
+        if (m.xgrec > 0) {
+            // Gradient records: value k * nd * nvar + dv is component dv = d * nvar + v
+            // of the face's k-th point in QFE ([nd][nvar][F_tot]).
+            const int ndv = m.nd * m.nvar;
+            auto gindices = [&](int64_t n, const int32_t* t, std::vector<int>& out) {
+                out.assign((size_t)n * m.xgrec, -1);
+                for (int64_t i = 0; i < n; ++i) {
+                    const int b = t[3 * i], e = t[3 * i + 1], f = t[3 * i + 2];
+                    const MBlock& q = b < nown ? *m.blocks[b] : *m.ghosts[b - nown];
+                    const RefElement& R = ctx->etypes[q.etype]->R;
+                    int k = 0;
+                    for (int sg = 0; sg < R.nfe; ++sg) {
+                        if (R.fe_face[sg] != f) continue;
+                        for (int dv = 0; dv < ndv; ++dv)
+                            out[(size_t)i * m.xgrec + k * ndv + dv] =
+                                (int)((int64_t)dv * m.Ftot + q.fe_base + (int64_t)sg * q.ld + e);
+                        ++k;
+                    }
+                }
+            };
+            std::vector<int> gs, gr;
+            gindices(nsend, send, gs);
+            gindices(nrecv, recv, gr);
+            if (!ctx->host_only) {
+                if (nsend > 0) SDRT_CUDA(upload(m.xsend_gidx, gs));
+                if (nrecv > 0) SDRT_CUDA(upload(m.xrecv_gidx, gr));
+            }
+        }
     }
     m.nsend = nsend;
     m.nrecv = nrecv;
     return SDRT_OK;
 }
 
-int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record) {
+int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* nrecv, int32_t* face_record,
+                           int32_t* grad_record) {
     int r = check_mesh(ctx, mesh_id);
     if (r) return r;
     const Mesh& m = *ctx->meshes[mesh_id];
@@ -1419,8 +1493,10 @@ int sdrt_get_exchange_info(sdrt_ctx* ctx, int mesh_id, int64_t* nsend, int64_t* 
     if (nsend) *nsend = m.nsend;
     if (nrecv) *nrecv = m.nrecv;
     if (face_record) *face_record = m.xfrec;
+    if (grad_record) *grad_record = m.xgrec;
     return SDRT_OK;
 }
+
 
 static int check_partition(sdrt_ctx* ctx, int mesh_id) {
     int r = check_compute(ctx, mesh_id);
@@ -1429,6 +1505,19 @@ static int check_partition(sdrt_ctx* ctx, int mesh_id) {
     if (!m.partition) return fail(ctx, SDRT_ERR_STATE, "not a partition mesh");
     if (m.nsend < 0) return fail(ctx, SDRT_ERR_STATE, "no exchange lists (sdrt_set_exchange)");
     return SDRT_OK;
+}
+
+int sdrt_residual_gradients(sdrt_ctx* ctx, int mesh_id, const void* recv, void* send_grad) {
+    int r = check_partition(ctx, mesh_id);
+    if (r) return r;
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (!viscous(m)) return fail(ctx, SDRT_ERR_STATE, "gradients are exchanged for the viscous systems only");
+    if (!m.part_u) return fail(ctx, SDRT_ERR_STATE, "sdrt_residual_gradients before sdrt_residual_begin");
+    if ((m.nrecv > 0 && !recv) || (m.nsend > 0 && !send_grad)) return fail(ctx, SDRT_ERR_ARG, "null array");
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if (m.phys.precision == SDRT_FP32)
+        return residual_gradients_impl<float>(ctx, m, static_cast<const float*>(recv), static_cast<float*>(send_grad));
+    return residual_gradients_impl<double>(ctx, m, static_cast<const double*>(recv), static_cast<double*>(send_grad));
 }
 
 int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U, void* send) {

@@ -153,46 +153,64 @@ class PartitionMesh(sdrt.Mesh):
         sdrt.sdrt_set_exchange(ctx.ptr, self.id, concat(plan["send"]), concat(plan["recv"]))
         self.xinfo = sdrt.sdrt_get_exchange_info(ctx.ptr, self.id)
         fr = self.xinfo["face_record"]
+        gr = self.xinfo["grad_record"]
+        self.viscous = gr > 0
         dt = torch.float32 if self.dtype_np == np.float32 else torch.float64
         dev = torch.device("cuda", ctx.device) if ctx.device >= 0 else torch.device("cpu")
         self.send_buf = torch.zeros(max(self.xinfo["nsend"], 1) * fr, dtype=dt, device=dev)
         self.recv_buf = torch.zeros(max(self.xinfo["nrecv"], 1) * fr, dtype=dt, device=dev)
+        if self.viscous:
+            self.send_gbuf = torch.zeros(max(self.xinfo["nsend"], 1) * gr, dtype=dt, device=dev)
+            self.recv_gbuf = torch.zeros(max(self.xinfo["nrecv"], 1) * gr, dtype=dt, device=dev)
 
     def residual_begin(self, U):
         self._check(U)
         sdrt.sdrt_residual_begin(self.ctx.ptr, self.id, U, self.send_buf)
 
+    def residual_gradients(self):
+        sdrt.sdrt_residual_gradients(self.ctx.ptr, self.id, self.recv_buf, self.send_gbuf)
+
     def residual_end(self, R):
         self._check(R)
-        sdrt.sdrt_residual_end(self.ctx.ptr, self.id, self.recv_buf, R)
+        sdrt.sdrt_residual_end(self.ctx.ptr, self.id, self.recv_gbuf if self.viscous else self.recv_buf, R)
 
-    def send_view(self, q):
-        s, n = self.send_seg[q]
-        fr = self.xinfo["face_record"]
-        return self.send_buf[s * fr:(s + n) * fr]
+    def _view(self, buf, seg, rec, q):
+        s, n = seg[q]
+        return buf[s * rec:(s + n) * rec]
 
-    def recv_view(self, q):
-        s, n = self.recv_seg[q]
-        fr = self.xinfo["face_record"]
-        return self.recv_buf[s * fr:(s + n) * fr]
+    def send_view(self, q, grad=False):
+        if grad:
+            return self._view(self.send_gbuf, self.send_seg, self.xinfo["grad_record"], q)
+        return self._view(self.send_buf, self.send_seg, self.xinfo["face_record"], q)
+
+    def recv_view(self, q, grad=False):
+        if grad:
+            return self._view(self.recv_gbuf, self.recv_seg, self.xinfo["grad_record"], q)
+        return self._view(self.recv_buf, self.recv_seg, self.xinfo["face_record"], q)
 
 
-def copy_local(parts):
+def copy_local(parts, grad=False):
     """Exchange between partitions held by one process (same stream): every
-    receive segment from its sender's send segment."""
+    receive segment from its sender's send segment (face states, or the
+    gradient records of the viscous systems)."""
     by_part = {pm.plan["part"]: pm for pm in parts}
     for pm in parts:
         p = pm.plan["part"]
         for q in pm.recv_seg:
-            pm.recv_view(q).copy_(by_part[q].send_view(p))
+            pm.recv_view(q, grad).copy_(by_part[q].send_view(p, grad))
 
 
 def residual_local(parts, Us, Rs):
     """Residual of partitions held by one process on one device: interpolate and
-    pack every partition, exchange by device copies, then fluxes and divergence."""
+    pack every partition, exchange by device copies (viscous systems: then the
+    flux-point gradients and a second exchange), then fluxes and divergence."""
     for pm, U in zip(parts, Us):
         pm.residual_begin(U)
     copy_local(parts)
+    if parts and parts[0].viscous:
+        for pm in parts:
+            pm.residual_gradients()
+        copy_local(parts, grad=True)
     for pm, R in zip(parts, Rs):
         pm.residual_end(R)
 
@@ -243,5 +261,9 @@ def rk4_step_distributed(part, U, dt, group=None):
         part.residual_begin(X[0])
         exchange({q: part.send_view(q) for q in part.send_seg}, {q: part.recv_view(q) for q in part.recv_seg},
                  group)
+        if part.viscous:
+            part.residual_gradients()
+            exchange({q: part.send_view(q, True) for q in part.send_seg},
+                     {q: part.recv_view(q, True) for q in part.recv_seg}, group)
         part.residual_end(R[0])
     _rk4(residual, [U], dt)

@@ -117,7 +117,9 @@ def lib():
         "sdrt_setup_partition": (I, [P, ctypes.POINTER(Physics), I, ctypes.POINTER(Block), ctypes.POINTER(ctypes.c_uint8),
                                      I64, ctypes.POINTER(Face), ctypes.POINTER(I)]),
         "sdrt_set_exchange": (I, [P, I, I64, ctypes.POINTER(ctypes.c_int32), I64, ctypes.POINTER(ctypes.c_int32)]),
-        "sdrt_get_exchange_info": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32)]),
+        "sdrt_get_exchange_info": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+        "sdrt_residual_gradients": (I, [P, I, P, P]),
         "sdrt_residual_begin": (I, [P, I, P, P]),
         "sdrt_residual_end": (I, [P, I, P, P]),
     }
@@ -235,9 +237,14 @@ def sdrt_set_exchange(ctx, mesh, send, recv):
 
 
 def sdrt_get_exchange_info(ctx, mesh):
-    ns, nr, fr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
-    _check(ctx, lib().sdrt_get_exchange_info(ctx, int(mesh), ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(fr)))
-    return {"nsend": ns.value, "nrecv": nr.value, "face_record": fr.value}
+    ns, nr, fr, gr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, lib().sdrt_get_exchange_info(ctx, int(mesh), ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(fr),
+                                             ctypes.byref(gr)))
+    return {"nsend": ns.value, "nrecv": nr.value, "face_record": fr.value, "grad_record": gr.value}
+
+
+def sdrt_residual_gradients(ctx, mesh, recv, send_grad):
+    _check(ctx, lib().sdrt_residual_gradients(ctx, int(mesh), _ptr(recv), _ptr(send_grad)))
 
 
 def sdrt_residual_begin(ctx, mesh, U, send):

@@ -47,20 +47,27 @@ def _owners(n, scheme, nparts):
     (["tet", "pri", "pri"], (3, 3, 3), "euler", "fp32", 2, "random", 3),
     ("tri", (6, 5), "advection", "fp64", 3, "random", 3),
     ("quad", (5, 4), "euler", "fp32", 3, "slabs", 2),
+    # viscous systems: face states, then flux-point gradients exchanged
+    ("tet", (3, 3, 3), "ns", "fp64", 2, "random", 3),
+    ("hex", (3, 3, 3), "ns", "fp32", 2, "random", 3),
+    ("tet", (3, 3, 3), "ns", "fp32", 3, "slabs", 2),
+    ("quad", (5, 4), "advdiff", "fp64", 3, "random", 3),
 ])
 def test_partitioned_residual_equals_whole_mesh(ctx, kinds, n, system, precision, p, scheme, nparts):
     from paper_2105_08632_gb300 import partition as pt
     from paper_2105_08632_gb300 import sdrt
     nd = len(n)
     mesh = meshes.box_mesh(kinds, n, [-1.0] * nd, [1.0] * nd)
-    kw = {"gamma": 1.4} if system == "euler" else {"a": (1.0, 0.5, 0.25)[:nd]}
-    riemann = "rusanov" if system == "euler" else "upwind"
+    kw = {"euler": {"gamma": 1.4}, "ns": {"gamma": 1.4, "mu": 0.02, "beta": 0.5, "eta": 0.1},
+          "advection": {"a": (1.0, 0.5, 0.25)[:nd]},
+          "advdiff": {"a": (1.0, 0.5, 0.25)[:nd], "mu": 0.05, "beta": 0.3, "eta": 0.2}}[system]
+    riemann = "rusanov" if system in ("euler", "ns") else "upwind"
     phys = sdrt.make_physics(system, nd, riemann, precision, **kw)
     M = sdrt.Mesh(ctx, mesh, p, phys)
     nv = M.nvar
     Ug = []
     for b, X in enumerate(M.sol_points()):
-        if system == "euler":
+        if system in ("euler", "ns"):
             u = gu.smooth_gas(X.reshape(-1, nd)).reshape(X.shape[0], X.shape[1], nv)
         else:
             u = np.sin(2 * X[..., :1]) * np.cos(X[..., 1:2] + (0.5 * X[..., 2:3] if nd == 3 else 0.0))

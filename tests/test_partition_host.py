@@ -127,10 +127,9 @@ def test_partition_errors(lib):
         with pytest.raises(sdrt.SdrtError):                    # unglued face on an owned element
             sdrt.sdrt_setup_partition(ctx, phys, blocks, pl["ghost"],
                                       (pl["mesh"]["faces"][1:], pl["mesh"]["shift"][1:]))
-        # partitions cover the inviscid systems: Navier-Stokes is refused
-        nsphys = sdrt.make_physics("ns", 3, "rusanov", "fp32", gamma=1.4, mu=0.01)
-        with pytest.raises(sdrt.SdrtError):
-            sdrt.sdrt_setup_partition(ctx, nsphys, blocks, pl["ghost"], faces)
+        # mismatched ghost flags (one per block)
+        with pytest.raises(ValueError):
+            sdrt.sdrt_setup_partition(ctx, phys, blocks, pl["ghost"][:-1].copy(), faces)
     finally:
         sdrt.sdrt_destroy(ctx)
 
@@ -243,5 +242,25 @@ def test_generic_partition_setup_in_host_context(lib, kinds, p, frec):
             pm = pt.PartitionMesh(ctx, pl, p, phys)
             assert pm.xinfo["face_record"] == frec
             assert pm.xinfo["nsend"] == sum(len(a) for a in pl["send"].values())
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("kinds,n,system,p,frec,grec", [("tet", (3, 3, 3), "ns", 2, 32, 92),
+                                                        ("hex", (2, 2, 3), "ns", 2, 48, 136),
+                                                        ("quad", (4, 4), "advdiff", 3, 4, 8)])
+def test_viscous_partition_records(lib, kinds, n, system, p, frec, grec):
+    """Viscous partitions exchange face states and then the face points'
+    gradients: records of (points per face) x nvar and x ndim x nvar values."""
+    nd = len(n)
+    mesh = meshes.box_mesh(kinds, n, [0.0] * nd, [1.0] * nd)
+    plans = pt.split(mesh, _owners(mesh, "random", 3), 3)
+    kw = {"gamma": 1.4, "mu": 0.02} if system == "ns" else {"a": (1.0, 0.5, 0.25)[:nd], "mu": 0.05}
+    phys = sdrt.make_physics(system, nd, "rusanov" if system == "ns" else "upwind", "fp64", **kw)
+    ctx = sdrt.Context(-1)
+    try:
+        for pl in plans:
+            pm = pt.PartitionMesh(ctx, pl, p, phys)
+            assert pm.viscous and pm.xinfo["face_record"] == frec and pm.xinfo["grad_record"] == grec
     finally:
         ctx.close()
