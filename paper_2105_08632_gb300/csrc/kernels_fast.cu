@@ -3,23 +3,31 @@
 // bulk asynchronous copies.
 //
 // One residual evaluation (paper Sec. 2.1, App. B) is two launches per block:
-//   k_interp_rec : [u_fe; u_fiu] = [M0; M12] U (Eqs. "interpolation_procedure"),
-//                  two threads per element, operator in shared memory; the
-//                  tile's records are assembled in shared memory and written
-//                  with one cp.async.bulk store each (REC: external points,
-//                  FIUR: internal points).
-//   k_flux_rec   : per tile, cp.async.bulk loads (completing on an mbarrier)
-//                  bring the tile's own records, the four partner face records
-//                  of every element, the metric rows and the partner
-//                  permutations into shared memory; G threads per element
-//                  compute the common fluxes (Sec. 2.1) and the normal
-//                  transformed internal fluxes (Eq. "normal_transformed_flux")
-//                  of their share of the points, exchange them with warp
-//                  shuffles and accumulate their share of the rows of
-//                  R~ = [M14 | M13] [F~_fe; F~_fi] (Eq. "residual_sdrt_matrices")
-//                  in registers; dU/dt = -R~ / det J goes through the fused RK4
-//                  stage epilogue.
+//   k_interp_pipe : [u_fe; u_fiu] = [M0; M12] U (Eq. "interpolation_procedure"),
+//                   FP32: one producer lane streams each tile of U with a 2D
+//                   tensor copy into a two-stage ring, consumer warps compute
+//                   all variables of their elements' rows and assemble the
+//                   records (REC: external points, FIUR: internal points) in
+//                   shared memory, written with bulk stores;
+//   k_interp_rec  : the same for FP64 (two threads per element, no TMA);
+//   k_flux_rec    : per tile, cp.async.bulk loads (completing on an mbarrier)
+//                   bring the tile's own records, the four partner face records
+//                   of every element, the metric rows and the partner
+//                   permutations into shared memory; G threads per element
+//                   compute the common fluxes (Sec. 2.1) and the normal
+//                   transformed internal fluxes (Eq. "normal_transformed_flux")
+//                   of their share of the points, exchange them with warp
+//                   shuffles and accumulate their share of the rows of
+//                   R~ = [M14 | M13] [F~_fe; F~_fi] (Eq. "residual_sdrt_matrices")
+//                   in registers (paired FP32 FMA); dU/dt = -R~ / det J goes
+//                   through the fused RK4 stage epilogue.  With FUSE (RK4 stages
+//                   1-3) the epilogue keeps the next stage's state in shared
+//                   memory, interpolates it and writes the next stage's records
+//                   into the other record buffer, so one RK4 step is one
+//                   interpolation and four flux launches.
 //   k_flux_rec_dual : the JVP (dual numbers), reading the records directly.
+//   k_face_records  : face records between REC and the packed exchange
+//                     buffers of a partitioned residual.
 #include <cstdint>
 #include <mutex>
 #include <type_traits>
