@@ -1,6 +1,9 @@
 // Generic (any element type) SDRT kernel templates for sm_103a, FMA path.
 //
-// One residual evaluation (paper Sec. 2.1 and App. B) is two launches per block:
+// One residual evaluation (paper Sec. 2.1 and App. B) is two launches, each a
+// persistent grid walking the tiles of every block of the mesh (block table
+// KTable, tile widths per block from the autotuner; viscous systems add k_grad
+// in between):
 //   k_interp_ext : U -> u_fe = M0 U at the external flux points (written to UFE,
 //                  the only data exchanged between elements);
 //   k_residual   : per tile of TE elements, entirely in shared memory:
