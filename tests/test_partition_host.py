@@ -264,3 +264,27 @@ def test_viscous_partition_records(lib, kinds, n, system, p, frec, grec):
             assert pm.viscous and pm.xinfo["face_record"] == frec and pm.xinfo["grad_record"] == grec
     finally:
         ctx.close()
+
+
+def test_single_partition_has_no_exchange(lib):
+    mesh = meshes.box_mesh("tet", (2, 2, 2), [0.0] * 3, [1.0] * 3)
+    plans = pt.split(mesh, np.zeros(48, int), 1)
+    pl = plans[0]
+    assert not pl["recv"] and not pl["send"] and not pl["ghosts"]
+    assert len(pl["mesh"]["faces"]) == len(mesh["faces"])
+    ctx = sdrt.Context(-1)
+    try:
+        pm = pt.PartitionMesh(ctx, pl, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
+        assert pm.xinfo["nsend"] == 0 and pm.xinfo["nrecv"] == 0
+        W = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
+        assert pm.state_len == W.state_len
+    finally:
+        ctx.close()
+
+
+def test_split_rejects_bad_owners():
+    mesh = meshes.box_mesh("tet", (2, 2, 2), [0.0] * 3, [1.0] * 3)
+    with pytest.raises(ValueError):
+        pt.split(mesh, np.zeros(47, int))
+    with pytest.raises(ValueError):
+        pt.split(mesh, np.full(48, 3), 2)
