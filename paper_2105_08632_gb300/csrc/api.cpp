@@ -1302,7 +1302,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
             m->ndof -= (int64_t)R.nsol * m->nvar * g.nelem;
             gsol += (int64_t)g.nelem * R.nsol * nd;
         }
-        m->state_len = m->blocks[nown]->u_off;
+        if (nown < nblocks) m->state_len = m->blocks[nown]->u_off;   // no ghost blocks: one partition
         m->sol_xyz.resize(m->sol_xyz.size() - (size_t)gsol);
         for (int b = nown; b < nblocks; ++b) m->ghosts.push_back(std::move(m->blocks[b]));
         m->blocks.resize(nown);
