@@ -288,3 +288,21 @@ def test_split_rejects_bad_owners():
         pt.split(mesh, np.zeros(47, int))
     with pytest.raises(ValueError):
         pt.split(mesh, np.full(48, 3), 2)
+
+
+@pytest.mark.parametrize("kinds,p", [("tet", 3), (["tet", "pri"], 2)])
+def test_partition_solution_points_are_the_owned_elements(lib, kinds, p):
+    mesh = meshes.box_mesh(kinds, (3, 2, 2), [0.0] * 3, [1.0] * 3)
+    plans = pt.split(mesh, _owners(mesh, "random", 3), 3)
+    ctx = sdrt.Context(-1)
+    try:
+        phys = sdrt.make_physics("euler", 3, "rusanov", "fp64", gamma=1.4)
+        W = sdrt.Mesh(ctx, mesh, p, phys)
+        wx = W.sol_points()
+        off = pt.global_offsets(mesh)
+        for pl in plans:
+            pm = pt.PartitionMesh(ctx, pl, p, phys)
+            for (b, ids), x in zip(pl["owned"], pm.sol_points()):
+                np.testing.assert_array_equal(x, wx[b][ids - off[b]])
+    finally:
+        ctx.close()
