@@ -26,7 +26,7 @@ upwind flux for linear advection, the Roe flux's Rankine-Hugoniot property on a
 single shock / exactness on a contact, and finite differences of the JVP
 (tests/test_oracle_residual.py, tests/test_oracle_physics.py).
 """
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 

@@ -1,7 +1,6 @@
 """Tile autotuner of the generic kernels: the chosen tiles are valid, the
 residual is bit-for-bit unchanged (tiles only partition the elements), and
 the RK4 graph re-captured afterwards gives the same steps."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

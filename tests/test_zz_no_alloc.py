@@ -7,7 +7,6 @@ face states exceed its fixed buffer.
 
 Kept in a file that pytest collects last; it is self-contained, so it passes
 alone in a fresh process and after the other tests."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
