@@ -27,6 +27,36 @@ def global_offsets(mesh):
     return np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
 
 
+def bisection_owners(mesh, nparts, weights=None):
+    """Owner array by recursive coordinate bisection of the element centroids:
+    each step cuts the element set across its longest centroid extent, at the
+    weighted quantile that gives the two sides parts in proportion to the
+    partitions they will hold (weights: work per element, e.g. nsol x nvar per
+    block; default 1).  Balanced to one element's weight for equal weights;
+    the cuts are planes, so the exchanged faces are those of ~nparts^(1/d)
+    planes across the box."""
+    cents = np.concatenate([np.asarray(b["verts"], float).mean(axis=1) for b in mesh["blocks"]])
+    n = len(cents)
+    w = np.ones(n) if weights is None else np.asarray(weights, float)
+    owner = np.zeros(n, np.int64)
+
+    def cut(idx, first, count):
+        if count == 1 or len(idx) == 0:
+            owner[idx] = first
+            return
+        left = count // 2
+        c = cents[idx]
+        axis = int(np.argmax(c.max(axis=0) - c.min(axis=0)))
+        order = idx[np.lexsort((idx, c[:, axis]))]           # ties broken by element id
+        cw = np.cumsum(w[order])
+        k = int(np.searchsorted(cw, cw[-1] * left / count, side="right"))
+        cut(order[:k], first, left)
+        cut(order[k:], first + left, count - left)
+
+    cut(np.arange(n), 0, int(nparts))
+    return owner
+
+
 def split(mesh, owner, nparts=None):
     """Plans of the partitions of `mesh` (dict of inputs.meshes) by owner[G]
     (partition of every global element).  Returns one dict per partition:

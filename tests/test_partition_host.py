@@ -306,3 +306,18 @@ def test_partition_solution_points_are_the_owned_elements(lib, kinds, p):
                 np.testing.assert_array_equal(x, wx[b][ids - off[b]])
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("kinds,n,nparts", [("tet", (4, 4, 4), 4), ("tet", (4, 4, 4), 3), (["tet", "pri"], (3, 3, 2), 5)])
+def test_bisection_owners_balance_and_cut(kinds, n, nparts):
+    """Recursive coordinate bisection: every partition within one element of the
+    mean size, and fewer exchanged faces than a random assignment (planar cuts)."""
+    mesh = meshes.box_mesh(kinds, n, [0.0] * 3, [1.0] * 3)
+    owner = pt.bisection_owners(mesh, nparts)
+    counts = np.bincount(owner, minlength=nparts)
+    assert counts.min() > 0 and counts.max() - counts.min() <= 1
+    def cut_faces(own):
+        return sum(len(k) for pl in pt.split(mesh, own, nparts) for k in pl["keys_recv"].values())
+    rnd = np.random.default_rng(1).integers(0, nparts, len(owner))
+    assert cut_faces(owner) < 0.5 * cut_faces(rnd)
+    assert np.array_equal(owner, pt.bisection_owners(mesh, nparts))     # deterministic
