@@ -321,3 +321,77 @@ def test_bisection_owners_balance_and_cut(kinds, n, nparts):
     rnd = np.random.default_rng(1).integers(0, nparts, len(owner))
     assert cut_faces(owner) < 0.5 * cut_faces(rnd)
     assert np.array_equal(owner, pt.bisection_owners(mesh, nparts))     # deterministic
+
+
+class _FakePart:
+    """A partition of a 1D periodic upwind operator (du_i/dt = u_{i-1} - u_i)
+    with the interface of PartitionMesh used by rk4_step_distributed: each rank
+    owns a contiguous half and receives its left neighbour's last value."""
+
+    def __init__(self, rank, world, n):
+        self.rank, self.world, self.n = rank, world, n
+        self.viscous = False
+        self.left, self.right = (rank - 1) % world, (rank + 1) % world
+        self.send_seg = {self.right: (0, 1)}
+        self.recv_seg = {self.left: (0, 1)}
+        self.send_buf = torch.zeros(1, dtype=torch.float64)
+        self.recv_buf = torch.zeros(1, dtype=torch.float64)
+        self.X = None
+
+    def residual_begin(self, X):
+        self.X = X
+        self.send_buf[0] = X[-1]
+
+    def residual_end(self, R):
+        up = torch.cat([self.recv_buf, self.X[:-1]])
+        R.copy_(up - self.X)
+
+    def send_view(self, q, grad=False):
+        return self.send_buf
+
+    def recv_view(self, q, grad=False):
+        return self.recv_buf
+
+
+def _rk4_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n = 8
+        x = np.arange(world * n)
+        u = np.sin(2 * np.pi * x / (world * n))
+        part = _FakePart(rank, world, n)
+        U = torch.from_numpy(u[rank * n:(rank + 1) * n].copy())
+        for _ in range(3):
+            pt.rk4_step_distributed(part, U, 0.1)
+        got = [None] * world
+        dist.all_gather_object(got, U.numpy().tolist())
+        if rank == 0:
+            out.put(np.concatenate(got))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_distributed_rk4_orchestration_with_gloo():
+    """rk4_step_distributed: one exchange per stage, stage combinations of
+    classical RK4 -- two gloo processes give the serial RK4 of the whole array."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rk4_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    u = np.sin(2 * np.pi * np.arange(16) / 16)
+    f = lambda v: np.roll(v, 1) - v
+    for _ in range(3):
+        k1 = f(u)
+        k2 = f(u + 0.05 * k1)
+        k3 = f(u + 0.05 * k2)
+        k4 = f(u + 0.1 * k3)
+        u = u + 0.1 / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    np.testing.assert_allclose(got, u, rtol=0, atol=1e-14)
