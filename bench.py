@@ -249,6 +249,12 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out):
+        """Median SM clock, maximum SM clock and the throttle reasons seen active,
+        from `nvidia-smi --query-gpu=<Q> --format=csv,noheader,nounits` lines."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():

@@ -52,3 +52,17 @@ def test_solution_point_counts_match_the_paper_table():
         assert bench.N_SOL[shape](p) == nsol, (shape, p)
         seen += 1
     assert seen >= 20
+
+
+def test_clock_sample_parsing():
+    out = "\n".join([
+        "0, 2070, 2070, 812.45, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 1390.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1965, 2070, 1398.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, 0.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage"])
+    c = bench.ClockSampler.parse(out)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    empty = bench.ClockSampler.parse("")
+    assert empty["sm_mhz"] is None and empty["samples"] == 0
