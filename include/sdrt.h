@@ -141,7 +141,10 @@ typedef struct {
  * (a cudaStream_t; NULL = legacy default stream).  The stream is borrowed:
  * it must outlive the context.  device = -1 creates a host-only context:
  * element types and meshes are built on the host (operators, metrics, face
- * maps can be queried) but every device computation returns SDRT_ERR_STATE. */
+ * maps can be queried) but every device computation returns SDRT_ERR_STATE.
+ * A device context also looks up the address of sdrt_residual_noalloc's
+ * static buffer, which takes its SDRT_NOALLOC_SCRATCH_BYTES of device memory
+ * (once per device and process) if no earlier context did. */
 int sdrt_create(sdrt_ctx** ctx, int device, void* cuda_stream);
 /* Destroy a context and every device buffer it owns. NULL is ignored. */
 void sdrt_destroy(sdrt_ctx* ctx);
@@ -253,15 +256,27 @@ int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev);
 /* Size in bytes of the fixed face-state buffer used by sdrt_residual_noalloc. */
 #define SDRT_NOALLOC_SCRATCH_BYTES (32u << 20)
 
-/* Same result as sdrt_residual, for callers that cannot allocate device
+/* The residual of sdrt_residual, for callers that cannot allocate device
  * memory (for example a solver running as a plugin inside a framework whose
  * memory pool owns the whole device, or a time-critical loop that cannot take
  * cudaMalloc's implicit device synchronisation).  The paper has no
  * counterpart: this is a property of the library, not of the method.
  *  - Allocates nothing: the face states exchanged between elements go to a
  *    fixed SDRT_NOALLOC_SCRATCH_BYTES buffer that is part of the library image
- *    on every GPU that loads the library (held until process exit).  The
- *    caller passes U_dev and R_dev as for sdrt_residual.
+ *    (a file-scope __device__ array).  Its device memory is taken when a
+ *    context is created on a device (sdrt_create looks up the buffer's
+ *    address, which loads the code module holding it) and held until process
+ *    exit; the address is kept per context, so a context created after a
+ *    device reset looks it up again.  The caller passes U_dev and R_dev as
+ *    for sdrt_residual.
+ *  - Kernel code: the CUDA runtime loads a kernel's code at its first launch
+ *    (lazy loading, the default); a caller that must see no change of free
+ *    device memory during its loop makes one call (or one sdrt_residual of
+ *    the same mesh) during set-up.
+ *  - Runs the generic kernels (interpolation to the external points, then the
+ *    residual kernel) for every mesh, so on meshes that sdrt_residual runs on
+ *    the record path (FP32 Euler / advection tetrahedra of degree 3 or 4) the
+ *    two results agree to FP32 rounding, not bit for bit.
  *  - Inviscid systems only (advection, Euler): the viscous systems need
  *    flux-point gradients that do not fit a fixed buffer of this size;
  *    they return SDRT_ERR_UNSUPPORTED.
@@ -271,8 +286,6 @@ int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev);
  *    message giving both sizes.  Example: Euler on 40,000 tetrahedra of degree
  *    3 in FP32 needs 40,000 x 40 points x 5 x 4 B = 32,000,000 B and fits
  *    (limit 33,554,432 B).
- *  - The first call on a device looks up the buffer's device address; make
- *    that first call before any stream capture.
  *  - All calls share the one buffer: calls whose kernels can overlap on the
  *    GPU (different streams, other contexts) race and give wrong results;
  *    serialise them.  Nothing needs clearing between calls: each call writes

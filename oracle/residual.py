@@ -64,10 +64,19 @@ def _to_phys_grad(Jinv, qt):
     return np.einsum("edi,dnve->inve", Jinv, qt)
 
 
-def _gradients(geom, phys, U, ufe, ufiu, fr=False):
-    """Physical gradients at external and unique internal points (viscous only)."""
+def solution_gradients(geom, phys, U, fr=False):
+    """Physical gradients q at the solution points, per block (ND, N_s, V, E):
+    q~ = M16 C + M15 u_fi with the common value C at the external points
+    (Sec. 2.1, Eq. "common_var_for_grad" and the transformed auxiliary
+    gradient), q = J^{-T} q~."""
+    ufe = [np.einsum("sr,rve->sve", g.ops.M0, u) for g, u in zip(geom.blocks, U)]
+    ufiu = [np.einsum("kr,rve->kve", g.ops.M12, u) for g, u in zip(geom.blocks, U)]
+    return _sol_gradients(geom, phys, U, ufe, ufiu, fr)
+
+
+def _sol_gradients(geom, phys, U, ufe, ufiu, fr=False):
     uL, uR = _gather_partner(geom, ufe)
-    qfe, qfiu = [], []
+    out = []
     for b, g in enumerate(geom.blocks):
         ops = g.ops
         C = phx.common_value(phys, uL[b], uR[b])            # (E, N_fe, V)
@@ -80,9 +89,16 @@ def _gradients(geom, phys, U, ufe, ufiu, fr=False):
             Du = np.einsum("dsr,rve->dsve", ops.Dsol, U[b]).reshape(nd * ns, *U[b].shape[1:])
             qt = Du + np.einsum("sr,rve->sve", ops.M16, C - ufe[b])
         qt = qt.reshape(nd, ns, *qt.shape[1:])
-        q = _to_phys_grad(g.Jinv, qt)                       # (ND, N_s, V, E)
-        qfe.append(np.einsum("fs,dsve->fdve", ops.M0, q))   # (N_fe, ND, V, E)
-        qfiu.append(np.einsum("ks,dsve->kdve", ops.M12, q))
+        out.append(_to_phys_grad(g.Jinv, qt))               # (ND, N_s, V, E)
+    return out
+
+
+def _gradients(geom, phys, U, ufe, ufiu, fr=False):
+    """Physical gradients at external and unique internal points (viscous only)."""
+    qfe, qfiu = [], []
+    for g, q in zip(geom.blocks, _sol_gradients(geom, phys, U, ufe, ufiu, fr)):
+        qfe.append(np.einsum("fs,dsve->fdve", g.ops.M0, q))   # (N_fe, ND, V, E)
+        qfiu.append(np.einsum("ks,dsve->kdve", g.ops.M12, q))
     return qfe, qfiu
 
 

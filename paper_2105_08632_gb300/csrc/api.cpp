@@ -132,6 +132,7 @@ struct sdrt_ctx {
     bool use_tc = false;          // tensor-core interpolation where instantiated (SDRT_OPT_TENSOR_CORES)
     bool use_tc_div = false;      // tensor-core divergence where instantiated (SDRT_OPT_TC_DIVERGENCE)
     bool fuse_rk = true;          // next-stage interpolation in the RK4 stage update (SDRT_OPT_FUSED_RK)
+    void* noalloc_scratch = nullptr;   // device address of sdrt_residual_noalloc's static buffer
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
     std::vector<std::unique_ptr<Mesh>> meshes;
@@ -816,6 +817,10 @@ int sdrt_create(sdrt_ctx** out, int device, void* stream) {
     ctx->nsm = prop.multiProcessorCount;
     if (ctx->flag.alloc(sizeof(int)) != cudaSuccess) return SDRT_ERR_CUDA;
     if (cudaMemset(ctx->flag.p, 0, sizeof(int)) != cudaSuccess) return SDRT_ERR_CUDA;
+    // The static buffer of sdrt_residual_noalloc: looking up its address loads
+    // the module that holds it (lazy module loading), so the device memory it
+    // takes is taken here and not in the allocation-free call.
+    if (sdrt::internal_noalloc_scratch_address(&ctx->noalloc_scratch) != cudaSuccess) return SDRT_ERR_CUDA;
     *out = ctx.release();
     return SDRT_OK;
 }
@@ -1821,6 +1826,8 @@ namespace sdrt {
 int internal_device(const sdrt_ctx* ctx) { return (!ctx || ctx->host_only) ? -1 : ctx->device; }
 
 int internal_fail(sdrt_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+
+void* internal_noalloc_scratch(const sdrt_ctx* ctx) { return ctx->noalloc_scratch; }
 
 int internal_residual_with_scratch(sdrt_ctx* ctx, int mesh_id, const void* U, void* R, void* scratch,
                                    size_t scratch_bytes) {

@@ -11,9 +11,6 @@
 // __device__ array), so the call itself allocates nothing.
 #include <cuda_runtime.h>
 
-#include <mutex>
-#include <string>
-
 #include "internal.hpp"
 #include "sdrt.h"
 
@@ -26,38 +23,25 @@ namespace {
 // points that exist), so nothing has to be cleared between calls.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SDRT_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
-
 }  // namespace
+
+namespace sdrt {
+
+int internal_noalloc_scratch_address(void** addr) {
+    *addr = nullptr;
+    // Host code cannot use the symbol itself: on the host it names a
+    // stand-in, not device memory.  The device address is looked up with the
+    // context's device current; the lookup loads this file's module.
+    return (int)cudaGetSymbolAddress(addr, g_noalloc_scratch);
+}
+
+}  // namespace sdrt
 
 extern "C" int sdrt_residual_noalloc(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R_dev) {
     if (!ctx) return SDRT_ERR_ARG;
-    const int dev = sdrt::internal_device(ctx);
-    if (dev < 0) return sdrt::internal_fail(ctx, SDRT_ERR_STATE, "host-only context: no device computation");
-    if (dev >= kMaxDevices) return sdrt::internal_fail(ctx, SDRT_ERR_UNSUPPORTED, "device index too large");
-    void* scratch = nullptr;
-    {
-        // First call on a device: look up the device address of the static
-        // buffer with that device current (host code cannot use the symbol
-        // itself: on the host it names a stand-in, not device memory).
-        std::lock_guard<std::mutex> lock(g_scratch_mutex);
-        if (!g_scratch_addr[dev]) {
-            int prev = 0;
-            if (cudaGetDevice(&prev) != cudaSuccess)
-                return sdrt::internal_fail(ctx, SDRT_ERR_CUDA, "cudaGetDevice failed");
-            if (prev != dev && cudaSetDevice(dev) != cudaSuccess)
-                return sdrt::internal_fail(ctx, SDRT_ERR_CUDA, "cudaSetDevice failed");
-            void* addr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-            if (prev != dev) cudaSetDevice(prev);
-            if (e != cudaSuccess || !addr)
-                return sdrt::internal_fail(ctx, SDRT_ERR_CUDA,
-                                           (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
-            g_scratch_addr[dev] = addr;
-        }
-        scratch = g_scratch_addr[dev];
-    }
+    if (sdrt::internal_device(ctx) < 0)
+        return sdrt::internal_fail(ctx, SDRT_ERR_STATE, "host-only context: no device computation");
+    void* scratch = sdrt::internal_noalloc_scratch(ctx);
+    if (!scratch) return sdrt::internal_fail(ctx, SDRT_ERR_STATE, "static scratch buffer not resolved");
     return sdrt::internal_residual_with_scratch(ctx, mesh_id, U_dev, R_dev, scratch, SDRT_NOALLOC_SCRATCH_BYTES);
 }

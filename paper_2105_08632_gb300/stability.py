@@ -2,7 +2,8 @@
 linear advection on uniform periodic meshes (paper Sec. 4, Eqs.
 "initial_condition_fourier_mode" to "semi_discrete_exponential", and the
 temporal linear stability of Sec. 4 with the RK polynomials of Eq.
-"rk_exponential").
+"rk_exponential"), and of pure diffusion (Sec. "Von-Neumann analysis with
+diffusion": BR1, beta = 0, eta = 0, tau = mu dt / h^2).
 
 For a Fourier mode U_c = U e^{i kappa . x_c} over the cells c of a uniform
 mesh (each cell split into the same pattern of elements), translation
@@ -12,13 +13,14 @@ reduced Jacobian
     G(kappa) = sum_c J_{c, c0} e^{-i kappa . (x_c - x_c0)},
 
 J_{c, c0} the block coupling the pattern DOFs of cell c0 to those of cell c.
-The blocks come from JVP probes of the library on a 3^d periodic box (every
-neighbour of the root cell is a distinct cell), one probe per pattern DOF of
-the root cell.  The eigenvalues of G on a kappa grid are computed in FP64 on
+The blocks come from JVP probes of the library on an n^d periodic box whose
+mesh the caller passes (n = 3 for advection, 5 for the two-layer diffusion
+stencil, so that every coupled cell is a distinct cell), one probe per
+pattern DOF of the root cell.  The eigenvalues of G on a kappa grid are computed in FP64 on
 the GPU (wavenumbers along the advection direction, as in the paper's
 tables, or the whole zone), and CFL_MAX is the largest tau = |a| dt / h with
 |P(tau lambda)| <= 1 for every eigenvalue, P the RK stability polynomial
-(h = cell size = 1, |a| = 1).
+(h = cell size = 1, |a| = 1 or mu = 1).
 """
 import numpy as np
 
@@ -41,23 +43,28 @@ def advection_direction(theta0, theta1=None):
     return (np.cos(theta0) * np.cos(theta1), np.sin(theta0), np.cos(theta0) * np.sin(theta1))
 
 
-def pattern_blocks(ctx, kind, degree, a, ncell=3):
+def pattern_blocks(ctx, mesh, ncell, degree, physics):
     """Blocks J_{c, c0} (ncell^d, N, N) and cell offsets x_c - x_c0 (ncell^d, d)
-    of linear advection along a on the periodic box of ncell^d unit cells,
-    N = elements per cell x solution points.  FP64 JVPs on the context's device."""
+    of a linear system on a periodic box of ncell^d unit cells, N = elements
+    per cell x solution points (one variable).  mesh: the box's mesh dict (one
+    element shape, elements numbered cell by cell, x fastest); physics: an
+    FP64 linear system (advection, or advection-diffusion with mu > 0, whose
+    BR1 stencil reaches two neighbour layers: ncell >= 5).  FP64 JVPs on the
+    context's device."""
     import torch
 
-    from inputs import meshes
-
     from . import sdrt
-    nd = len(a)
-    mesh = meshes.box_mesh(kind, (ncell,) * nd, [0.0] * nd, [float(ncell)] * nd)
+    nd = mesh["blocks"][0]["verts"].shape[2]
     if len(mesh["blocks"]) != 1:
         raise ValueError("one element shape per cell pattern")
-    M = sdrt.Mesh(ctx, mesh, degree, sdrt.make_physics("advection", nd, "upwind", "fp64", a=a))
+    M = sdrt.Mesh(ctx, mesh, degree, physics)
+    if M.nvar != 1:
+        raise ValueError("scalar linear systems only")
     lay = M.layouts[0]
     nsol, ld, nelem = lay["nsol"], lay["ld"], lay["nelem"]
     ncells = ncell ** nd
+    if nelem % ncells:
+        raise ValueError("element count is not a multiple of the cell count")
     k = nelem // ncells                                  # elements per cell (cells in order, x fastest)
     N = k * nsol
     c0 = sum((ncell // 2) * ncell ** i for i in range(nd))   # the central cell
@@ -93,9 +100,9 @@ def kappa_grid(nd, n):
 
 
 def kappa_line(a, n, kmax=2 * np.pi):
-    """kappa parallel to the advection direction, kappa h in [0, kmax] (n
-    samples): the wavenumbers of the paper's CFL_MAX tables (the values are
-    converged by kmax = 2 pi)."""
+    """kappa along the direction a, kappa h in [0, kmax] (n samples): the
+    wavenumbers of the paper's CFL_MAX tables (advection: along the advection
+    direction; diffusion: along a mesh axis; converged by kmax = 2 pi)."""
     import torch
     d = np.asarray(a, float) / np.linalg.norm(a)
     t = np.linspace(0.0, kmax, n)
@@ -126,7 +133,7 @@ def cfl_max(eigs, scheme="rk4", tol=1e-10, iters=60, round_tol=1e-8):
     amax = float(lam.abs().max())
     re = lam.real
     lam = torch.complex(torch.where((re > 0) & (re < round_tol * amax), torch.zeros_like(re), re), lam.imag)
-    hi = 4.0 / amax
+    hi = 8.0 / amax                     # above every RK stability limit used here
     lo = 0.0
 
     def stable(t):
@@ -143,18 +150,14 @@ def cfl_max(eigs, scheme="rk4", tol=1e-10, iters=60, round_tol=1e-8):
     return lo
 
 
-def cfl_table(ctx, kind, degrees, a, nkappa, schemes=("rk4",), wavenumbers="parallel"):
-    """CFL_MAX per degree and scheme, plus the largest real part of the
-    spatial eigenvalues (stability of the semi-discrete operator).
-    wavenumbers: "parallel" (kappa along a, nkappa samples of kappa h in
-    [0, 2 pi]) or "grid" (the whole zone kappa h in [-pi, pi)^d, nkappa per
-    direction; at least as restrictive)."""
-    nd = len(a)
+def cfl_table(ctx, mesh, ncell, degrees, physics, kappas, schemes=("rk4",)):
+    """CFL_MAX per degree and scheme on the wavenumbers `kappas` (kappa h per
+    axis, e.g. kappa_line or kappa_grid), plus the largest real part and the
+    largest modulus of the spatial eigenvalues."""
     out = {}
     for p in degrees:
-        blocks, off = pattern_blocks(ctx, kind, p, a)
-        kap = kappa_line(a, nkappa) if wavenumbers == "parallel" else kappa_grid(nd, nkappa)
-        eig = reduced_eigenvalues(blocks, off, kap)
+        blocks, off = pattern_blocks(ctx, mesh, ncell, p, physics)
+        eig = reduced_eigenvalues(blocks, off, kappas)
         out[p] = {s: cfl_max(eig, s) for s in schemes}
         out[p]["max_real"] = float(eig.real.max())
         out[p]["max_abs"] = float(eig.abs().max())

@@ -12,7 +12,9 @@ degree 2 is more restrictive (0.266 on quadrilaterals).
 The reduced Jacobians are assembled from the library's FP64 JVPs; eigenvalues
 in FP64 on the GPU.  The whole-zone 32^3 grid of the differentiation
 configuration is exercised for tetrahedra and prisms (stable operator,
-finite CFL)."""
+finite CFL).  The pure-diffusion table for quadrilateral SDRT (Sec.
+"Von-Neumann analysis with diffusion", Table "diff_quad_sdrt_cfl") pins the
+library's LDG path the same way."""
 import numpy as np
 import pytest
 
@@ -40,11 +42,21 @@ def ctx():
     c.close()
 
 
+def _advection(ctx, kind, p, a, kappas, schemes):
+    from inputs import meshes
+    from paper_2105_08632_gb300 import sdrt
+    from paper_2105_08632_gb300 import stability as st
+    nd = len(a)
+    mesh = meshes.box_mesh(kind, (3,) * nd, [0.0] * nd, [3.0] * nd)
+    phys = sdrt.make_physics("advection", nd, "upwind", "fp64", a=a)
+    return st.cfl_table(ctx, mesh, 3, [p], phys, kappas, schemes)[p]
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_quadrilateral_cfl_table(ctx, p):
     from paper_2105_08632_gb300 import stability as st
     a = st.advection_direction(np.pi / 6)
-    got = st.cfl_table(ctx, "quad", [p], a, nkappa=721, schemes=("rk3", "rk4", "rk54"))[p]
+    got = _advection(ctx, "quad", p, a, st.kappa_line(a, 721), ("rk3", "rk4", "rk54"))
     assert got["max_real"] < 1e-10                 # the semi-discrete operator is stable
     for s, want in zip(("rk3", "rk4", "rk54"), QUAD[p]):
         assert abs(got[s] - want) <= TOL * want, (p, s, got[s], want)
@@ -55,7 +67,7 @@ def test_quadrilateral_cfl_table(ctx, p):
 def test_hexahedron_cfl_table(ctx, p):
     from paper_2105_08632_gb300 import stability as st
     a = st.advection_direction(np.pi / 6, np.pi / 4)
-    got = st.cfl_table(ctx, "hex", [p], a, nkappa=361, schemes=("rk4",))[p]
+    got = _advection(ctx, "hex", p, a, st.kappa_line(a, 361), ("rk4",))
     assert got["max_real"] < 1e-10
     assert abs(got["rk4"] - HEX[p][1]) <= TOL * HEX[p][1], (p, got["rk4"], HEX[p][1])
 
@@ -64,7 +76,30 @@ def test_hexahedron_cfl_table(ctx, p):
 def test_simplex_whole_zone_grid(ctx, kind, p):
     from paper_2105_08632_gb300 import stability as st
     a = st.advection_direction(np.pi / 6, np.pi / 4)
-    got = st.cfl_table(ctx, kind, [p], a, nkappa=32, schemes=("rk4",), wavenumbers="grid")[p]
+    got = _advection(ctx, kind, p, a, st.kappa_grid(3, 32), ("rk4",))
     # stable up to the eigen-solver's rounding on a non-normal G
     assert got["max_real"] < 1e-8 * got["max_abs"], got
     assert 0.02 < got["rk4"] < 1.0, got
+
+
+# Table "diff_quad_sdrt_cfl" (pure diffusion, BR1 beta = 0, eta = 0): (RK3,
+# RK4, RK54) per degree, as printed; the printed values are the CFL_MAX
+# truncated to 4 decimals, with kappa along a mesh axis, kappa h in [0, 2 pi].
+DIFF_QUAD = {1: (0.2791, 0.3094, 0.5174), 2: (0.0348, 0.0386, 0.0646), 3: (0.0157, 0.0174, 0.0291),
+             4: (0.0055, 0.0061, 0.0103)}
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_quadrilateral_diffusion_cfl_table(ctx, p):
+    """The library's LDG path (common value, lifting, gradient interpolation,
+    common viscous flux) through its FP64 JVP reproduces the paper's diffusion
+    table exactly (4-decimal truncation), like the oracle does."""
+    from inputs import meshes
+    from paper_2105_08632_gb300 import sdrt
+    from paper_2105_08632_gb300 import stability as st
+    mesh = meshes.box_mesh("quad", (5, 5), [0.0, 0.0], [5.0, 5.0])
+    phys = sdrt.make_physics("advdiff", 2, "upwind", "fp64", a=(0.0, 0.0), mu=1.0, beta=0.0, eta=0.0)
+    got = st.cfl_table(ctx, mesh, 5, [p], phys, st.kappa_line((1.0, 0.0), 361), ("rk3", "rk4", "rk54"))[p]
+    assert got["max_real"] < 1e-10 * got["max_abs"]
+    for s, want in zip(("rk3", "rk4", "rk54"), DIFF_QUAD[p]):
+        assert np.floor(got[s] * 1e4 + 1e-9) == round(want * 1e4), (p, s, got[s], want)

@@ -58,6 +58,31 @@ def test_noalloc_matches_residual_on_two_calls(ctx, precision):
             assert linf < TOL32[0] and l2 < TOL32[1], (linf, l2)
 
 
+def test_first_noalloc_call_allocates_nothing():
+    """A fresh context: the static buffer is resolved when the context is
+    created, so free device memory is unchanged across the first
+    allocation-free call (kernel code loaded beforehand by sdrt_residual on
+    the same generic-path mesh)."""
+    from paper_2105_08632_gb300 import sdrt
+    c = sdrt.Context(0)
+    try:
+        M, geom, oph, _ = gu.build_pair(c, "hex", (3, 3, 2), 2, "euler", "rusanov", "fp32")
+        U = torch.from_numpy(M.pack(_states(geom, (31,))[0])).to("cuda")
+        ref, out = torch.zeros_like(U), torch.zeros_like(U)
+        M.residual(U, ref)
+        M.sync()
+        torch.cuda.synchronize()
+        free_before, _ = torch.cuda.mem_get_info()
+        sdrt.sdrt_residual_noalloc(c.ptr, M.id, U, out)
+        M.sync()
+        free_after, _ = torch.cuda.mem_get_info()
+        assert free_after == free_before, (free_before, free_after)
+        # generic path on both sides: the same kernels on the same data
+        assert torch.equal(out, ref)
+    finally:
+        c.close()
+
+
 def test_noalloc_rejects_meshes_beyond_its_buffer(ctx):
     from inputs import meshes
     from paper_2105_08632_gb300 import sdrt
