@@ -130,7 +130,13 @@ typedef struct {
     int64_t state_len;   /* length of a state array in elements (with padding) */
     int64_t ndof;        /* sum over blocks of nsol * nvar * nelem */
     int64_t nfe_total;   /* number of external flux points of the mesh */
+    int32_t path;        /* kernels of the residual and RK4 steps: SDRT_PATH_* */
+    int32_t reserved;
 } sdrt_mesh_info;
+/* Kernel paths of a mesh (sdrt_mesh_info.path). */
+#define SDRT_PATH_GENERIC 0      /* generic tile kernels, any element type / system */
+#define SDRT_PATH_RECORD 1       /* register-blocked record kernels (tetrahedra of degree 3 / 4) */
+#define SDRT_PATH_GENERATED 2    /* operator-specialised kernels (SDRT_OPT_GENERATED) */
 
 typedef struct {
     int32_t etype, nsol, nvar, nelem, ld, nfe;
@@ -364,6 +370,15 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     state inside the previous stage's update; 0 = one interpolation kernel
  *     per stage.  Same operations either way: the results are bit-identical. */
 #define SDRT_OPT_FUSED_RK 2
+/*   SDRT_OPT_GENERATED (default 1): 1 = residuals and RK4 steps of FP32 3D
+ *     Euler / Rusanov meshes whose element types all have operator-specialised
+ *     kernels (hexahedra of degree 1-3, prisms and tetrahedra of degree 1-4,
+ *     SDRT scheme; meshes of degree-3 / 4 tetrahedra only keep the record path)
+ *     run them: the structural non-zeros of [M0; M12] and [M14 | M13] compiled
+ *     in, one fused stage kernel per element type and RK stage writing the
+ *     next stage's face records, the element types as concurrent branches;
+ *     0 = the generic kernels.  Results agree to FP32 rounding. */
+#define SDRT_OPT_GENERATED 3
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 
 /* Per-launch device timing with CUDA events recorded on the context's stream

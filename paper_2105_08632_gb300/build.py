@@ -23,7 +23,35 @@ def _nvcc():
 
 
 def _sources():
-    return sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+
+
+def _host_cxx():
+    return shutil.which("g++") or shutil.which("c++")
+
+
+def generate(gen_dir):
+    """Build and run the operator generator (csrc/gen/opgen.cpp, linked with the
+    library's own operator code refel.cpp): one CUDA translation unit per
+    specialised element type plus the dispatch table, written to gen_dir."""
+    os.makedirs(gen_dir, exist_ok=True)
+    exe = os.path.join(BUILD, "opgen")
+    srcs = [os.path.join(CSRC, "gen", "opgen.cpp"), os.path.join(CSRC, "refel.cpp")]
+    cxx = _host_cxx()
+    if cxx:
+        cmd = [cxx, "-O1", "-std=c++17", "-I", CSRC, *srcs, "-o", exe]
+    else:
+        cmd = [_nvcc(), "-O1", "-std=c++17", "-x", "c++", "-I", CSRC, *srcs, "-o", exe]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError("operator generator build failed:\n" + r.stdout.decode(errors="replace"))
+    for f in os.listdir(gen_dir):
+        if f.startswith("gen_"):
+            os.remove(os.path.join(gen_dir, f))
+    r = subprocess.run([exe, gen_dir], stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError("operator generator failed:\n" + r.stdout.decode(errors="replace"))
+    return sorted(os.path.join(gen_dir, f) for f in os.listdir(gen_dir) if f.endswith((".cu", ".cpp")))
 
 
 def build(verbose=False, extra_flags=()):
@@ -31,10 +59,10 @@ def build(verbose=False, extra_flags=()):
     nvcc = _nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     procs, objs = [], []
-    for src in _sources():
+    for path in _sources() + generate(os.path.join(BUILD, "gen")):
+        src = os.path.basename(path)
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
-        path = os.path.join(CSRC, src)
         if src.endswith(".cu"):
             cmd = [nvcc, "-c", path, "-o", obj, "-std=c++17", "-O3", "-lineinfo", *ARCH,
                    "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v" if verbose else "-O3",

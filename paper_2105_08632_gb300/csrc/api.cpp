@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "kargs.hpp"
+#include "gen_api.hpp"
 #include "launch.hpp"
 #include "refel.hpp"
 #include "internal.hpp"
@@ -74,6 +75,11 @@ struct MBlock {
     int ers = 0, frs = 0, frec = 0, nmp = 0, pstride = 0;
     int64_t rec_base = 0, fiur_base = 0;
     DevBuf maos, pfr, perm, recoff;
+    // Operator-specialised path (gen_stage.cuh): launcher of the element
+    // type and the face-record index (canonical partner * nvar) of every
+    // external point, [nfe][ld].
+    GenLauncher gen = nullptr;
+    DevBuf pmap;
 };
 
 struct Mesh {
@@ -117,8 +123,21 @@ struct Mesh {
     int xgrec = 0;
     DevBuf xsend_gidx, xrecv_gidx;
     bool part_grad = false;           // sdrt_residual_gradients ran since the last begin
+    // Operator-specialised path: every block has a generated kernel (FP32
+    // 3D Euler / Rusanov, SDRT scheme, whole mesh); two face-record arrays
+    // (canonical points x nvar) alternate between RK stages; the blocks run as
+    // concurrent branches (one stream each, forked from and joined to the
+    // context's stream).
+    bool gen = false;
+    DevBuf fr[2];
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> brev;
+    cudaEvent_t fork_ev = nullptr;
     ~Mesh() {
         if (graph) cudaGraphExecDestroy(graph);
+        for (cudaStream_t st : br) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : brev) cudaEventDestroy(ev);
+        if (fork_ev) cudaEventDestroy(fork_ev);
     }
 };
 
@@ -132,6 +151,7 @@ struct sdrt_ctx {
     bool use_tc = false;          // tensor-core interpolation where instantiated (SDRT_OPT_TENSOR_CORES)
     bool use_tc_div = false;      // tensor-core divergence where instantiated (SDRT_OPT_TC_DIVERGENCE)
     bool fuse_rk = true;          // next-stage interpolation in the RK4 stage update (SDRT_OPT_FUSED_RK)
+    bool use_gen = true;          // operator-specialised kernels where generated (SDRT_OPT_GENERATED)
     void* noalloc_scratch = nullptr;   // device address of sdrt_residual_noalloc's static buffer
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
@@ -169,7 +189,8 @@ int new_slot(sdrt_ctx* ctx, int kind) {
 }
 
 // Start timing one launch: returns the slot (or -1 when profiling is off).
-int prof_begin(sdrt_ctx* ctx, int kind) {
+int prof_begin(sdrt_ctx* ctx, int kind, cudaStream_t st = nullptr) {
+    if (!st) st = ctx->stream;
     if (!ctx->prof) return -1;
     int s;
     if (ctx->capture_slots) {
@@ -188,15 +209,16 @@ int prof_begin(sdrt_ctx* ctx, int kind) {
     }
     // Inside a stream capture a plain record is only a dependency marker: an
     // external record becomes an event-record node that replays record.
-    if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s], ctx->stream, cudaEventRecordExternal);
-    else cudaEventRecord(ctx->ev[2 * s], ctx->stream);
+    if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s], st, cudaEventRecordExternal);
+    else cudaEventRecord(ctx->ev[2 * s], st);
     return s;
 }
 
-void prof_end(sdrt_ctx* ctx, int s) {
+void prof_end(sdrt_ctx* ctx, int s, cudaStream_t st = nullptr) {
     if (s < 0) return;
-    if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s + 1], ctx->stream, cudaEventRecordExternal);
-    else cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream);
+    if (!st) st = ctx->stream;
+    if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s + 1], st, cudaEventRecordExternal);
+    else cudaEventRecord(ctx->ev[2 * s + 1], st);
 }
 
 bool viscous(const Mesh& m) {
@@ -338,10 +360,60 @@ KPhys<T> make_phys(const sdrt_physics& p) {
     return P;
 }
 
+// Operator-specialised path: one launch of `kind` (0 interpolation into the
+// face records FRout, 1 fused stage) per block; with several blocks each
+// block is a branch of its own stream, forked from and joined to the
+// context's stream (concurrent kernels; inside a graph capture, parallel
+// graph branches).
+int gen_launch_blocks(sdrt_ctx* ctx, Mesh& m, int kind, const float* U, const float* FRin, float* FRout,
+                      const KEpi<float>& E) {
+    const KPhys<float> P = make_phys<float>(m.phys);
+    const int nb = (int)m.blocks.size();
+    const bool fork = nb > 1;
+    if (fork) SDRT_CUDA(cudaEventRecord(m.fork_ev, ctx->stream));
+    for (int b = 0; b < nb; ++b) {
+        MBlock& mb = *m.blocks[b];
+        cudaStream_t st = fork ? m.br[b] : ctx->stream;
+        if (fork) SDRT_CUDA(cudaStreamWaitEvent(st, m.fork_ev, 0));
+        GenArgs a{};
+        a.nelem = mb.nelem;
+        a.ld = mb.ld;
+        a.u_off = mb.u_off;
+        a.fr_base = mb.canon_base * m.nvar;
+        a.metric = mb.metric.as<float>();
+        a.pmap = mb.pmap.as<int>();
+        a.U = U;
+        a.FRin = FRin;
+        a.FRout = FRout;
+        a.P = P;
+        a.E = E;
+        const int s = prof_begin(ctx, kind == 0 ? KIND_INTERP : KIND_RESIDUAL, st);
+        const int r = mb.gen(kind, a, m.nvar, m.phys.system, m.phys.riemann, ctx->nsm, st);
+        prof_end(ctx, s, st);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "generated kernel not instantiated for this system");
+        ++ctx->launches;
+        if (fork) {
+            SDRT_CUDA(cudaEventRecord(m.brev[b], st));
+            SDRT_CUDA(cudaStreamWaitEvent(ctx->stream, m.brev[b], 0));
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
 // Residual-type evaluation of the whole mesh: interpolation of every block,
 // then the residual kernel of every block with epilogue E.
 template <typename T>
 int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>& E) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (!dU && m.gen && ctx->use_gen) {
+            // Operator-specialised kernels: face records of U, then the fused stage.
+            int r = gen_launch_blocks(ctx, m, 0, U, nullptr, m.fr[0].as<float>(), E);
+            if (r) return r;
+            return gen_launch_blocks(ctx, m, 1, U, m.fr[0].as<float>(), nullptr, E);
+        }
+    }
     const KPhys<T> P = make_phys<T>(m.phys);
     T* ufe = m.ufe.as<T>();
     T* dufe = m.dufe.as<T>();
@@ -524,9 +596,40 @@ int rk4_stages_fused(sdrt_ctx* ctx, Mesh& m, float* U, double dt) {
     return SDRT_OK;
 }
 
+// RK4 on the operator-specialised path: the face records of U, then four
+// fused stages; stages 1-3 write the face records of the next stage's state
+// (the two record arrays alternate), so each stage reads its partners' states
+// without a separate interpolation launch.
+int rk4_stages_gen(sdrt_ctx* ctx, Mesh& m, float* U, double dt) {
+    float* fr[2] = {m.fr[0].as<float>(), m.fr[1].as<float>()};
+    float* us = m.ustage.as<float>();
+    KEpi<float> E{};
+    E.flag = ctx->flag.as<int>();
+    E.u0 = U;
+    E.uacc = m.uacc.as<float>();
+    E.unext = us;
+    int r = gen_launch_blocks(ctx, m, 0, U, nullptr, fr[0], E);
+    if (r) return r;
+    const float c6 = (float)(dt / 6.0), c3 = (float)(dt / 3.0), c2 = (float)(dt / 2.0), c1 = (float)dt;
+    const int modes[4] = {EPI_RK_FIRST, EPI_RK_MID, EPI_RK_MID, EPI_RK_LAST};
+    const float cacc[4] = {c6, c3, c3, c6};
+    const float cnext[4] = {c2, c2, c1, 0.0f};
+    for (int stage = 0; stage < 4; ++stage) {
+        E.mode = modes[stage];
+        E.cacc = cacc[stage];
+        E.cnext = cnext[stage];
+        E.out = stage == 3 ? U : nullptr;
+        r = gen_launch_blocks(ctx, m, 1, stage == 0 ? U : us, fr[stage & 1], stage < 3 ? fr[(stage + 1) & 1] : nullptr,
+                              E);
+        if (r) return r;
+    }
+    return SDRT_OK;
+}
+
 template <typename T>
 int rk4_stages(sdrt_ctx* ctx, Mesh& m, T* U, double dt) {
     if constexpr (std::is_same<T, float>::value) {
+        if (m.gen && ctx->use_gen) return rk4_stages_gen(ctx, m, U, dt);
         if (ctx->fuse_rk && rk_fusable(ctx, m)) return rk4_stages_fused(ctx, m, U, dt);
     }
     KEpi<T> E{};
@@ -614,6 +717,11 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
     if (need_rk && m.fast && m.phys.precision == SDRT_FP32) {
         if (!m.rec2.p) SDRT_CUDA(m.rec2.alloc((size_t)m.rec_total * es));
         if (!m.fiur2.p) SDRT_CUDA(m.fiur2.alloc((size_t)m.fiur_total * es));
+    }
+    if (m.gen) {
+        const size_t nfr = (size_t)m.nfe_total * m.nvar * sizeof(float);
+        if (!m.fr[0].p) SDRT_CUDA(m.fr[0].alloc(nfr));
+        if (need_rk && !m.fr[1].p) SDRT_CUDA(m.fr[1].alloc(nfr));
     }
     if (need_rk && !m.ustage.p) {
         SDRT_CUDA(m.ustage.alloc((size_t)m.state_len * es));
@@ -1328,6 +1436,41 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
             if (viscous(*m)) m->xgrec = round_up(npf * nd * m->nvar, 4);
         }
     }
+    // Operator-specialised path: FP32 3D Euler / Rusanov on whole meshes of
+    // SDRT element types that have generated kernels and are not on the
+    // record path.
+    if (!ghost && !m->fast && f32 && phys->system == SDRT_EULER && nd == 3 && phys->riemann == SDRT_RUSANOV &&
+        (int64_t)m->nfe_total * m->nvar < INT32_MAX) {
+        bool all = true;
+        for (auto& bp : m->blocks) {
+            const EType& et = *ctx->etypes[bp->etype];
+            bp->gen = et.desc.scheme == SDRT_SCHEME_SDRT ? gen_launcher(et.R.shape, et.R.p) : nullptr;
+            all = all && bp->gen != nullptr;
+        }
+        m->gen = all;
+    }
+    if (m->gen && !ctx->host_only) {
+        for (auto& bp : m->blocks) {
+            MBlock& mb = *bp;
+            const int nfe = ctx->etypes[mb.etype]->R.nfe;
+            std::vector<int> pm((size_t)nfe * mb.ld, 0);
+            for (int e = 0; e < mb.nelem; ++e)
+                for (int sg = 0; sg < nfe; ++sg)
+                    pm[(size_t)sg * mb.ld + e] = m->partner[mb.canon_base + (int64_t)e * nfe + sg] * m->nvar;
+            SDRT_CUDA(upload(mb.pmap, pm));
+        }
+        if (m->blocks.size() > 1) {
+            SDRT_CUDA(cudaEventCreateWithFlags(&m->fork_ev, cudaEventDisableTiming));
+            for (size_t b = 0; b < m->blocks.size(); ++b) {
+                cudaStream_t st;
+                cudaEvent_t ev;
+                SDRT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+                m->br.push_back(st);
+                SDRT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                m->brev.push_back(ev);
+            }
+        }
+    }
     // Block tables of the generic kernels (tile widths are final here).
     if (int rt = refresh_tables(ctx, *m)) return rt;
     ctx->meshes.push_back(std::move(m));
@@ -1347,6 +1490,8 @@ int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out) {
     out->state_len = m.state_len;
     out->ndof = m.ndof;
     out->nfe_total = m.nfe_total;
+    out->path = m.fast ? SDRT_PATH_RECORD : (m.gen && ctx->use_gen) ? SDRT_PATH_GENERATED : SDRT_PATH_GENERIC;
+    out->reserved = 0;
     return SDRT_OK;
 }
 
@@ -1609,6 +1754,7 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     if (option == SDRT_OPT_TENSOR_CORES) ctx->use_tc = value != 0;
     else if (option == SDRT_OPT_TC_DIVERGENCE) ctx->use_tc_div = value != 0;
     else if (option == SDRT_OPT_FUSED_RK) ctx->fuse_rk = value != 0;
+    else if (option == SDRT_OPT_GENERATED) ctx->use_gen = value != 0;
     else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {
@@ -1701,6 +1847,9 @@ int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
     if (!U || reps < 1) return fail(ctx, SDRT_ERR_ARG, "null state or reps < 1");
     Mesh& m = *ctx->meshes[mesh_id];
     if (m.fast) return SDRT_OK;                 // the record-path kernels have fixed tiles
+    // The operator-specialised kernels have fixed tiles too: on their meshes
+    // the generic kernels' tiles are tuned with those kernels switched off
+    // (they run with SDRT_OPT_GENERATED = 0).
     if ((r = ensure_workspace(ctx, m, false, false))) return r;
     const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
     DevBuf R;
@@ -1710,6 +1859,8 @@ int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
     SDRT_CUDA(cudaEventCreate(&b));
     const bool prof = ctx->prof;
     ctx->prof = false;
+    const bool use_gen = ctx->use_gen;
+    ctx->use_gen = false;
     // Time `reps` residual evaluations of the whole mesh (ms per evaluation).
     auto timed = [&](float* ms) -> int {
         int rr;
@@ -1754,6 +1905,7 @@ int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
         if (rc) break;
     }
     ctx->prof = prof;
+    ctx->use_gen = use_gen;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (m.graph) {

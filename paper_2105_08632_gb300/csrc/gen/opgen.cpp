@@ -1,0 +1,289 @@
+// Build-time generator of the operator-specialised SDRT kernels.
+//
+// For every (element shape, degree) listed below it builds the reference
+// element with the library's own FP64 operator code (refel.cpp: point sets of
+// paper App. A, operators M0, M12, M13, M14 of App. B) and writes one CUDA
+// translation unit that instantiates the fused stage kernel of gen_stage.cuh
+// with those operators baked in as FP32 immediates:
+//   * interpolation rows [M0; M12] and divergence columns [M14 | M13] keep only
+//     their structural non-zeros (entries below 1e-11 of the matrix's largest
+//     are the rounding of exact zeros: on tensor-product elements each flux
+//     point depends on one line of solution points; the entries are dropped
+//     only when the gap to the smallest kept entry exceeds 1e6, otherwise
+//     only exact zeros are; both sizes are printed in each file);
+//   * the flux points are split into groups (external points face by face,
+//     then the unique internal points) whose point states and DOF fluxes fit a
+//     shared-memory budget; the kernel interpolates, evaluates the fluxes and
+//     accumulates the divergence group by group.
+// Also writes gen_table.cpp, which maps (shape, degree) to the launchers.
+//
+// Usage: opgen <output directory>
+#include <algorithm>
+#include <cctype>
+#include <cmath>
+#include <cstdio>
+#include <fstream>
+#include <sstream>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "refel.hpp"
+
+using namespace sdrt;
+
+namespace {
+
+struct Key {
+    int shape, p;
+    const char* name;
+};
+
+// The specialised element types: the shapes and degrees of the batched
+// mixed-element workloads (hexahedra and prisms up to degree 3 / 4,
+// tetrahedra up to 4).  Degree-4 hexahedra (125 solution points) stay on the
+// generic kernels: their register and shared-memory footprint does not fit
+// this scheme.
+const Key kKeys[] = {{HEX, 1, "hex1"}, {HEX, 2, "hex2"}, {HEX, 3, "hex3"}, {PRI, 1, "pri1"}, {PRI, 2, "pri2"},
+                     {PRI, 3, "pri3"}, {PRI, 4, "pri4"}, {TET, 1, "tet1"}, {TET, 2, "tet2"}, {TET, 3, "tet3"},
+                     {TET, 4, "tet4"}};
+
+// Row units (point states + DOF fluxes) of one group.
+constexpr int kBudget = 80;
+constexpr double kZeroRel = 1e-11;
+
+std::string flt(double x) {
+    char b[64];
+    std::snprintf(b, sizeof b, "%.9ef", (double)(float)x);
+    return b;
+}
+
+struct Sparse {
+    // entries (row, col, value) of a dense row-major matrix above the threshold
+    std::vector<std::vector<std::pair<int, double>>> rows;
+    double dropped_max = 0, kept_min = 1e300;
+};
+
+Sparse sparsify_at(const std::vector<double>& A, int nr, int nc, double thr) {
+    double mx = 0;
+    for (double a : A) mx = std::max(mx, std::fabs(a));
+    Sparse S;
+    S.rows.resize(nr);
+    for (int r = 0; r < nr; ++r)
+        for (int c = 0; c < nc; ++c) {
+            const double a = A[(size_t)r * nc + c];
+            const double rel = std::fabs(a) / mx;
+            if (rel > thr) {
+                S.rows[r].push_back({c, a});
+                S.kept_min = std::min(S.kept_min, rel);
+            } else {
+                S.dropped_max = std::max(S.dropped_max, rel);
+            }
+        }
+    return S;
+}
+
+// Structural zeros dropped when they are separated from the kept entries by
+// more than six orders of magnitude; otherwise (the simplices' dense
+// operators, whose small entries are genuine) only exact zeros are dropped.
+Sparse sparsify(const std::vector<double>& A, int nr, int nc) {
+    Sparse S = sparsify_at(A, nr, nc, kZeroRel);
+    if (S.dropped_max > 0 && S.kept_min / S.dropped_max < 1e6) S = sparsify_at(A, nr, nc, 0.0);
+    return S;
+}
+
+struct Point {
+    bool ext;
+    int id;                    // external point sigma or unique internal point k
+    int face;                  // external: its face
+    std::vector<int> dofs;     // internal: DOF indices nu
+    std::vector<int> axes;     // internal: their reference axes
+};
+
+void generate(const Key& key, const std::string& dir, std::ostringstream& table) {
+    const RefElement R = build_ref_element(key.shape, key.p);
+    const int NS = R.nsol, NFE = R.nfe, NFIU = R.nfiu, NFI = R.nfi;
+    // [M0; M12] (NFE + NFIU) x NS and [M14 | M13] NS x (NFE + NFI).
+    std::vector<double> Ai((size_t)(NFE + NFIU) * NS), Ad((size_t)NS * (NFE + NFI));
+    for (int r = 0; r < NFE; ++r)
+        for (int c = 0; c < NS; ++c) Ai[(size_t)r * NS + c] = R.M0[(size_t)r * NS + c];
+    for (int r = 0; r < NFIU; ++r)
+        for (int c = 0; c < NS; ++c) Ai[(size_t)(NFE + r) * NS + c] = R.M12[(size_t)r * NS + c];
+    for (int r = 0; r < NS; ++r) {
+        for (int c = 0; c < NFE; ++c) Ad[(size_t)r * (NFE + NFI) + c] = R.M14[(size_t)r * NFE + c];
+        for (int c = 0; c < NFI; ++c) Ad[(size_t)r * (NFE + NFI) + NFE + c] = R.M13[(size_t)r * NFI + c];
+    }
+    const Sparse SI = sparsify(Ai, NFE + NFIU, NS);
+    // columns of the divergence: transpose of the sparse rows
+    const Sparse SDr = sparsify(Ad, NS, NFE + NFI);
+    std::vector<std::vector<std::pair<int, double>>> dcol(NFE + NFI);
+    for (int r = 0; r < NS; ++r)
+        for (auto& e : SDr.rows[r]) dcol[e.first].push_back({r, e.second});
+
+    // Points and groups.
+    std::vector<Point> pts;
+    for (int s = 0; s < NFE; ++s) pts.push_back({true, s, R.fe_face[s], {}, {}});
+    for (int k = 0; k < NFIU; ++k) {
+        Point P{false, k, -1, {}, {}};
+        for (int nu = 0; nu < NFI; ++nu)
+            if (R.fi_point[nu] == k) {
+                P.dofs.push_back(nu);
+                P.axes.push_back(R.fi_axis[nu]);
+            }
+        if (P.dofs.empty() || P.dofs.size() > 3) throw std::runtime_error("internal point without 1..3 DOFs");
+        pts.push_back(P);
+    }
+    std::vector<std::vector<int>> groups(1);
+    int units = 0;
+    for (int i = 0; i < (int)pts.size(); ++i) {
+        const int u = 1 + (pts[i].ext ? 1 : (int)pts[i].dofs.size());
+        if (units + u > kBudget && !groups.back().empty()) {
+            groups.emplace_back();
+            units = 0;
+        }
+        groups.back().push_back(i);
+        units += u;
+    }
+    int GR = 0;                    // largest group: point rows + DOF rows
+    for (auto& g : groups) {
+        int nf = 0;
+        for (int i : g) nf += pts[i].ext ? 1 : (int)pts[i].dofs.size();
+        GR = std::max(GR, (int)g.size() + nf);
+    }
+    long nnzI = 0, nnzD = 0;
+    for (auto& r : SI.rows) nnzI += (long)r.size();
+    for (auto& c : dcol) nnzD += (long)c.size();
+
+    std::ostringstream o;
+    const std::string N = key.name;
+    std::string T = N;
+    T[0] = (char)std::toupper(T[0]);
+    o << "// Generated by csrc/gen/opgen.cpp from the library's FP64 operators: do not edit.\n"
+      << "// " << N << ": nsol " << NS << ", nfe " << NFE << ", nfiu " << NFIU << ", nfi " << NFI << "; non-zeros "
+      << "[M0; M12] " << nnzI << " of " << (long)(NFE + NFIU) * NS << ", [M14 | M13] " << nnzD << " of "
+      << (long)NS * (NFE + NFI) << "\n"
+      << "// relative size of the largest dropped / smallest kept entry: interpolation " << SI.dropped_max << " / "
+      << SI.kept_min << ", divergence " << SDr.dropped_max << " / " << SDr.kept_min << "\n"
+      << "#include \"gen_stage.cuh\"\n\nnamespace sdrt {\nnamespace gen {\nnamespace {\n\n";
+    // point descriptors: (ext sigma | -(k+1), face, first FS row, ndof | axes << 2)
+    o << "__constant__ int4 c_desc[" << pts.size() << "] = {";
+    std::vector<int> goff;
+    int off = 0;
+    for (auto& g : groups) {
+        goff.push_back(off);
+        int fs = 0;
+        for (int i : g) {
+            const Point& P = pts[i];
+            if (P.ext) {
+                o << "{" << P.id << "," << P.face << "," << fs << ",1},";
+                fs += 1;
+            } else {
+                int w = (int)P.dofs.size();
+                for (size_t q = 0; q < P.axes.size(); ++q) w |= P.axes[q] << (2 + 2 * q);
+                o << "{" << -(P.id + 1) << ",-1," << fs << "," << w << "},";
+                fs += (int)P.dofs.size();
+            }
+            ++off;
+        }
+    }
+    o << "};\n\n";
+    o << "struct " << T << " {\n"
+      << "    static constexpr int NS = " << NS << ", NFE = " << NFE << ", NFIU = " << NFIU << ", NFI = " << NFI
+      << ", NF = " << R.nfaces << ", NG = " << groups.size() << ", GR = " << GR << ";\n"
+      << "    template <int G> struct Grp;\n"
+      << "    static __device__ __forceinline__ int4 desc(int i) { return c_desc[i]; }\n";
+    // ext: external-point rows from registers
+    o << "    static __device__ __forceinline__ void ext(const float (&w)[NS], float* __restrict__ o, const int ldo) {\n";
+    for (int r = 0; r < NFE; ++r) {
+        auto& row = SI.rows[r];
+        std::string e = "0.0f";
+        for (size_t j = 0; j < row.size(); ++j) {
+            const std::string term = "w[" + std::to_string(row[j].first) + "]";
+            e = j == 0 ? flt(row[j].second) + " * " + term
+                       : "fmaf(" + flt(row[j].second) + ", " + term + ", " + e + ")";
+        }
+        o << "        o[" << r << " * ldo] = " << e << ";\n";
+    }
+    o << "    }\n};\n\n";
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        auto& g = groups[gi];
+        std::vector<int> used(NS, 0);
+        for (int i : g) {
+            const int row = pts[i].ext ? pts[i].id : NFE + pts[i].id;
+            for (auto& e : SI.rows[row]) used[e.first] = 1;
+        }
+        int nf = 0;
+        for (int i : g) nf += pts[i].ext ? 1 : (int)pts[i].dofs.size();
+        o << "template <> struct " << T << "::Grp<" << gi << "> {\n"
+          << "    static constexpr int NP = " << g.size() << ", NDOF = " << nf << ", OFF = " << goff[gi] << ";\n"
+          << "    static __device__ __forceinline__ void interp(const float* __restrict__ u, const int ldu, "
+             "float* __restrict__ x, const int ldx) {\n";
+        for (int c = 0; c < NS; ++c)
+            if (used[c]) o << "        const float u" << c << " = u[" << c << " * ldu];\n";
+        for (size_t j = 0; j < g.size(); ++j) {
+            const Point& P = pts[g[j]];
+            const int row = P.ext ? P.id : NFE + P.id;
+            auto& rr = SI.rows[row];
+            std::string e = "0.0f";
+            for (size_t q = 0; q < rr.size(); ++q) {
+                const std::string term = "u" + std::to_string(rr[q].first);
+                e = q == 0 ? flt(rr[q].second) + " * " + term
+                           : "fmaf(" + flt(rr[q].second) + ", " + term + ", " + e + ")";
+            }
+            o << "        x[" << j << " * ldx] = " << e << ";\n";
+        }
+        o << "    }\n"
+          << "    static __device__ __forceinline__ void div(const float* __restrict__ f, const int ldf, "
+             "float (&r)[" << NS << "]) {\n";
+        int fs = 0;
+        for (int i : g) {
+            const Point& P = pts[i];
+            std::vector<int> cols;
+            if (P.ext) cols.push_back(P.id);
+            else
+                for (int nu : P.dofs) cols.push_back(NFE + nu);
+            for (int col : cols) {
+                o << "        { const float t = f[" << fs << " * ldf];";
+                for (auto& e : dcol[col]) o << " r[" << e.first << "] = fmaf(" << flt(e.second) << ", t, r[" << e.first << "]);";
+                o << " }\n";
+                ++fs;
+            }
+        }
+        o << "    }\n};\n\n";
+    }
+    o << "}  // namespace\n}  // namespace gen\n\n"
+      << "int launch_gen_" << N << "(int kind, const GenArgs& a, int V, int sys, int rie, int nsm, cudaStream_t st) {\n"
+      << "    return gen::launch_gen<gen::" << T << ">(kind, a, V, sys, rie, nsm, st);\n}\n\n"
+      << "}  // namespace sdrt\n";
+    std::ofstream f(dir + "/gen_" + N + ".cu");
+    f << o.str();
+    if (!f) throw std::runtime_error("cannot write " + dir + "/gen_" + N + ".cu");
+    table << "    if (shape == " << key.shape << " && p == " << key.p << ") return launch_gen_" << N << ";\n";
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+    if (argc != 2) {
+        std::fprintf(stderr, "usage: opgen <output directory>\n");
+        return 2;
+    }
+    const std::string dir = argv[1];
+    try {
+        std::ostringstream table, decl;
+        for (const Key& k : kKeys) {
+            generate(k, dir, table);
+            decl << "int launch_gen_" << k.name
+                 << "(int kind, const GenArgs& a, int V, int sys, int rie, int nsm, cudaStream_t st);\n";
+        }
+        std::ofstream f(dir + "/gen_table.cpp");
+        f << "// Generated by csrc/gen/opgen.cpp: do not edit.\n#include \"gen_api.hpp\"\n\nnamespace sdrt {\n\n"
+          << decl.str() << "\nGenLauncher gen_launcher(int shape, int p) {\n"
+          << table.str() << "    return nullptr;\n}\n\n}  // namespace sdrt\n";
+        if (!f) throw std::runtime_error("cannot write gen_table.cpp");
+    } catch (const std::exception& e) {
+        std::fprintf(stderr, "opgen: %s\n", e.what());
+        return 1;
+    }
+    return 0;
+}

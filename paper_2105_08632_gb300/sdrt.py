@@ -66,7 +66,7 @@ class Face(ctypes.Structure):
 class MeshInfo(ctypes.Structure):
     _fields_ = [("nvar", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("ndim", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("state_len", ctypes.c_int64), ("ndof", ctypes.c_int64),
-                ("nfe_total", ctypes.c_int64)]
+                ("nfe_total", ctypes.c_int64), ("path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BlockLayout(ctypes.Structure):
@@ -318,6 +318,8 @@ def sdrt_launch_count(ctx):
 SDRT_OPT_TENSOR_CORES = 0
 SDRT_OPT_TC_DIVERGENCE = 1
 SDRT_OPT_FUSED_RK = 2
+SDRT_OPT_GENERATED = 3
+PATHS = {0: "generic", 1: "record", 2: "generated"}
 
 
 def sdrt_autotune(ctx, mesh, U, reps=3):
