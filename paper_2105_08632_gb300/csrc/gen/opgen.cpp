@@ -49,7 +49,7 @@ const Key kKeys[] = {{HEX, 1, "hex1"}, {HEX, 2, "hex2"}, {HEX, 3, "hex3"}, {PRI,
                      {TET, 4, "tet4"}};
 
 // Row units (point states + DOF fluxes) of one group.
-constexpr int kBudget = 80;
+constexpr int kBudget = 64;
 constexpr double kZeroRel = 1e-11;
 
 std::string flt(double x) {

@@ -17,10 +17,12 @@
 // thread (lane, v) owns variable v of element e0 + lane for the operator
 // applications (one column of the paper's state matrix, App. B), and the
 // threads share the tile's points for the flux evaluation:
-//   1. the tile's state goes to shared memory (US, coalesced rows);
-//   2. per group: interpolation (each thread its column), the common fluxes at
-//      external points (partner state from the face records FRin, Sec. 2.1)
-//      and the normal transformed fluxes at internal DOFs (Eq.
+//   1. the tile's state, metric rows and partner map go to shared memory
+//      with asynchronous copies (coalesced rows);
+//   2. per group: the partners' states of its external points are copied
+//      asynchronously (face records FRin) while the group is interpolated
+//      (each thread its column); then the common fluxes at external points
+//      (Sec. 2.1) and the normal transformed fluxes at internal DOFs (Eq.
 //      "normal_transformed_flux"), then the divergence accumulated in
 //      registers, column by column;
 //   3. dU/dt = -R~ / det J, the RK stage epilogue, and (FRout) the new state's
@@ -39,12 +41,27 @@ constexpr int TE = 32;   // elements per tile (one per lane)
 template <class K, int V>
 struct Smem {
     static constexpr int LDX = V * TE;                       // row stride (values) of US / group rows
+    static constexpr int NM = 1 + 9 + K::NF * 4;             // metric rows (3D, kargs.hpp layout)
     static constexpr int NREC = K::NFE * V;                  // values of one element's face records
     static constexpr int PADREC = NREC % 2 == 0 ? NREC + 1 : NREC;   // odd: conflict-free staging
     static constexpr int STAGE = TE * PADREC;
-    static constexpr int MAIN = (K::NS + K::GR) * LDX;
+    // [US: NS rows][group rows: GR][metric: NM x TE][partner map: NFE x TE (int)]
+    static constexpr int US = 0;
+    static constexpr int XS = K::NS * LDX;
+    static constexpr int MS = XS + K::GR * LDX;
+    static constexpr int PM = MS + NM * TE;
+    static constexpr int MAIN = PM + K::NFE * TE;
     static constexpr int FLOATS = MAIN > STAGE ? MAIN : STAGE;
 };
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// 4-byte asynchronous global -> shared copy (no register staging).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // External-point values of the tile (thread (lane, v) holds w[NS] of its
 // column) into the face-record array: staged per element with an odd stride,
@@ -62,19 +79,36 @@ __device__ __forceinline__ void write_records(const float (&w)[K::NS], float* S,
     }
 }
 
+// One group of flux points: the partners' states of its external points are
+// copied asynchronously into the DOF-flux rows those points will overwrite
+// (each item's copy and use by the same thread), overlapping the
+// interpolation; then the fluxes, then the divergence.
 template <class K, int V, int SYS, int RIE, int G>
-__device__ __forceinline__ void run_groups(const GenArgs& a, const float* US, float* XS, float (&acc)[K::NS], int e0,
-                                           int v, int lane) {
+__device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&acc)[K::NS], int v, int lane) {
     using Grp = typename K::template Grp<G>;
+    using SM = Smem<K, V>;
     constexpr int LDX = V * TE, ND = 3, ND2 = ND * ND;
+    const float* US = sm + SM::US;
+    float* XS = sm + SM::XS;
     float* FS = XS + Grp::NP * LDX;
+    const float* MS = sm + SM::MS;
+    const int* PM = reinterpret_cast<const int*>(sm + SM::PM);
     __syncthreads();                                    // previous group's rows consumed
+    for (int it = threadIdx.x; it < Grp::NP * TE; it += V * TE) {
+        const int4 d = K::desc(Grp::OFF + (it >> 5));
+        if (d.x >= 0) {
+            const int te = it & 31;
+            const float* src = a.FRin + PM[d.x * TE + te];
+            #pragma unroll
+            for (int q = 0; q < V; ++q) cp_async4(FS + (d.z * V + q) * TE + te, src + q);
+        }
+    }
     Grp::interp(US + v * TE + lane, LDX, XS + v * TE + lane, LDX);
+    cp_async_wait_all();
     __syncthreads();
     for (int it = threadIdx.x; it < Grp::NP * TE; it += V * TE) {
         const int r = it >> 5;                          // point row (warp-uniform)
         const int te = it & 31;
-        const int e = min(e0 + te, a.nelem - 1);
         const int4 d = K::desc(Grp::OFF + r);
         float u[V];
         #pragma unroll
@@ -84,12 +118,11 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, const float* US, fl
             const int mrow = 1 + ND2 + d.y * (ND + 1);
             float n[ND];
             #pragma unroll
-            for (int c = 0; c < ND; ++c) n[c] = __ldg(a.metric + (size_t)(mrow + c) * a.ld + e);
-            const float s = __ldg(a.metric + (size_t)(mrow + ND) * a.ld + e);
-            const int pm = __ldg(a.pmap + (size_t)d.x * a.ld + e);
+            for (int c = 0; c < ND; ++c) n[c] = MS[(mrow + c) * TE + te];
+            const float s = MS[(mrow + ND) * TE + te];
             float nb[V], uL[V], uR[V], F[V];
             #pragma unroll
-            for (int q = 0; q < V; ++q) nb[q] = __ldg(a.FRin + pm + q);
+            for (int q = 0; q < V; ++q) nb[q] = FS[(d.z * V + q) * TE + te];
             orient<V>(s > 0.f, u, nb, uL, uR);          // this point on its face's L side when s > 0
             common_flux<SYS, RIE, ND>(uL, uR, n, a.P, F);
             #pragma unroll
@@ -101,7 +134,7 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, const float* US, fl
                 const int ax = (d.w >> (2 + 2 * k)) & 3;
                 float Srow[ND], Ft[V];
                 #pragma unroll
-                for (int i = 0; i < ND; ++i) Srow[i] = __ldg(a.metric + (size_t)(1 + ax * ND + i) * a.ld + e);
+                for (int i = 0; i < ND; ++i) Srow[i] = MS[(1 + ax * ND + i) * TE + te];
                 internal_flux<SYS, ND>(u, Srow, a.P, Ft);
                 #pragma unroll
                 for (int q = 0; q < V; ++q) FS[((d.z + k) * V + q) * TE + te] = Ft[q];
@@ -110,7 +143,7 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, const float* US, fl
     }
     __syncthreads();
     Grp::div(FS + v * TE + lane, LDX, acc);
-    if constexpr (G + 1 < K::NG) run_groups<K, V, SYS, RIE, G + 1>(a, US, XS, acc, e0, v, lane);
+    if constexpr (G + 1 < K::NG) run_groups<K, V, SYS, RIE, G + 1>(a, sm, acc, v, lane);
 }
 
 template <class K, int V, int SYS, int RIE>
@@ -118,8 +151,6 @@ __global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
     extern __shared__ __align__(16) float smem[];
     using SM = Smem<K, V>;
     constexpr int NS = K::NS;
-    float* US = smem;
-    float* XS = smem + NS * SM::LDX;
     const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const KEpi<float>& E = a.E;
     for (int tile = blockIdx.x; tile * TE < a.nelem; tile += gridDim.x) {
@@ -127,15 +158,25 @@ __global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
         const bool valid = e0 + lane < a.nelem;
         const int e = valid ? e0 + lane : a.nelem - 1;  // lanes past the end repeat the last element
         __syncthreads();                                // previous tile's shared memory free
+        // The tile's state, metric rows and partner map, copied asynchronously.
         #pragma unroll 4
         for (int r = 0; r < NS; ++r)
-            US[(r * V + v) * TE + lane] = __ldg(a.U + a.u_off + (size_t)(r * V + v) * a.ld + e);
+            cp_async4(smem + SM::US + (r * V + v) * TE + lane, a.U + a.u_off + (size_t)(r * V + v) * a.ld + e);
+        for (int i = threadIdx.x; i < SM::NM * TE; i += V * TE) {
+            const int k = i >> 5, te = i & 31;
+            cp_async4(smem + SM::MS + i, a.metric + (size_t)k * a.ld + min(e0 + te, a.nelem - 1));
+        }
+        for (int i = threadIdx.x; i < K::NFE * TE; i += V * TE) {
+            const int k = i >> 5, te = i & 31;
+            cp_async4(smem + SM::PM + i, a.pmap + (size_t)k * a.ld + min(e0 + te, a.nelem - 1));
+        }
+        cp_async_wait_all();
         float acc[NS];
         #pragma unroll
         for (int r = 0; r < NS; ++r) acc[r] = 0.f;
-        run_groups<K, V, SYS, RIE, 0>(a, US, XS, acc, e0, v, lane);
+        run_groups<K, V, SYS, RIE, 0>(a, smem, acc, v, lane);   // its first barrier publishes the copies
         // dU/dt = -R~ / det J and the stage update; acc becomes the new state.
-        const float inv = -__ldg(a.metric + e);
+        const float inv = -smem[SM::MS + lane];
         bool bad = false;
         #pragma unroll
         for (int r = 0; r < NS; ++r) {
