@@ -377,7 +377,9 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     run them: the structural non-zeros of [M0; M12] and [M14 | M13] compiled
  *     in, one fused stage kernel per element type and RK stage writing the
  *     next stage's face records, the element types as concurrent branches;
- *     0 = the generic kernels.  Results agree to FP32 rounding. */
+ *     0 = the generic kernels; 2 = as 1, and meshes set up afterwards take the
+ *     operator-specialised kernels also where the record path would run.
+ *     Results agree to FP32 rounding. */
 #define SDRT_OPT_GENERATED 3
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 

@@ -151,7 +151,7 @@ struct sdrt_ctx {
     bool use_tc = false;          // tensor-core interpolation where instantiated (SDRT_OPT_TENSOR_CORES)
     bool use_tc_div = false;      // tensor-core divergence where instantiated (SDRT_OPT_TC_DIVERGENCE)
     bool fuse_rk = true;          // next-stage interpolation in the RK4 stage update (SDRT_OPT_FUSED_RK)
-    bool use_gen = true;          // operator-specialised kernels where generated (SDRT_OPT_GENERATED)
+    int use_gen = 1;              // operator-specialised kernels where generated (SDRT_OPT_GENERATED)
     void* noalloc_scratch = nullptr;   // device address of sdrt_residual_noalloc's static buffer
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
@@ -1136,6 +1136,16 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         m->blocks.push_back(std::move(mb));
     }
     m->nfe_total = canon;
+    if (m->fast && ctx->use_gen == 2 && !ghost && f32 && phys->system == SDRT_EULER && nd == 3 &&
+        phys->riemann == SDRT_RUSANOV) {
+        // SDRT_OPT_GENERATED = 2: the operator-specialised kernels replace the record path.
+        bool all = true;
+        for (auto& bp : m->blocks) {
+            const RefElement& R = ctx->etypes[bp->etype]->R;
+            all = all && gen_launcher(R.shape, R.p) != nullptr;
+        }
+        if (all) m->fast = false;
+    }
     if (m->fast) {
         // Record strides: multiples of 4 values (16-byte bulk copies), odd multiples
         // of 4 for conflict-free shared-memory rows.
@@ -1754,7 +1764,7 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     if (option == SDRT_OPT_TENSOR_CORES) ctx->use_tc = value != 0;
     else if (option == SDRT_OPT_TC_DIVERGENCE) ctx->use_tc_div = value != 0;
     else if (option == SDRT_OPT_FUSED_RK) ctx->fuse_rk = value != 0;
-    else if (option == SDRT_OPT_GENERATED) ctx->use_gen = value != 0;
+    else if (option == SDRT_OPT_GENERATED) ctx->use_gen = value < 0 ? 0 : value > 2 ? 2 : value;
     else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {
@@ -1859,8 +1869,8 @@ int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
     SDRT_CUDA(cudaEventCreate(&b));
     const bool prof = ctx->prof;
     ctx->prof = false;
-    const bool use_gen = ctx->use_gen;
-    ctx->use_gen = false;
+    const int use_gen = ctx->use_gen;
+    ctx->use_gen = 0;
     // Time `reps` residual evaluations of the whole mesh (ms per evaluation).
     auto timed = [&](float* ms) -> int {
         int rr;

@@ -30,6 +30,7 @@
 //      tile's contiguous face records.
 #pragma once
 
+#include "flux_rec.cuh"
 #include "gen_api.hpp"
 #include "generic.cuh"
 
@@ -124,20 +125,46 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
             #pragma unroll
             for (int q = 0; q < V; ++q) nb[q] = FS[(d.z * V + q) * TE + te];
             orient<V>(s > 0.f, u, nb, uL, uR);          // this point on its face's L side when s > 0
-            common_flux<SYS, RIE, ND>(uL, uR, n, a.P, F);
-            #pragma unroll
-            for (int q = 0; q < V; ++q) FS[(d.z * V + q) * TE + te] = s * F[q];
+            if constexpr (SYS == SYS_EULER && RIE == RIE_RUSANOV) {
+                rusanov_rec<float, ND>(uL, uR, n, a.P.gamma, s, F);   // s F, one reciprocal per state
+                #pragma unroll
+                for (int q = 0; q < V; ++q) FS[(d.z * V + q) * TE + te] = F[q];
+            } else {
+                common_flux<SYS, RIE, ND>(uL, uR, n, a.P, F);
+                #pragma unroll
+                for (int q = 0; q < V; ++q) FS[(d.z * V + q) * TE + te] = s * F[q];
+            }
         } else {
             // internal point: one transformed flux component per DOF axis
             const int ndof = d.w & 3;
-            for (int k = 0; k < ndof; ++k) {
-                const int ax = (d.w >> (2 + 2 * k)) & 3;
-                float Srow[ND], Ft[V];
-                #pragma unroll
-                for (int i = 0; i < ND; ++i) Srow[i] = MS[(1 + ax * ND + i) * TE + te];
-                internal_flux<SYS, ND>(u, Srow, a.P, Ft);
-                #pragma unroll
-                for (int q = 0; q < V; ++q) FS[((d.z + k) * V + q) * TE + te] = Ft[q];
+            if constexpr (SYS == SYS_EULER) {
+                // primitive state once per point (one reciprocal), then n . f per axis
+                float inv, vel[ND], p;
+                prim_rec<float, ND>(u, a.P.gamma, inv, vel, p);
+                for (int k = 0; k < ndof; ++k) {
+                    const int ax = (d.w >> (2 + 2 * k)) & 3;
+                    float Srow[ND];
+                    #pragma unroll
+                    for (int i = 0; i < ND; ++i) Srow[i] = MS[(1 + ax * ND + i) * TE + te];
+                    float vn = vel[0] * Srow[0];
+                    #pragma unroll
+                    for (int i = 1; i < ND; ++i) vn = fmaf(vel[i], Srow[i], vn);
+                    float* o = FS + (d.z + k) * V * TE + te;
+                    o[0] = u[0] * vn;
+                    #pragma unroll
+                    for (int i = 0; i < ND; ++i) o[(1 + i) * TE] = fmaf(u[1 + i], vn, p * Srow[i]);
+                    o[(V - 1) * TE] = (u[V - 1] + p) * vn;
+                }
+            } else {
+                for (int k = 0; k < ndof; ++k) {
+                    const int ax = (d.w >> (2 + 2 * k)) & 3;
+                    float Srow[ND], Ft[V];
+                    #pragma unroll
+                    for (int i = 0; i < ND; ++i) Srow[i] = MS[(1 + ax * ND + i) * TE + te];
+                    internal_flux<SYS, ND>(u, Srow, a.P, Ft);
+                    #pragma unroll
+                    for (int q = 0; q < V; ++q) FS[((d.z + k) * V + q) * TE + te] = Ft[q];
+                }
             }
         }
     }
@@ -178,35 +205,48 @@ __global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
         // dU/dt = -R~ / det J and the stage update; acc becomes the new state.
         const float inv = -smem[SM::MS + lane];
         bool bad = false;
-        #pragma unroll
-        for (int r = 0; r < NS; ++r) {
-            const size_t idx = a.u_off + (size_t)(r * V + v) * a.ld + e;
-            const float R = acc[r] * inv;
-            bad |= !isfinite(R);
-            float w;
-            if (E.mode == EPI_STORE) {
-                w = R;
-                if (valid) E.out[idx] = R;
-            } else if (E.mode == EPI_RK_FIRST) {
-                const float u0 = __ldg(E.u0 + idx);
-                w = fmaf(E.cnext, R, u0);
-                if (valid) {
-                    E.uacc[idx] = fmaf(E.cacc, R, u0);
-                    E.unext[idx] = w;
-                }
-            } else if (E.mode == EPI_RK_MID) {
-                const float u0 = __ldg(E.u0 + idx);
-                const float ua = E.uacc[idx];
-                w = fmaf(E.cnext, R, u0);
-                if (valid) {
-                    E.uacc[idx] = fmaf(E.cacc, R, ua);
-                    E.unext[idx] = w;
-                }
-            } else {
-                w = fmaf(E.cacc, R, E.uacc[idx]);
-                if (valid) E.out[idx] = w;
+        const size_t base = a.u_off + (size_t)v * a.ld + e;
+        const size_t rs = (size_t)V * a.ld;           // row stride of one solution point
+        if (E.mode == EPI_STORE) {
+            #pragma unroll
+            for (int r = 0; r < NS; ++r) {
+                acc[r] *= inv;
+                bad |= !isfinite(acc[r]);
+                if (valid) E.out[base + r * rs] = acc[r];
             }
-            acc[r] = w;
+        } else if (E.mode == EPI_RK_FIRST) {
+            #pragma unroll
+            for (int r = 0; r < NS; ++r) {
+                const float R = acc[r] * inv;
+                const float u0 = __ldg(E.u0 + base + r * rs);
+                bad |= !isfinite(R);
+                acc[r] = fmaf(E.cnext, R, u0);
+                if (valid) {
+                    E.uacc[base + r * rs] = fmaf(E.cacc, R, u0);
+                    E.unext[base + r * rs] = acc[r];
+                }
+            }
+        } else if (E.mode == EPI_RK_MID) {
+            #pragma unroll
+            for (int r = 0; r < NS; ++r) {
+                const float R = acc[r] * inv;
+                const float u0 = __ldg(E.u0 + base + r * rs);
+                const float ua = E.uacc[base + r * rs];
+                bad |= !isfinite(R);
+                acc[r] = fmaf(E.cnext, R, u0);
+                if (valid) {
+                    E.uacc[base + r * rs] = fmaf(E.cacc, R, ua);
+                    E.unext[base + r * rs] = acc[r];
+                }
+            }
+        } else {
+            #pragma unroll
+            for (int r = 0; r < NS; ++r) {
+                const float R = acc[r] * inv;
+                bad |= !isfinite(R);
+                acc[r] = fmaf(E.cacc, R, E.uacc[base + r * rs]);
+                if (valid) E.out[base + r * rs] = acc[r];
+            }
         }
         if (bad && valid) *E.flag = 1;
         if (a.FRout) {
