@@ -62,7 +62,9 @@ __device__ __forceinline__ void rusanov_rec_pair(const float* uL, const float* u
     for (int d = 1; d < ND; ++d) vn = __ffma2_rn(vv[d], make_float2(n[d], n[d]), vn);
     const float2 c2 = __fmul2_rn(__fmul2_rn(make_float2(gamma, gamma), p), inv);
     const float cL = c2.x * rsqrtf(c2.x), cR = c2.y * rsqrtf(c2.y);
-    const float phi = fmaxf(fabsf(vn.x) + cL, fabsf(vn.y) + cR);
+    // + 0 (cL + cR): a non-physical state (negative pressure or density, NaN
+    // sound speed) stays NaN instead of being dropped by fmaxf.
+    const float phi = fmaxf(fabsf(vn.x) + cL, fabsf(vn.y) + cR) + 0.0f * (cL + cR);
     const float hs = 0.5f * s;
     F[0] = hs * fmaf(phi, u[0].x - u[0].y, fmaf(u[0].x, vn.x, u[0].y * vn.y));
     const float pp = p.x + p.y;
@@ -91,7 +93,7 @@ __device__ __forceinline__ void rusanov_rec(const T* uL, const T* uR, const T* n
     }
     const T cL = pos_sqrt(gamma * pL * iL);
     const T cR = pos_sqrt(gamma * pR * iR);
-    const T phi = fmax(fabs(vnL) + cL, fabs(vnR) + cR);
+    const T phi = fmax(fabs(vnL) + cL, fabs(vnR) + cR) + T(0) * (cL + cR);
     const T hs = T(0.5) * s;
     F[0] = hs * fma(phi, uL[0] - uR[0], fma(uL[0], vnL, uR[0] * vnR));
     const T pp = pL + pR;
