@@ -133,11 +133,16 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
         if (P.dofs.empty() || P.dofs.size() > 3) throw std::runtime_error("internal point without 1..3 DOFs");
         pts.push_back(P);
     }
+    // Threads per (element, variable) column: large element types split the
+    // rows of every operator application over SPLIT threads (more warps per
+    // SM at the same shared memory per element).
+    const int SPLIT = NS > 20 ? 2 : 1;
+    const int budget = SPLIT > 1 ? kBudget : (NS <= 10 ? kBudget / 2 : kBudget * 3 / 4);
     std::vector<std::vector<int>> groups(1);
     int units = 0;
     for (int i = 0; i < (int)pts.size(); ++i) {
         const int u = 1 + (pts[i].ext ? 1 : (int)pts[i].dofs.size());
-        if (units + u > kBudget && !groups.back().empty()) {
+        if (units + u > budget && !groups.back().empty()) {
             groups.emplace_back();
             units = 0;
         }
@@ -153,6 +158,26 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     long nnzI = 0, nnzD = 0;
     for (auto& r : SI.rows) nnzI += (long)r.size();
     for (auto& c : dcol) nnzD += (long)c.size();
+    const int NSH = (NS + SPLIT - 1) / SPLIT;      // divergence rows per part
+
+    // x[j * ldx] = sum_c A[row_j][c] u[c * ldu] for the rows (row_j, j) listed
+    auto emit_rows = [&](std::ostringstream& o, const std::vector<std::pair<int, int>>& rows) {
+        std::vector<int> used(NS, 0);
+        for (auto& rj : rows)
+            for (auto& e : SI.rows[rj.first]) used[e.first] = 1;
+        for (int c = 0; c < NS; ++c)
+            if (used[c]) o << "        const float u" << c << " = u[" << c << " * ldu];\n";
+        for (auto& rj : rows) {
+            auto& rr = SI.rows[rj.first];
+            std::string e = "0.0f";
+            for (size_t q = 0; q < rr.size(); ++q) {
+                const std::string term = "u" + std::to_string(rr[q].first);
+                e = q == 0 ? flt(rr[q].second) + " * " + term
+                           : "fmaf(" + flt(rr[q].second) + ", " + term + ", " + e + ")";
+            }
+            o << "        x[" << rj.second << " * ldx] = " << e << ";\n";
+        }
+    };
 
     std::ostringstream o;
     const std::string N = key.name;
@@ -189,67 +214,78 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     o << "};\n\n";
     o << "struct " << T << " {\n"
       << "    static constexpr int NS = " << NS << ", NFE = " << NFE << ", NFIU = " << NFIU << ", NFI = " << NFI
-      << ", NF = " << R.nfaces << ", NG = " << groups.size() << ", GR = " << GR << ";\n"
+      << ", NF = " << R.nfaces << ", NG = " << groups.size() << ", GR = " << GR << ", SPLIT = " << SPLIT
+      << ", NSH = " << NSH << ";\n"
       << "    template <int G> struct Grp;\n"
       << "    static __device__ __forceinline__ int4 desc(int i) { return c_desc[i]; }\n";
-    // ext: external-point rows from registers
-    o << "    static __device__ __forceinline__ void ext(const float (&w)[NS], float* __restrict__ o, const int ldo) {\n";
-    for (int r = 0; r < NFE; ++r) {
-        auto& row = SI.rows[r];
-        std::string e = "0.0f";
-        for (size_t j = 0; j < row.size(); ++j) {
-            const std::string term = "w[" + std::to_string(row[j].first) + "]";
-            e = j == 0 ? flt(row[j].second) + " * " + term
-                       : "fmaf(" + flt(row[j].second) + ", " + term + ", " + e + ")";
+    // ext: external-point rows of chunk c (ECH rows), part h, from the state
+    // in shared memory; x indexed from the chunk's first row
+    const int ECH = std::min(NFE, std::max(1, GR - 1)), NECH = (NFE + ECH - 1) / ECH;
+    o << "    static constexpr int ECH = " << ECH << ", NECH = " << NECH << ";\n";
+    o << "    static __device__ __forceinline__ void ext(int c, int h, const float* __restrict__ u, const int ldu, "
+         "float* __restrict__ x, const int ldx) {\n";
+    bool first = true;
+    for (int c = 0; c < NECH; ++c) {
+        const int c0 = c * ECH, c1 = std::min(NFE, c0 + ECH);
+        for (int h = 0; h < SPLIT; ++h) {
+            const int r0 = c0 + h * (c1 - c0) / SPLIT, r1 = c0 + (h + 1) * (c1 - c0) / SPLIT;
+            std::vector<std::pair<int, int>> rows;
+            for (int r = r0; r < r1; ++r) rows.push_back({r, r - c0});
+            o << "      " << (first ? "" : "} else ") << "if (c == " << c << " && h == " << h << ") {\n";
+            first = false;
+            emit_rows(o, rows);
         }
-        o << "        o[" << r << " * ldo] = " << e << ";\n";
     }
-    o << "    }\n};\n\n";
+    o << "      }\n    }\n};\n\n";
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         auto& g = groups[gi];
-        std::vector<int> used(NS, 0);
-        for (int i : g) {
-            const int row = pts[i].ext ? pts[i].id : NFE + pts[i].id;
-            for (auto& e : SI.rows[row]) used[e.first] = 1;
-        }
         int nf = 0;
         for (int i : g) nf += pts[i].ext ? 1 : (int)pts[i].dofs.size();
         o << "template <> struct " << T << "::Grp<" << gi << "> {\n"
           << "    static constexpr int NP = " << g.size() << ", NDOF = " << nf << ", OFF = " << goff[gi] << ";\n"
-          << "    static __device__ __forceinline__ void interp(const float* __restrict__ u, const int ldu, "
+          << "    static __device__ __forceinline__ void interp(int h, const float* __restrict__ u, const int ldu, "
              "float* __restrict__ x, const int ldx) {\n";
-        for (int c = 0; c < NS; ++c)
-            if (used[c]) o << "        const float u" << c << " = u[" << c << " * ldu];\n";
-        for (size_t j = 0; j < g.size(); ++j) {
-            const Point& P = pts[g[j]];
-            const int row = P.ext ? P.id : NFE + P.id;
-            auto& rr = SI.rows[row];
-            std::string e = "0.0f";
-            for (size_t q = 0; q < rr.size(); ++q) {
-                const std::string term = "u" + std::to_string(rr[q].first);
-                e = q == 0 ? flt(rr[q].second) + " * " + term
-                           : "fmaf(" + flt(rr[q].second) + ", " + term + ", " + e + ")";
+        const int np = (int)g.size();
+        for (int h = 0; h < SPLIT; ++h) {
+            std::vector<std::pair<int, int>> rows;
+            for (int j = h * np / SPLIT; j < (h + 1) * np / SPLIT; ++j) {
+                const Point& P = pts[g[j]];
+                rows.push_back({P.ext ? P.id : NFE + P.id, j});
             }
-            o << "        x[" << j << " * ldx] = " << e << ";\n";
+            o << "      " << (h ? "} else " : "") << (h + 1 < SPLIT ? "if (h == " + std::to_string(h) + ") " : "")
+              << "{\n";
+            emit_rows(o, rows);
         }
-        o << "    }\n"
-          << "    static __device__ __forceinline__ void div(const float* __restrict__ f, const int ldf, "
-             "float (&r)[" << NS << "]) {\n";
-        int fs = 0;
-        for (int i : g) {
-            const Point& P = pts[i];
-            std::vector<int> cols;
-            if (P.ext) cols.push_back(P.id);
-            else
-                for (int nu : P.dofs) cols.push_back(NFE + nu);
-            for (int col : cols) {
-                o << "        { const float t = f[" << fs << " * ldf];";
-                for (auto& e : dcol[col]) o << " r[" << e.first << "] = fmaf(" << flt(e.second) << ", t, r[" << e.first << "]);";
-                o << " }\n";
-                ++fs;
+        o << "      }\n    }\n"
+          << "    static __device__ __forceinline__ void div(int h, const float* __restrict__ f, const int ldf, "
+             "float (&r)[" << NSH << "]) {\n";
+        for (int h = 0; h < SPLIT; ++h) {
+            const int q0 = h * NSH, q1 = std::min(NS, (h + 1) * NSH);
+            o << "      " << (h ? "} else " : "") << (h + 1 < SPLIT ? "if (h == " + std::to_string(h) + ") " : "")
+              << "{\n";
+            int fs = 0;
+            for (int i : g) {
+                const Point& P = pts[i];
+                std::vector<int> cols;
+                if (P.ext) cols.push_back(P.id);
+                else
+                    for (int nu : P.dofs) cols.push_back(NFE + nu);
+                for (int col : cols) {
+                    bool any = false;
+                    for (auto& e : dcol[col]) any = any || (e.first >= q0 && e.first < q1);
+                    if (any) {
+                        o << "        { const float t = f[" << fs << " * ldf];";
+                        for (auto& e : dcol[col])
+                            if (e.first >= q0 && e.first < q1)
+                                o << " r[" << e.first - q0 << "] = fmaf(" << flt(e.second) << ", t, r[" << e.first - q0
+                                  << "]);";
+                        o << " }\n";
+                    }
+                    ++fs;
+                }
             }
         }
-        o << "    }\n};\n\n";
+        o << "      }\n    }\n};\n\n";
     }
     o << "}  // namespace\n}  // namespace gen\n\n"
       << "int launch_gen_" << N << "(int kind, const GenArgs& a, int V, int sys, int rie, int nsm, cudaStream_t st) {\n"

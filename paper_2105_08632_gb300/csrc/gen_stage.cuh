@@ -3,20 +3,26 @@
 // csrc/gen/opgen.cpp writes at build time; K supplies the operator code:
 //   K::NS, NFE, NG, GR          sizes, number of flux-point groups, the largest
 //                                group's point + DOF rows
-//   K::Grp<g>::interp(u, ldu, x, ldx)   point states of group g, x = A_g u
-//                                        (rows of [M0; M12], structural
-//                                        non-zeros only, FP32 immediates)
-//   K::Grp<g>::div(f, ldf, r)   r += D_g f (columns of [M14 | M13] of the
-//                                group's DOFs)
+//   K::SPLIT, NSH               threads per (element, variable) column and the
+//                                divergence rows each of them owns
+//   K::Grp<g>::interp(h, u, ldu, x, ldx)  point states of group g, x = A_g u,
+//                                        part h of the rows (rows of
+//                                        [M0; M12], structural non-zeros
+//                                        only, FP32 immediates)
+//   K::Grp<g>::div(h, f, ldf, r)  r += D_g f for the rows of part h (columns
+//                                of [M14 | M13] of the group's DOFs)
 //   K::desc(i)                  point descriptors: external point sigma and
 //                                its face, or internal point with its DOF axes,
 //                                and the first DOF row of the point
-//   K::ext(w, o, ldo)           o = M0 w (external points)
+//   K::ext(c, h, u, ldu, x, ldx)  x = M0 u for chunk c of the external points,
+//                                part h
 //
-// A CTA works on a tile of 32 consecutive elements of one block with V warps:
-// thread (lane, v) owns variable v of element e0 + lane for the operator
-// applications (one column of the paper's state matrix, App. B), and the
-// threads share the tile's points for the flux evaluation:
+// A CTA works on a tile of 32 consecutive elements of one block with
+// SPLIT x V warps: thread (lane, v, h) owns part h of the rows of variable v
+// of element e0 + lane for the operator applications (one column of the
+// paper's state matrix, App. B), and the threads share the tile's points for
+// the flux evaluation.  Persistent CTAs walk the tiles and prefetch the next
+// tile's rows into L2:
 //   1. the tile's state, metric rows and partner map go to shared memory
 //      with asynchronous copies (coalesced rows);
 //   2. per group: the partners' states of its external points are copied
@@ -41,18 +47,21 @@ constexpr int TE = 32;   // elements per tile (one per lane)
 
 template <class K, int V>
 struct Smem {
+    static constexpr int NT = K::SPLIT * V * TE;             // threads of a CTA
     static constexpr int LDX = V * TE;                       // row stride (values) of US / group rows
     static constexpr int NM = 1 + 9 + K::NF * 4;             // metric rows (3D, kargs.hpp layout)
-    static constexpr int NREC = K::NFE * V;                  // values of one element's face records
-    static constexpr int PADREC = NREC % 2 == 0 ? NREC + 1 : NREC;   // odd: conflict-free staging
-    static constexpr int STAGE = TE * PADREC;
     // [US: NS rows][group rows: GR][metric: NM x TE][partner map: NFE x TE (int)]
     static constexpr int US = 0;
     static constexpr int XS = K::NS * LDX;
     static constexpr int MS = XS + K::GR * LDX;
     static constexpr int PM = MS + NM * TE;
     static constexpr int MAIN = PM + K::NFE * TE;
-    static constexpr int FLOATS = MAIN > STAGE ? MAIN : STAGE;
+    // face-record staging of one chunk of ECH external points per element
+    // (odd element stride: conflict-free), after US
+    static constexpr int CREC = K::ECH * V;
+    static constexpr int PADREC = CREC % 2 == 0 ? CREC + 1 : CREC;
+    static constexpr int STAGE_END = XS + TE * PADREC;
+    static constexpr int FLOATS = MAIN > STAGE_END ? MAIN : STAGE_END;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -63,20 +72,42 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-// External-point values of the tile (thread (lane, v) holds w[NS] of its
-// column) into the face-record array: staged per element with an odd stride,
-// then written as one contiguous run (the tile's elements are consecutive).
+// The tile's rows of a [rows][ld] array (element fastest) into shared memory,
+// [rows][TE], with asynchronous copies (lanes past the end repeat the last
+// element).
+template <int NT, typename E>
+__device__ __forceinline__ void stage_rows(E* dst, const E* src, int rows, int ld, int e0, int nelem) {
+    for (int i = threadIdx.x; i < rows * TE; i += NT)
+        cp_async4(dst + i, src + (size_t)(i >> 5) * ld + min(e0 + (i & 31), nelem - 1));
+}
+// L2 prefetch of the same rows for a later tile (one 128-byte line per row).
+template <int NT, typename E>
+__device__ __forceinline__ void prefetch_rows(const E* src, int rows, int ld, int e0) {
+    for (int i = threadIdx.x; i < rows; i += NT) prefetch_l2(src + (size_t)i * ld + e0);
+}
+
+// The external-point values of the tile's state (in US) into the face-record
+// array, chunk by chunk: each chunk staged per element with an odd stride and
+// written as one run per element (the tile's elements are consecutive).
 template <class K, int V>
-__device__ __forceinline__ void write_records(const float (&w)[K::NS], float* S, float* dst, int nvalid, int v,
-                                              int lane) {
+__device__ __forceinline__ void write_records(float* sm, float* dst, int nvalid, int v, int h, int lane) {
     using SM = Smem<K, V>;
-    K::ext(w, S + lane * SM::PADREC + v, V);
-    __syncthreads();
-    const int n = nvalid * SM::NREC;
-    for (int i = threadIdx.x; i < n; i += V * TE) {
-        const int el = i / SM::NREC;
-        dst[i] = S[el * SM::PADREC + (i - el * SM::NREC)];
+    float* S = sm + SM::XS;
+    #pragma unroll 1
+    for (int c = 0; c < K::NECH; ++c) {
+        const int c0 = c * K::ECH;
+        const int rows = min(K::ECH, K::NFE - c0);
+        __syncthreads();                                // staging free, US complete
+        K::ext(c, h, sm + SM::US + v * TE + lane, SM::LDX, S + lane * SM::PADREC + v, V);
+        __syncthreads();
+        const int nv = rows * V;
+        for (int i = threadIdx.x; i < nvalid * nv; i += SM::NT) {
+            const int el = i / nv;
+            const int j = i - el * nv;
+            dst[((size_t)el * K::NFE + c0) * V + j] = S[el * SM::PADREC + j];
+        }
     }
 }
 
@@ -85,17 +116,17 @@ __device__ __forceinline__ void write_records(const float (&w)[K::NS], float* S,
 // (each item's copy and use by the same thread), overlapping the
 // interpolation; then the fluxes, then the divergence.
 template <class K, int V, int SYS, int RIE, int G>
-__device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&acc)[K::NS], int v, int lane) {
+__device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&acc)[K::NSH], int v, int h, int lane) {
     using Grp = typename K::template Grp<G>;
     using SM = Smem<K, V>;
-    constexpr int LDX = V * TE, ND = 3, ND2 = ND * ND;
+    constexpr int LDX = V * TE, ND = 3, ND2 = ND * ND, NT = SM::NT;
     const float* US = sm + SM::US;
     float* XS = sm + SM::XS;
     float* FS = XS + Grp::NP * LDX;
     const float* MS = sm + SM::MS;
     const int* PM = reinterpret_cast<const int*>(sm + SM::PM);
     __syncthreads();                                    // previous group's rows consumed
-    for (int it = threadIdx.x; it < Grp::NP * TE; it += V * TE) {
+    for (int it = threadIdx.x; it < Grp::NP * TE; it += NT) {
         const int4 d = K::desc(Grp::OFF + (it >> 5));
         if (d.x >= 0) {
             const int te = it & 31;
@@ -104,10 +135,10 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
             for (int q = 0; q < V; ++q) cp_async4(FS + (d.z * V + q) * TE + te, src + q);
         }
     }
-    Grp::interp(US + v * TE + lane, LDX, XS + v * TE + lane, LDX);
+    Grp::interp(h, US + v * TE + lane, LDX, XS + v * TE + lane, LDX);
     cp_async_wait_all();
     __syncthreads();
-    for (int it = threadIdx.x; it < Grp::NP * TE; it += V * TE) {
+    for (int it = threadIdx.x; it < Grp::NP * TE; it += NT) {
         const int r = it >> 5;                          // point row (warp-uniform)
         const int te = it & 31;
         const int4 d = K::desc(Grp::OFF + r);
@@ -169,54 +200,59 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
         }
     }
     __syncthreads();
-    Grp::div(FS + v * TE + lane, LDX, acc);
-    if constexpr (G + 1 < K::NG) run_groups<K, V, SYS, RIE, G + 1>(a, sm, acc, v, lane);
+    Grp::div(h, FS + v * TE + lane, LDX, acc);
+    if constexpr (G + 1 < K::NG) run_groups<K, V, SYS, RIE, G + 1>(a, sm, acc, v, h, lane);
 }
 
 template <class K, int V, int SYS, int RIE>
-__global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
+__global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen_stage(const GenArgs a) {
     extern __shared__ __align__(16) float smem[];
     using SM = Smem<K, V>;
-    constexpr int NS = K::NS;
-    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NS = K::NS, NSH = K::NSH, NT = SM::NT;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = w % V, h = w / V;                      // thread (lane, v, h): rows of part h of column (e, v)
     const KEpi<float>& E = a.E;
+    const float* Ub = a.U + a.u_off;
     for (int tile = blockIdx.x; tile * TE < a.nelem; tile += gridDim.x) {
         const int e0 = tile * TE;
         const bool valid = e0 + lane < a.nelem;
         const int e = valid ? e0 + lane : a.nelem - 1;  // lanes past the end repeat the last element
         __syncthreads();                                // previous tile's shared memory free
-        // The tile's state, metric rows and partner map, copied asynchronously.
-        #pragma unroll 4
-        for (int r = 0; r < NS; ++r)
-            cp_async4(smem + SM::US + (r * V + v) * TE + lane, a.U + a.u_off + (size_t)(r * V + v) * a.ld + e);
-        for (int i = threadIdx.x; i < SM::NM * TE; i += V * TE) {
-            const int k = i >> 5, te = i & 31;
-            cp_async4(smem + SM::MS + i, a.metric + (size_t)k * a.ld + min(e0 + te, a.nelem - 1));
-        }
-        for (int i = threadIdx.x; i < K::NFE * TE; i += V * TE) {
-            const int k = i >> 5, te = i & 31;
-            cp_async4(smem + SM::PM + i, a.pmap + (size_t)k * a.ld + min(e0 + te, a.nelem - 1));
+        // The tile's state, metric rows and partner map, copied asynchronously;
+        // the next tile's rows prefetched into L2 meanwhile.
+        stage_rows<NT>(smem + SM::US, Ub, NS * V, a.ld, e0, a.nelem);
+        stage_rows<NT>(smem + SM::MS, a.metric, SM::NM, a.ld, e0, a.nelem);
+        stage_rows<NT>(reinterpret_cast<int*>(smem + SM::PM), a.pmap, K::NFE, a.ld, e0, a.nelem);
+        const int en = (tile + gridDim.x) * TE;
+        if (en < a.nelem) {
+            prefetch_rows<NT>(Ub, NS * V, a.ld, en);
+            prefetch_rows<NT>(a.metric, SM::NM, a.ld, en);
+            prefetch_rows<NT>(a.pmap, K::NFE, a.ld, en);
         }
         cp_async_wait_all();
-        float acc[NS];
+        float acc[NSH];
         #pragma unroll
-        for (int r = 0; r < NS; ++r) acc[r] = 0.f;
-        run_groups<K, V, SYS, RIE, 0>(a, smem, acc, v, lane);   // its first barrier publishes the copies
-        // dU/dt = -R~ / det J and the stage update; acc becomes the new state.
+        for (int r = 0; r < NSH; ++r) acc[r] = 0.f;
+        run_groups<K, V, SYS, RIE, 0>(a, smem, acc, v, h, lane);   // its first barrier publishes the copies
+        // dU/dt = -R~ / det J and the stage update of this thread's rows
+        // rho = h NSH + r; acc becomes the new state.
         const float inv = -smem[SM::MS + lane];
         bool bad = false;
-        const size_t base = a.u_off + (size_t)v * a.ld + e;
         const size_t rs = (size_t)V * a.ld;           // row stride of one solution point
+        const size_t base = a.u_off + (size_t)v * a.ld + e + (size_t)(h * NSH) * rs;
+        const int nrow = min(NSH, NS - h * NSH);
         if (E.mode == EPI_STORE) {
             #pragma unroll
-            for (int r = 0; r < NS; ++r) {
+            for (int r = 0; r < NSH; ++r) {
+                if (r >= nrow) break;
                 acc[r] *= inv;
                 bad |= !isfinite(acc[r]);
                 if (valid) E.out[base + r * rs] = acc[r];
             }
         } else if (E.mode == EPI_RK_FIRST) {
             #pragma unroll
-            for (int r = 0; r < NS; ++r) {
+            for (int r = 0; r < NSH; ++r) {
+                if (r >= nrow) break;
                 const float R = acc[r] * inv;
                 const float u0 = __ldg(E.u0 + base + r * rs);
                 bad |= !isfinite(R);
@@ -228,7 +264,8 @@ __global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
             }
         } else if (E.mode == EPI_RK_MID) {
             #pragma unroll
-            for (int r = 0; r < NS; ++r) {
+            for (int r = 0; r < NSH; ++r) {
+                if (r >= nrow) break;
                 const float R = acc[r] * inv;
                 const float u0 = __ldg(E.u0 + base + r * rs);
                 const float ua = E.uacc[base + r * rs];
@@ -241,7 +278,8 @@ __global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
             }
         } else {
             #pragma unroll
-            for (int r = 0; r < NS; ++r) {
+            for (int r = 0; r < NSH; ++r) {
+                if (r >= nrow) break;
                 const float R = acc[r] * inv;
                 bad |= !isfinite(R);
                 acc[r] = fmaf(E.cacc, R, E.uacc[base + r * rs]);
@@ -250,51 +288,64 @@ __global__ void __launch_bounds__(V * TE, 2) k_gen_stage(const GenArgs a) {
         }
         if (bad && valid) *E.flag = 1;
         if (a.FRout) {
-            __syncthreads();                            // every group's shared rows consumed
-            write_records<K, V>(acc, smem, a.FRout + a.fr_base + (size_t)e0 * SM::NREC, min(TE, a.nelem - e0), v,
+            // the new state into US (every group has read it), then its face records
+            __syncthreads();
+            #pragma unroll
+            for (int r = 0; r < NSH; ++r)
+                if (r < nrow) smem[SM::US + ((h * NSH + r) * V + v) * TE + lane] = acc[r];
+            write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h,
                                 lane);
         }
     }
 }
 
 template <class K, int V>
-__global__ void __launch_bounds__(V * TE) k_gen_interp(const GenArgs a) {
+__global__ void __launch_bounds__(K::SPLIT * V * TE) k_gen_interp(const GenArgs a) {
     extern __shared__ __align__(16) float smem[];
     using SM = Smem<K, V>;
-    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NT = SM::NT;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = w % V, h = w / V;
     for (int tile = blockIdx.x; tile * TE < a.nelem; tile += gridDim.x) {
         const int e0 = tile * TE;
-        const int e = min(e0 + lane, a.nelem - 1);
-        float w[K::NS];
-        #pragma unroll
-        for (int r = 0; r < K::NS; ++r) w[r] = __ldg(a.U + a.u_off + (size_t)(r * V + v) * a.ld + e);
         __syncthreads();                                // previous tile's staging read
-        write_records<K, V>(w, smem, a.FRout + a.fr_base + (size_t)e0 * SM::NREC, min(TE, a.nelem - e0), v, lane);
+        stage_rows<NT>(smem + SM::US, a.U + a.u_off, K::NS * V, a.ld, e0, a.nelem);
+        cp_async_wait_all();
+        write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h, lane);
     }
 }
 
+// Persistent grid: every CTA that fits on the SMs at once, at most one per tile.
+template <typename Kern>
+int persistent_ctas(Kern k, int threads, int smem, int tiles, int nsm) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return tiles < per * nsm ? tiles : per * nsm;
+}
+
 template <class K, int V, int SYS, int RIE>
-int launch_gen_v(int kind, const GenArgs& a, cudaStream_t st) {
+int launch_gen_v(int kind, const GenArgs& a, int nsm, cudaStream_t st) {
     using SM = Smem<K, V>;
     const int tiles = (a.nelem + TE - 1) / TE;
     if (kind == 0) {
         auto k = k_gen_interp<K, V>;
-        const int smem = SM::STAGE * (int)sizeof(float);
+        const int smem = SM::STAGE_END * (int)sizeof(float);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k<<<tiles, V * TE, smem, st>>>(a);
+        k<<<persistent_ctas(k, SM::NT, smem, tiles, nsm), SM::NT, smem, st>>>(a);
     } else {
         auto k = k_gen_stage<K, V, SYS, RIE>;
         const int smem = SM::FLOATS * (int)sizeof(float);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k<<<tiles, V * TE, smem, st>>>(a);
+        k<<<persistent_ctas(k, SM::NT, smem, tiles, nsm), SM::NT, smem, st>>>(a);
     }
     return 0;
 }
 
 // Instantiated combinations: 3D Euler with the Rusanov flux (five variables).
 template <class K>
-int launch_gen(int kind, const GenArgs& a, int V, int sys, int rie, int /*nsm*/, cudaStream_t st) {
-    if (V == 5 && sys == SYS_EULER && rie == RIE_RUSANOV) return launch_gen_v<K, 5, SYS_EULER, RIE_RUSANOV>(kind, a, st);
+int launch_gen(int kind, const GenArgs& a, int V, int sys, int rie, int nsm, cudaStream_t st) {
+    if (V == 5 && sys == SYS_EULER && rie == RIE_RUSANOV)
+        return launch_gen_v<K, 5, SYS_EULER, RIE_RUSANOV>(kind, a, nsm, st);
     return -1;
 }
 
