@@ -397,6 +397,14 @@ int sdrt_profile_enable(sdrt_ctx* ctx, int enable);
  * last replay's timings: collect after every sdrt_rk4_step call. */
 int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out);
 
+/* The same timings split by mesh block: ADD to ms_out[row * 4 + kind] and
+ * count_out[row * 4 + kind], row 0 for launches that cover every block of a
+ * mesh (generic and record kernels), row b + 1 for launches of block b alone
+ * (the operator-specialised kernels, one launch per block; blocks past
+ * max_blocks count in row 0).  Arrays of 4 (max_blocks + 1) entries, caller
+ * owned.  Consumes the recorded timings like sdrt_profile_collect. */
+int sdrt_profile_collect_blocks(sdrt_ctx* ctx, int max_blocks, double* ms_out, int64_t* count_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -387,7 +387,8 @@ int gen_launch_blocks(sdrt_ctx* ctx, Mesh& m, int kind, const float* U, const fl
         a.FRout = FRout;
         a.P = P;
         a.E = E;
-        const int s = prof_begin(ctx, kind == 0 ? KIND_INTERP : KIND_RESIDUAL, st);
+        // timing slot of this block's launch (kind | (block + 1) << 8: sdrt_profile_collect_blocks)
+        const int s = prof_begin(ctx, (kind == 0 ? KIND_INTERP : KIND_RESIDUAL) | ((b + 1) << 8), st);
         const int r = mb.gen(kind, a, m.nvar, m.phys.system, m.phys.riemann, ctx->nsm, st);
         prof_end(ctx, s, st);
         if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "generated kernel not instantiated for this system");
@@ -1788,6 +1789,24 @@ int sdrt_profile_enable(sdrt_ctx* ctx, int enable) {
     return SDRT_OK;
 }
 
+int sdrt_profile_collect_blocks(sdrt_ctx* ctx, int max_blocks, double* ms_out, int64_t* count_out) {
+    if (!ctx || !ms_out || !count_out || max_blocks < 0) return SDRT_ERR_ARG;
+    if (ctx->host_only) return fail(ctx, SDRT_ERR_STATE, "host-only context");
+    SDRT_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int s : ctx->pending) {
+        float t = 0;
+        SDRT_CUDA(cudaEventElapsedTime(&t, ctx->ev[2 * s], ctx->ev[2 * s + 1]));
+        const int kind = ctx->slot_kind[s] & 0xff;
+        int row = ctx->slot_kind[s] >> 8;         // 0: launch over all blocks, b + 1: block b only
+        if (row > max_blocks) row = 0;
+        ms_out[row * KIND_COUNT + kind] += t;
+        count_out[row * KIND_COUNT + kind] += 1;
+    }
+    ctx->pending.clear();
+    ctx->eager_next = 0;
+    return SDRT_OK;
+}
+
 int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out) {
     if (!ctx || !ms_out || !count_out) return SDRT_ERR_ARG;
     if (ctx->host_only) return fail(ctx, SDRT_ERR_STATE, "host-only context");
@@ -1795,8 +1814,8 @@ int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out) {
     for (int s : ctx->pending) {
         float t = 0;
         SDRT_CUDA(cudaEventElapsedTime(&t, ctx->ev[2 * s], ctx->ev[2 * s + 1]));
-        ms_out[ctx->slot_kind[s]] += t;
-        count_out[ctx->slot_kind[s]] += 1;
+        ms_out[ctx->slot_kind[s] & 0xff] += t;
+        count_out[ctx->slot_kind[s] & 0xff] += 1;
     }
     ctx->pending.clear();
     ctx->eager_next = 0;

@@ -26,7 +26,7 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_get_block_layout", "sdrt_get_sol_points", "sdrt_get_face_map", "sdrt_residual",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
             "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option",
-            "sdrt_autotune", "sdrt_get_tiles"]
+            "sdrt_autotune", "sdrt_get_tiles", "sdrt_profile_collect_blocks"]
 
 
 class SdrtError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
         "sdrt_launch_count": (I64, [P]),
         "sdrt_profile_enable": (I, [P, I]),
         "sdrt_profile_collect": (I, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "sdrt_profile_collect_blocks": (I, [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "sdrt_residual_noalloc": (I, [P, I, P, P]),
         "sdrt_set_option": (I, [P, I, I]),
         "sdrt_autotune": (I, [P, I, P, I]),
@@ -352,6 +353,16 @@ def sdrt_profile_collect(ctx):
     cnt = (ctypes.c_int64 * 4)()
     _check(ctx, lib().sdrt_profile_collect(ctx, ms, cnt))
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def sdrt_profile_collect_blocks(ctx, nblocks):
+    """List of nblocks + 1 dicts kind -> (milliseconds, launches): entry 0 for
+    launches over all blocks, entry b + 1 for launches of block b alone."""
+    n = 4 * (nblocks + 1)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(ctx, lib().sdrt_profile_collect_blocks(ctx, int(nblocks), ms, cnt))
+    return [{k: (ms[4 * r + i], cnt[4 * r + i]) for i, k in enumerate(KERNEL_KINDS)} for r in range(nblocks + 1)]
 
 
 # ---------------------------------------------------------------------------
