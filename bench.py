@@ -461,6 +461,22 @@ N_SOL = {"tri": lambda p: (p + 1) * (p + 2) // 2, "quad": lambda p: (p + 1) ** 2
          "hex": lambda p: (p + 1) ** 3}
 
 
+def full_ndof(name, ncell=None):
+    """DOF of a full-size workload from its element counts (no mesh built)."""
+    if name == "euler":
+        return 6 * (ncell or NCELL) ** 3 * N_SOL["tet"](3) * 5
+    if name == "tgv":
+        return 6 * (ncell or 48) ** 3 * N_SOL["tet"](4) * 5
+    f = ncell / 40.0 if ncell else 1.0
+    total = 0
+    for kind, p, nc, n1, n2 in MIXED_PARTS:
+        m = max(12, int(round(nc * f)))
+        a, b_ = max(1, int(round(n1 * f))), max(1, int(round(n2 * f)))
+        main = N_SOL["hex"](p) * a if kind == "hex" else N_SOL["tet"](p) * 6 * a
+        total += m * m * (main + N_SOL["pri"](p) * 2 * b_) * 5
+    return total
+
+
 def run_reference(args):
     """The oracle as the reference arm: one RK4 step of a bounded sample of the
     workload per bench step (its independent meshes in parallel processes),
@@ -486,8 +502,7 @@ def run_reference(args):
     pool.close()
     step_s = float(np.mean(secs))
     v = ndof * 4 / step_s
-    full = Workload(args.workload, args.ncell, 0)
-    ndof_full = sum(N_SOL[b["shape"]](p) * full.nvar * len(b["verts"]) for b, p in zip(full.mesh["blocks"], full.degrees))
+    ndof_full = full_ndof(args.workload, args.ncell)
     label = workload_label(args.workload, args.ncell)
     sample = (f"{small.label} ({small.nelem} elements, {len(jobs)} independent mesh(es) in {pool.n} processes), "
               f"one RK4 step per bench step; {len(secs)} of {args.steps} steps timed within the "

@@ -66,3 +66,24 @@ def test_clock_sample_parsing():
     assert c["reasons"] == ["sw_power_cap"]
     empty = bench.ClockSampler.parse("")
     assert empty["sm_mhz"] is None and empty["samples"] == 0
+
+
+def test_full_size_dof_counts():
+    """The reference arm's projection uses element counts without building the
+    mesh: the counts of the workloads' stated sizes."""
+    assert bench.full_ndof("euler") == 82944 * 20 * 5
+    assert bench.full_ndof("tgv") == 663552 * 35 * 5
+    # mixed: hexahedra / x-prisms p1, tets / z-prisms p2, hexahedra / x-prisms p3, tets / z-prisms p4
+    want = (40 * 40 * (100 * 8 + 44 * 2 * 6) + 32 * 32 * (16 * 6 * 10 + 10 * 2 * 18)
+            + 24 * 24 * (45 * 64 + 21 * 2 * 40) + 16 * 16 * (11 * 6 * 35 + 6 * 2 * 75)) * 5
+    assert bench.full_ndof("mixed") == want == 34624000
+
+
+def test_byte_models_per_element():
+    """Residual bytes s V (3 N_s + 2 N_fe) + geometry + connectivity for the
+    degree-3 tetrahedron (FP32, Euler): 4 * 5 * (60 + 80) + (1 + 9 + 16) * 4 + 32."""
+    assert bench.residual_bytes(TET3, 5, 4, False) == 2800 + 104 + 32
+    g = bench.generated_bytes(TET3, 5, 4)
+    vol, rec, side = 400, 800, 104 + 160
+    assert g["interp_ext"] == vol + rec
+    assert g["residual"] == 4 * (vol + rec + side) + 13 * vol + 3 * rec
