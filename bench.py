@@ -748,8 +748,9 @@ def measure(sdrt, ctx, stream, flush, spec, args, steps, warmup, dist, local, wo
                 "kernel_sources_sha256_16": kernel_sources_sha(family),
                 "kernels": entries,
                 "timing": "kernel durations from a second pass of the same steps with per-launch events "
-                          "inside the graph (ms_per_step there: %.4f); value and ms_per_step from the pass "
-                          "without them" % (inst_total / max(steps, 1)),
+                          "inside the graph (element types' kernels one after the other instead of concurrent; "
+                          "ms_per_step there: %.4f); value and ms_per_step from the pass without them"
+                          % (inst_total / max(steps, 1)),
                 "fused_rk_stages": fused,
                 "step_hbm_frac": (4 * sum(res_b) / (ms_per_step / 1e3) / 1e9) / peak,
                 "step_hbm_frac_implementation": (impl_step / (ms_per_step / 1e3) / 1e9) / peak}

@@ -386,7 +386,10 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 /* Per-launch device timing with CUDA events recorded on the context's stream
  * around every kernel the context launches, including inside the captured
  * RK4 graphs (enabling or disabling drops captured graphs, which are then
- * re-captured).  Costs two event records per launch. */
+ * re-captured).  Costs two event records per launch.  While it is on, the
+ * element types' kernels of the operator-specialised path run one after the
+ * other instead of as concurrent branches, so that each launch is timed
+ * alone. */
 int sdrt_profile_enable(sdrt_ctx* ctx, int enable);
 
 /* Synchronise the stream, then ADD to ms_out[kind] the device milliseconds and

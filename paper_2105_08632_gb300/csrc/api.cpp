@@ -364,12 +364,14 @@ KPhys<T> make_phys(const sdrt_physics& p) {
 // face records FRout, 1 fused stage) per block; with several blocks each
 // block is a branch of its own stream, forked from and joined to the
 // context's stream (concurrent kernels; inside a graph capture, parallel
-// graph branches).
+// graph branches), except while per-launch timing is on.
 int gen_launch_blocks(sdrt_ctx* ctx, Mesh& m, int kind, const float* U, const float* FRin, float* FRout,
                       const KEpi<float>& E) {
     const KPhys<float> P = make_phys<float>(m.phys);
     const int nb = (int)m.blocks.size();
-    const bool fork = nb > 1;
+    // With per-launch timing on, the branches run one after the other on the
+    // context's stream, so that each launch's events time that launch alone.
+    const bool fork = nb > 1 && !ctx->prof;
     if (fork) SDRT_CUDA(cudaEventRecord(m.fork_ev, ctx->stream));
     for (int b = 0; b < nb; ++b) {
         MBlock& mb = *m.blocks[b];
