@@ -137,7 +137,7 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     // rows of every operator application over SPLIT threads (more warps per
     // SM at the same shared memory per element).
     const int SPLIT = NS > 20 ? 2 : 1;
-    const int budget = SPLIT > 1 ? kBudget : kBudget / 2;
+    const int budget = SPLIT > 1 ? kBudget : (NS <= 10 ? kBudget / 2 : kBudget * 3 / 4);
     std::vector<std::vector<int>> groups(1);
     int units = 0;
     for (int i = 0; i < (int)pts.size(); ++i) {
@@ -215,7 +215,7 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     o << "struct " << T << " {\n"
       << "    static constexpr int NS = " << NS << ", NFE = " << NFE << ", NFIU = " << NFIU << ", NFI = " << NFI
       << ", NF = " << R.nfaces << ", NG = " << groups.size() << ", GR = " << GR << ", SPLIT = " << SPLIT
-      << ", NSH = " << NSH << ", PBALL = " << (NFE <= 40 ? 1 : 0) << ";\n"
+      << ", NSH = " << NSH << ";\n"
       << "    template <int G> struct Grp;\n"
       << "    static __device__ __forceinline__ int4 desc(int i) { return c_desc[i]; }\n";
     // ext: external-point rows of chunk c (ECH rows), part h, from the state

@@ -51,16 +51,11 @@ struct Smem {
     static constexpr int LDX = V * TE;                       // row stride (values) of US / group rows
     static constexpr int NM = 1 + 9 + K::NF * 4;             // metric rows (3D, kargs.hpp layout)
     // [US: NS rows][group rows: GR][metric: NM x TE][partner map: NFE x TE (int)]
-    // and, with PBALL (element types with few external points), a second
-    // partner-map buffer (the next tile's) and the partners' states of every
-    // external point of the tile [NFE][V][TE]
     static constexpr int US = 0;
     static constexpr int XS = K::NS * LDX;
     static constexpr int MS = XS + K::GR * LDX;
     static constexpr int PM = MS + NM * TE;
-    static constexpr int PM2 = PM + K::NFE * TE;
-    static constexpr int PB = PM2 + (K::PBALL ? K::NFE * TE : 0);
-    static constexpr int MAIN = PB + (K::PBALL ? K::NFE * V * TE : 0);
+    static constexpr int MAIN = PM + K::NFE * TE;
     // face-record staging of one chunk of ECH external points per element
     // (odd element stride: conflict-free), after US
     static constexpr int CREC = K::ECH * V;
@@ -130,21 +125,18 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
     float* FS = XS + Grp::NP * LDX;
     const float* MS = sm + SM::MS;
     const int* PM = reinterpret_cast<const int*>(sm + SM::PM);
-    const float* PB = sm + SM::PB;
     __syncthreads();                                    // previous group's rows consumed
-    if constexpr (!K::PBALL) {
-        for (int it = threadIdx.x; it < Grp::NP * TE; it += NT) {
-            const int4 d = K::desc(Grp::OFF + (it >> 5));
-            if (d.x >= 0) {
-                const int te = it & 31;
-                const float* src = a.FRin + PM[d.x * TE + te];
-                #pragma unroll
-                for (int q = 0; q < V; ++q) cp_async4(FS + (d.z * V + q) * TE + te, src + q);
-            }
+    for (int it = threadIdx.x; it < Grp::NP * TE; it += NT) {
+        const int4 d = K::desc(Grp::OFF + (it >> 5));
+        if (d.x >= 0) {
+            const int te = it & 31;
+            const float* src = a.FRin + PM[d.x * TE + te];
+            #pragma unroll
+            for (int q = 0; q < V; ++q) cp_async4(FS + (d.z * V + q) * TE + te, src + q);
         }
     }
     Grp::interp(h, US + v * TE + lane, LDX, XS + v * TE + lane, LDX);
-    if constexpr (!K::PBALL) cp_async_wait_all();
+    cp_async_wait_all();
     __syncthreads();
     for (int it = threadIdx.x; it < Grp::NP * TE; it += NT) {
         const int r = it >> 5;                          // point row (warp-uniform)
@@ -162,7 +154,7 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
             const float s = MS[(mrow + ND) * TE + te];
             float nb[V], uL[V], uR[V], F[V];
             #pragma unroll
-            for (int q = 0; q < V; ++q) nb[q] = K::PBALL ? PB[(d.x * V + q) * TE + te] : FS[(d.z * V + q) * TE + te];
+            for (int q = 0; q < V; ++q) nb[q] = FS[(d.z * V + q) * TE + te];
             orient<V>(s > 0.f, u, nb, uL, uR);          // this point on its face's L side when s > 0
             if constexpr (SYS == SYS_EULER && RIE == RIE_RUSANOV) {
                 rusanov_rec<float, ND>(uL, uR, n, a.P.gamma, s, F);   // s F, one reciprocal per state
@@ -221,52 +213,23 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
     const int v = w % V, h = w / V;                      // thread (lane, v, h): rows of part h of column (e, v)
     const KEpi<float>& E = a.E;
     const float* Ub = a.U + a.u_off;
-    int* PMc = reinterpret_cast<int*>(smem + SM::PM);   // this tile's partner map
-    int* PMn = reinterpret_cast<int*>(smem + SM::PM2);  // the next tile's (PBALL)
-    if constexpr (K::PBALL) {
-        if (blockIdx.x * TE < a.nelem) {
-            stage_rows<NT>(PMc, a.pmap, K::NFE, a.ld, blockIdx.x * TE, a.nelem);
-            cp_async_wait_all();
-        }
-    }
     for (int tile = blockIdx.x; tile * TE < a.nelem; tile += gridDim.x) {
         const int e0 = tile * TE;
         const bool valid = e0 + lane < a.nelem;
         const int e = valid ? e0 + lane : a.nelem - 1;  // lanes past the end repeat the last element
-        const int en = (tile + gridDim.x) * TE;         // the next tile of this CTA
         __syncthreads();                                // previous tile's shared memory free
-        // The tile's state, metric rows and partner map (or, PBALL, the
-        // partners' states of every external point and the next tile's
-        // partner map), copied asynchronously; the next tile's rows
-        // prefetched into L2 meanwhile.
+        // The tile's state, metric rows and partner map, copied asynchronously;
+        // the next tile's rows prefetched into L2 meanwhile.
         stage_rows<NT>(smem + SM::US, Ub, NS * V, a.ld, e0, a.nelem);
         stage_rows<NT>(smem + SM::MS, a.metric, SM::NM, a.ld, e0, a.nelem);
-        if constexpr (K::PBALL) {
-            for (int i = threadIdx.x; i < K::NFE * TE; i += NT) {
-                const float* src = a.FRin + PMc[i];
-                const int sg = i >> 5, te = i & 31;
-                #pragma unroll
-                for (int q = 0; q < V; ++q) cp_async4(smem + SM::PB + (sg * V + q) * TE + te, src + q);
-            }
-            if (en < a.nelem) stage_rows<NT>(PMn, a.pmap, K::NFE, a.ld, en, a.nelem);
-        } else {
-            stage_rows<NT>(PMc, a.pmap, K::NFE, a.ld, e0, a.nelem);
-        }
+        stage_rows<NT>(reinterpret_cast<int*>(smem + SM::PM), a.pmap, K::NFE, a.ld, e0, a.nelem);
+        const int en = (tile + gridDim.x) * TE;
         if (en < a.nelem) {
             prefetch_rows<NT>(Ub, NS * V, a.ld, en);
             prefetch_rows<NT>(a.metric, SM::NM, a.ld, en);
-            if constexpr (!K::PBALL) prefetch_rows<NT>(a.pmap, K::NFE, a.ld, en);
+            prefetch_rows<NT>(a.pmap, K::NFE, a.ld, en);
         }
         cp_async_wait_all();
-        if constexpr (K::PBALL) {
-            // the next tile's partners into L2 (its map has just arrived)
-            __syncthreads();
-            if (en < a.nelem)
-                for (int i = threadIdx.x; i < K::NFE * TE; i += NT) prefetch_l2(a.FRin + PMn[i]);
-            int* t = PMc;
-            PMc = PMn;
-            PMn = t;
-        }
         float acc[NSH];
         #pragma unroll
         for (int r = 0; r < NSH; ++r) acc[r] = 0.f;
