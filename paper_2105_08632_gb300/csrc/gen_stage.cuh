@@ -74,13 +74,25 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// 16-byte asynchronous copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
 // The tile's rows of a [rows][ld] array (element fastest) into shared memory,
-// [rows][TE], with asynchronous copies (lanes past the end repeat the last
-// element).
+// [rows][TE], with asynchronous copies.  A full tile of an array whose start
+// is 16-byte aligned moves each row as eight 16-byte copies (ld and the block
+// offsets are multiples of 32 elements); otherwise, and on the last, partial
+// tile, value by value, the lanes past the end repeating the last element.
 template <int NT, typename E>
 __device__ __forceinline__ void stage_rows(E* dst, const E* src, int rows, int ld, int e0, int nelem) {
-    for (int i = threadIdx.x; i < rows * TE; i += NT)
-        cp_async4(dst + i, src + (size_t)(i >> 5) * ld + min(e0 + (i & 31), nelem - 1));
+    if (e0 + TE <= nelem && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        for (int i = threadIdx.x; i < rows * (TE / 4); i += NT)
+            cp_async16(dst + 4 * i, src + (size_t)(i >> 3) * ld + e0 + 4 * (i & 7));
+    } else {
+        for (int i = threadIdx.x; i < rows * TE; i += NT)
+            cp_async4(dst + i, src + (size_t)(i >> 5) * ld + min(e0 + (i & 31), nelem - 1));
+    }
 }
 // L2 prefetch of the same rows for a later tile (one 128-byte line per row).
 template <int NT, typename E>
