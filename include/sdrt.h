@@ -323,10 +323,12 @@ int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* V_dev, v
  * layout; the adjoint of the discrete operator of Sec. 2.1 / App. B, which the
  * paper does not spell out: W is carried back through the divergence
  * [M14 | M13]^T, the transposed Jacobians of the common and internal fluxes,
- * and the interpolation [M0; M12]^T).  Same branch convention at ties as
- * sdrt_jvp, so <W, J V> = <J^T W, V> up to rounding.  Inviscid systems only
- * (SDRT_ERR_UNSUPPORTED for advection-diffusion / Navier-Stokes).  Uses the
- * mesh's face-state buffers (allocated on first use). */
+ * and the interpolation [M0; M12]^T).  Viscous systems (advection-diffusion,
+ * Navier-Stokes: LDG, Sec. 2.1) also carry W back through the flux-point
+ * gradients: [M0; M12]^T at the solution points, J^{-1}, [M16 | M15 P M12]^T,
+ * and the common value C(u_L, u_R) of the two sides of each face.  Same branch
+ * convention at ties as sdrt_jvp, so <W, J V> = <J^T W, V> up to rounding.
+ * Uses the mesh's face-state and gradient buffers (allocated on first use). */
 int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* W_dev, void* JTW_dev);
 
 /* Tile autotuner of the generic kernels (every element type other than the

@@ -57,8 +57,8 @@ cudaError_t upload(DevBuf& b, const std::vector<T>& h) {
 struct EType {
     sdrt_etype_desc desc{};
     RefElement R;
-    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0, Mir = 0, Mdt_pad = 0;
-    DevBuf Ai[2], Ad[2], Air[2], Ag[2], Adt[2];  // [0] double, [1] float
+    int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0, Mir = 0, Mdt_pad = 0, Agr_pad = 0;
+    DevBuf Ai[2], Ad[2], Air[2], Ag[2], Adt[2], Agr[2];  // [0] double, [1] float
     DevBuf fe_face, fi_tab;
 };
 
@@ -96,6 +96,7 @@ struct Mesh {
     DevBuf ufe, dufe, ustage, uacc, uhost_dev, rec, drec, fiur, dfiur;
     DevBuf rec2, fiur2;          // second record buffers of the fused RK4 stages
     DevBuf qfe, dqfe, qfiu, dqfiu;    // viscous: flux-point gradients (kargs.hpp layout)
+    DevBuf cbar;                      // viscous VJP: adjoint of the common value (UFE layout)
     // Block tables of the generic kernels (one launch per kernel kind walks
     // every block): host copies and the device array, in the mesh precision.
     std::vector<KBlock<float>> kb_f;
@@ -310,6 +311,8 @@ KBlock<T> make_kblock(const EType& et, const MBlock& b) {
     K.Adt = et.Adt[pi].as<T>();
     K.Mdt_pad = et.Mdt_pad;
     K.Mg_pad = et.Mg_pad;
+    K.Agr = et.Agr[pi].as<T>();
+    K.Agr_pad = et.Agr_pad;
     K.qfiu_off = b.qfiu_off;
     K.fe_face = et.fe_face.as<int>();
     K.fi_tab = et.fi_tab.as<int>();
@@ -529,6 +532,27 @@ int run_vjp(sdrt_ctx* ctx, Mesh& m, const T* U, const T* W, T* out) {
     launch_interp_ext<T>(ks, m.nvar, U, ufe, m.Ftot, ctx->nsm, ctx->stream);
     prof_end(ctx, s);
     ++ctx->launches;
+    if (viscous(m)) {
+        // Forward gradients at the flux points, then the three adjoint passes.
+        s = prof_begin(ctx, KIND_GRAD);
+        int r = launch_grad<T>(ks, m.phys.system, m.nd, U, nullptr, ufe, nullptr, m.Ftot, P, m.qfe.as<T>(), nullptr,
+                               m.qfiu.as<T>(), nullptr, ctx->nsm, ctx->stream);
+        prof_end(ctx, s);
+        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
+        ++ctx->launches;
+        for (int pass = 0; pass < 3; ++pass) {
+            s = prof_begin(ctx, KIND_JVP);
+            r = launch_vjp_visc<T>(ks, pass, m.phys.system, m.phys.riemann, m.nd, U, W, ufe, m.qfe.as<T>(),
+                                   m.qfiu.as<T>(), gs, m.cbar.as<T>(), m.Ftot, P, out, ctx->flag.as<int>(), ctx->nsm,
+                                   ctx->stream);
+            prof_end(ctx, s);
+            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system / flux combination not supported by the VJP");
+            ++ctx->launches;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+        return SDRT_OK;
+    }
     for (int pass = 0; pass < 2; ++pass) {
         s = prof_begin(ctx, KIND_JVP);
         int r = launch_vjp<T>(ks, pass, m.phys.system, m.phys.riemann, m.nd, U, W, ufe, gs, m.Ftot, P, out,
@@ -1007,6 +1031,15 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
         }
     }
     std::vector<float> Agf(Ag.begin(), Ag.end());
+    // The same operator row-major with rows (rho, d), for its transpose in the
+    // viscous VJP: Agr[(rho ND + d)][k] = [M16 | M15 P M12][d nsol + rho][k].
+    et->Agr_pad = round_up(R.nfe + R.nsol, 8);
+    std::vector<double> Agr((size_t)R.nd * R.nsol * et->Agr_pad, 0.0);
+    for (int d = 0; d < R.nd; ++d)
+        for (int r = 0; r < R.nsol; ++r)
+            for (int k = 0; k < R.nfe + R.nsol; ++k)
+                Agr[((size_t)r * R.nd + d) * et->Agr_pad + k] = Ag[(size_t)k * et->Mg_pad + d * R.nsol + r];
+    std::vector<float> Agrf(Agr.begin(), Agr.end());
     // Row-major interpolation operator for the register-blocked kernels.
     et->Mir = round_up(et->Mi + 2, 4);   // zero rows past Mi: row pairs (j, j + 2) stay in bounds
     std::vector<double> Air((size_t)et->Mir * et->Md_pad, 0.0);
@@ -1036,6 +1069,8 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
         SDRT_CUDA(upload(et->Ag[1], Agf));
         SDRT_CUDA(upload(et->Adt[0], Adt));
         SDRT_CUDA(upload(et->Adt[1], Adtf));
+        SDRT_CUDA(upload(et->Agr[0], Agr));
+        SDRT_CUDA(upload(et->Agr[1], Agrf));
     }
     ctx->etypes.push_back(std::move(et));
     *etype_id = (int)ctx->etypes.size() - 1;
@@ -1412,7 +1447,11 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
             }
         }
         {
-            auto vsmem_of = [&](int TE) { return (R.nsol + R.nfiu + R.nfi + R.nfe) * m->nvar * TE * (f32 ? 4 : 8); };
+            const bool visc = phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES;
+            auto vsmem_of = [&](int TE) {
+                const int rows = R.nsol + R.nfiu + R.nfi + R.nfe + (visc ? nd * (R.nfe + R.nfiu + R.nsol) : 0);
+                return rows * m->nvar * TE * (f32 ? 4 : 8);
+            };
             int TE = 32;
             while (TE > 1 && vsmem_of(TE) > 100 * 1024) TE /= 2;
             mb.vtile = vsmem_of(TE) <= 220 * 1024 ? TE : 0;
@@ -1863,8 +1902,9 @@ int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW
     if (r) return r;
     if (!U || !W || !JTW || JTW == U || JTW == W) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
     Mesh& m = *ctx->meshes[mesh_id];
-    if (viscous(m)) return fail(ctx, SDRT_ERR_UNSUPPORTED, "VJP of the viscous systems is not implemented");
     if ((r = ensure_workspace(ctx, m, true, false))) return r;
+    if (viscous(m) && !m.cbar.p)
+        SDRT_CUDA(m.cbar.alloc((size_t)m.nvar * m.Ftot * (m.phys.precision == SDRT_FP32 ? 4 : 8)));
     if (m.phys.precision == SDRT_FP32)
         return run_vjp<float>(ctx, m, static_cast<const float*>(U), static_cast<const float*>(W),
                               static_cast<float*>(JTW));

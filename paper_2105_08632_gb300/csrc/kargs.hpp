@@ -32,6 +32,8 @@ struct KBlock {
     int Mdt_pad;
     const T* Ag;         // viscous: [M16 | M15 P M12] transposed: [nfe + nsol][Mg_pad], columns (d, rho)
     int Mg_pad;          // ND * nsol rounded up to 8
+    const T* Agr;        // viscous VJP: [M16 | M15 P M12] row-major with rows (rho, d): [ND * nsol][Agr_pad]
+    int Agr_pad;         // nfe + nsol rounded up to 8
     int64_t qfiu_off;    // viscous: element offset of the block in QFIU
     const int* fe_face;  // [nfe] local face of each external point
     const int* fi_tab;   // [nfiu][4]: count, then (nu | axis << 16) per internal DOF of the point

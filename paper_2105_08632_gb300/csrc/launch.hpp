@@ -71,6 +71,19 @@ int launch_vjp(const KSet<T>& ks, int pass, int system, int riemann, int nd, con
 template <typename T>
 int vjp_smem(const KBlock<T>& B, int V, int TE);
 
+// Vector-Jacobian product of the viscous residual (advection-diffusion,
+// Navier-Stokes; kernels_vjp.cu), every block in one launch per pass, after
+// the forward interpolation (UFE) and gradients (QFE, QFIU): pass 0 GS = s G;
+// pass 1 out = W^T J without the common value's term and CB = its adjoint at
+// the external points (UFE layout); pass 2 out += that term.  Returns -1 for
+// an unsupported combination, -2 without tile widths.
+template <typename T>
+int launch_vjp_visc(const KSet<T>& ks, int pass, int system, int riemann, int nd, const T* U, const T* W,
+                    const T* UFE, const T* QFE, const T* QFIU, T* GS, T* CB, int64_t Ftot, const KPhys<T>& P, T* out,
+                    int* flag, int nsm, cudaStream_t st);
+template <typename T>
+int vjp_visc_smem(const KBlock<T>& B, int V, int nd, int TE);
+
 // Dynamic shared memory of the gradient kernel for tile width TE.
 template <typename T>
 int grad_smem(const KBlock<T>& B, int V, int nd, int TE, bool dual);

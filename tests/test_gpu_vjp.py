@@ -1,4 +1,5 @@
-"""Vector-Jacobian product of the inviscid residual on the CUDA path.
+"""Vector-Jacobian product of the residual on the CUDA path (inviscid and
+viscous: LDG advection-diffusion and Navier-Stokes).
 
 1. Against the oracle's W^T J built from its dense Jacobian (complex-step
    columns) on small periodic meshes.
@@ -126,13 +127,65 @@ def test_adjoint_identity_mixed_mesh(ctx):
     assert abs(lhs - rhs) <= 1e-11 * np.sqrt(_dot(W, W) * _dot(JV, JV)), (lhs, rhs)
 
 
-def test_vjp_viscous_rejected(ctx):
-    from paper_2105_08632_gb300 import sdrt
-    M, geom, oph, _ = gu.build_pair(ctx, "tet", (2, 2, 2), 2, "ns", "rusanov", "fp64", mu=0.01)
-    U = torch.ones(M.state_len, dtype=torch.float64, device="cuda")
-    with pytest.raises(sdrt.SdrtError) as ei:
-        M.vjp(U, U.clone(), torch.zeros_like(U))
-    assert ei.value.code == -2
+# Viscous systems with non-symmetric LDG weights (beta != 0) and a penalty, so
+# that the face orientation and every term of the common value / flux enter.
+VISC = [("hex", (2, 2, 2), 1, "ns", "rusanov"), ("quad", (3, 3), 2, "ns", "roe"),
+        ("tet", (2, 2, 1), 1, "ns", "rusanov"), ("tet", (2, 2, 2), 2, "advdiff", "upwind"),
+        ("tri", (4, 4), 3, "advdiff", "upwind")]
+VISC_KW = {"mu": 0.03, "beta": 0.3, "eta": 0.1, "prandtl": 0.71}
+
+
+@pytest.mark.parametrize("kind,n,p,system,riemann", VISC)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_viscous_vjp_matches_oracle_dense_jacobian(ctx, kind, n, p, system, riemann, precision):
+    a = (0.8, -0.4, 0.3) if system == "advdiff" else (1.0, 0.5, 0.25)
+    M, geom, oph, _ = gu.build_pair(ctx, kind, n, p, system, riemann, precision, a=a, **VISC_KW)
+    if system == "ns":
+        U = gu.perturb(gu.oracle_state(geom, _shifted_gas, oph.nvar), 41, 0.02)
+    else:
+        U = _state(geom, oph, 41)
+    rng = np.random.default_rng(42)
+    W = [rng.normal(size=u.shape) for u in U]
+    want = ores.vjp(geom, oph, U, W)
+    linf, l2 = gu.rel_errors(_vjp(M, U, W), want)
+    if precision == "fp64":
+        assert linf < TOL64, linf
+    else:
+        assert linf < TOL32[0] and l2 < TOL32[1], (linf, l2)
+
+
+@pytest.mark.parametrize("kind,n,p,system", [("tet", (4, 3, 3), 3, "ns"), ("pri", (3, 3, 3), 2, "ns"),
+                                             ("hex", (4, 3, 2), 2, "advdiff"), ("tet", (3, 3, 2), 4, "ns")])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_viscous_adjoint_identity(ctx, kind, n, p, system, precision):
+    riem = "upwind" if system == "advdiff" else "rusanov"
+    M, geom, oph, _ = gu.build_pair(ctx, kind, n, p, system, riem, precision, **VISC_KW)
+    if system == "ns":
+        U = gu.perturb(gu.oracle_state(geom, _shifted_gas, oph.nvar), 43, 0.02)
+    else:
+        U = _state(geom, oph, 43)
+    rng = np.random.default_rng(44)
+    V = [rng.normal(size=u.shape) for u in U]
+    W = [rng.normal(size=u.shape) for u in U]
+    JV = _jvp(M, U, V)
+    JTW = _vjp(M, U, W)
+    lhs, rhs = _dot(W, JV), _dot(JTW, V)
+    scale = np.sqrt(_dot(W, W) * _dot(JV, JV))
+    tol = 1e-11 if precision == "fp64" else 1e-4
+    assert abs(lhs - rhs) <= tol * scale, (lhs, rhs, scale)
+
+
+def test_autograd_backward_navier_stokes(ctx):
+    from paper_2105_08632_gb300 import autograd
+    M, geom, oph, _ = gu.build_pair(ctx, "tet", (2, 2, 2), 2, "ns", "rusanov", "fp64", **VISC_KW)
+    U = _dev(M, gu.perturb(gu.oracle_state(geom, _shifted_gas, 5), 45, 0.02))
+    rng = np.random.default_rng(46)
+    W = _dev(M, [rng.normal(size=(g.ops.n_sol, 5, g.nelem)) for g in geom.blocks])
+    Ug = U.clone().requires_grad_(True)
+    (g,) = torch.autograd.grad((autograd.residual(Ug, M) * W).sum(), Ug)
+    g_ref = torch.zeros_like(U)
+    M.vjp(U, W, g_ref)
+    assert torch.equal(g, g_ref)
 
 
 def test_autograd_function_matches_the_c_abi(ctx):
