@@ -66,6 +66,9 @@ def test_first_noalloc_call_allocates_nothing():
     from paper_2105_08632_gb300 import sdrt
     c = sdrt.Context(0)
     try:
+        # the generic kernels for sdrt_residual too (the operator-specialised
+        # ones would otherwise take this mesh), so that their code is loaded
+        sdrt.sdrt_set_option(c.ptr, sdrt.SDRT_OPT_GENERATED, 0)
         M, geom, oph, _ = gu.build_pair(c, "hex", (3, 3, 2), 2, "euler", "rusanov", "fp32")
         U = torch.from_numpy(M.pack(_states(geom, (31,))[0])).to("cuda")
         ref, out = torch.zeros_like(U), torch.zeros_like(U)
