@@ -14,7 +14,8 @@
  *  - Device calls are asynchronous and ordered on the context's CUDA stream.
  *    Argument / state errors are reported immediately; kernel launch errors
  *    are returned by the call that launched; the non-finite flag raised by a
- *    kernel is reported by sdrt_sync().
+ *    kernel, and the timeout flag of a bounded device wait, are reported by
+ *    sdrt_sync().
  *  - Pointers named *_dev are device pointers owned by the caller; *_host are
  *    host pointers owned by the caller.  The library never frees caller memory.
  *  - State layout: the state of a mesh is one array holding its blocks one
@@ -347,8 +348,10 @@ int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U_dev, int reps);
  * VJP}; 0 = not available for this block. */
 int sdrt_get_tiles(sdrt_ctx* ctx, int mesh_id, int block, int32_t* out);
 
-/* Synchronise the context's stream; returns SDRT_ERR_NONFINITE (and clears the
- * flag) if a kernel wrote NaN / Inf into a residual since the last sync. */
+/* Synchronise the context's stream; returns SDRT_ERR_TIMEOUT if a kernel's
+ * bounded wait for its asynchronous copies ran out, else SDRT_ERR_NONFINITE if
+ * a kernel wrote NaN / Inf into a residual, since the last sync (and clears
+ * the flags). */
 int sdrt_sync(sdrt_ctx* ctx);
 
 /* Number of kernel launches issued by the context since creation (for
@@ -383,6 +386,14 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     operator-specialised kernels also where the record path would run.
  *     Results agree to FP32 rounding. */
 #define SDRT_OPT_GENERATED 3
+/*   SDRT_OPT_WAIT_POLLS (default 0): > 0 = the record-path flux kernel (FP32 /
+ *     FP64 tetrahedra of degree 3 / 4) checks its first wait for its copies
+ *     that many times without blocking; when that runs out it records a
+ *     timeout, which sdrt_sync reports as SDRT_ERR_TIMEOUT, and then waits for
+ *     its copies with the normal bound, so its results stay correct.  A test
+ *     hook for the timeout path; 0 = the normal bound (about 2^26 polls).
+ *     Changing it drops captured RK4 graphs. */
+#define SDRT_OPT_WAIT_POLLS 4
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 
 /* Per-launch device timing with CUDA events recorded on the context's stream

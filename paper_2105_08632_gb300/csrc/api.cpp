@@ -153,6 +153,7 @@ struct sdrt_ctx {
     bool use_tc_div = false;      // tensor-core divergence where instantiated (SDRT_OPT_TC_DIVERGENCE)
     bool fuse_rk = true;          // next-stage interpolation in the RK4 stage update (SDRT_OPT_FUSED_RK)
     int use_gen = 1;              // operator-specialised kernels where generated (SDRT_OPT_GENERATED)
+    int wait_polls = 0;           // first copy wait of the record flux kernel (SDRT_OPT_WAIT_POLLS)
     void* noalloc_scratch = nullptr;   // device address of sdrt_residual_noalloc's static buffer
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
@@ -462,6 +463,8 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
                 ++ctx->launches;
             }
         }
+        KEpi<T> Ew = E;
+        Ew.wait_polls = ctx->wait_polls;
         for (auto& bp : m.blocks) {
             const EType& et = *ctx->etypes[bp->etype];
             KBlock<T> K = make_kblock<T>(et, *bp);
@@ -472,7 +475,7 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
                     r = launch_flux_tc(K, rec, fiur, P, E, ctx->nsm, ctx->stream);
             }
             if (r != 0)
-                launch_flux_rec<T>(K, sys, rec, dU ? drec : nullptr, fiur, dU ? dfiur : nullptr, P, E, ctx->nsm,
+                launch_flux_rec<T>(K, sys, rec, dU ? drec : nullptr, fiur, dU ? dfiur : nullptr, P, Ew, ctx->nsm,
                                    ctx->stream);
             prof_end(ctx, s);
             ++ctx->launches;
@@ -595,6 +598,7 @@ int rk4_stages_fused(sdrt_ctx* ctx, Mesh& m, float* U, double dt) {
     }
     KEpi<float> E{};
     E.flag = ctx->flag.as<int>();
+    E.wait_polls = ctx->wait_polls;
     E.u0 = U;
     E.uacc = m.uacc.as<float>();
     E.unext = m.ustage.as<float>();
@@ -1807,6 +1811,7 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     else if (option == SDRT_OPT_TC_DIVERGENCE) ctx->use_tc_div = value != 0;
     else if (option == SDRT_OPT_FUSED_RK) ctx->fuse_rk = value != 0;
     else if (option == SDRT_OPT_GENERATED) ctx->use_gen = value < 0 ? 0 : value > 2 ? 2 : value;
+    else if (option == SDRT_OPT_WAIT_POLLS) ctx->wait_polls = value < 0 ? 0 : value;
     else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {
@@ -2008,6 +2013,7 @@ int sdrt_sync(sdrt_ctx* ctx) {
     SDRT_CUDA(cudaMemcpy(&h, ctx->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
         SDRT_CUDA(cudaMemset(ctx->flag.p, 0, sizeof(int)));
+        if (h & 2) return fail(ctx, SDRT_ERR_TIMEOUT, "a kernel's bounded wait for its copies ran out");
         return fail(ctx, SDRT_ERR_NONFINITE, "a kernel produced a non-finite value");
     }
     return SDRT_OK;

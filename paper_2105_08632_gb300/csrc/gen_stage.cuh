@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
                 if (valid) E.out[base + r * rs] = acc[r];
             }
         }
-        if (bad && valid) *E.flag = 1;
+        if (bad && valid) atomicOr(E.flag, 1);
         if (a.FRout) {
             // the new state into US (every group has read it), then its face records
             __syncthreads();

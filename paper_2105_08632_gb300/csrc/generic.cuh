@@ -340,7 +340,7 @@ __device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const T* acc, T 
             default: E.out[idx] = fma(E.cacc, r, b[i]); break;
         }
     }
-    if (bad) *E.flag = 1;
+    if (bad) atomicOr(E.flag, 1);
 }
 template <typename T>
 __device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const Dual<T>* acc, T inv, size_t base,
@@ -353,7 +353,7 @@ __device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const Dual<T>* a
         bad |= !isfinite(d);
         E.out[base + (size_t)(m0 + i) * rstride] = d;
     }
-    if (bad) *E.flag = 1;
+    if (bad) atomicOr(E.flag, 1);
 }
 
 template <typename S, typename T, int V>

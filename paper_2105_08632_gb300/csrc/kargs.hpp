@@ -121,7 +121,8 @@ struct KEpi {
     T* uacc;
     T* unext;
     T cacc, cnext;
-    int* flag;           // set to 1 when a non-finite value is produced
+    int* flag;           // bit 0: a non-finite value was produced; bit 1: a bounded wait ran out
+    int wait_polls;      // record flux kernel: polls of its first copy wait (0: the normal bound)
     // Non-null (record path, stages 1-3 of RK4): the next stage's state
     // u0 + cnext R is not stored but interpolated right away into these record
     // buffers (the layouts of REC and FIUR).

@@ -74,6 +74,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     }
     return false;
 }
+// At most n non-blocking tests of the phase with the given parity; false if
+// it has not completed by then.
+__device__ __forceinline__ bool mbar_test_n(uint64_t* bar, uint32_t parity, int n) {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < n; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 // Global -> shared bulk copy completing on bar (16-byte aligned, size multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -155,7 +172,7 @@ __device__ __forceinline__ void internal_flux_f(const S* u, const T* Srow, const
 
 template <typename T>
 __device__ __forceinline__ void epi_store(const KEpi<T>& E, size_t idx, T r) {
-    if (!isfinite(r)) *E.flag = 1;
+    if (!isfinite(r)) atomicOr(E.flag, 1);
     switch (E.mode) {
         case EPI_STORE: E.out[idx] = r; break;
         case EPI_RK_FIRST: {
@@ -214,7 +231,7 @@ __device__ __forceinline__ void epi_block(const KEpi<T>& E, const T (&acc)[RS][V
             }
         }
     }
-    if (bad) *E.flag = 1;
+    if (bad) atomicOr(E.flag, 1);
 }
 
 // Stage update of stages 1-3 with the next stage's state kept on chip: uacc
@@ -247,7 +264,7 @@ __device__ __forceinline__ void epi_block_next(const KEpi<T>& E, const T (&acc)[
             ut[(r0 + i) * 8 + v] = fma(E.cnext, r, a[i][v]);
         }
     }
-    if (bad) *E.flag = 1;
+    if (bad) atomicOr(E.flag, 1);
 }
 
 // Rows j = h + G i (i < NRT) of [M0; M12] u for one element whose state tile
@@ -548,7 +565,7 @@ __global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, TE <= 32 ? 2 : 
             int k = 0;
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
                 const int s = k & 1;
-                if (k >= 2 && !mbar_wait(&bar[2 + s], ((k >> 1) - 1) & 1)) *err = 2;
+                if (k >= 2 && !mbar_wait(&bar[2 + s], ((k >> 1) - 1) & 1)) atomicOr(err, 2);
                 mbar_arrive_expect_tx(&bar[s], (uint32_t)(NROW * TE * sizeof(float)));
                 fence_proxy_async();
                 tma_load_2d(Ub + (size_t)s * NROW * TE, &umap, t * TE, 0, &bar[s]);
@@ -574,7 +591,7 @@ __global__ void __launch_bounds__((ALLV ? 1 : V) * TE * GR + 32, TE <= 32 ? 2 : 
         const int s = k & 1;
         const int e0 = t * TE;
         const int n = min(TE, B.nelem - e0);
-        if (!mbar_wait(&bar[s], (k >> 1) & 1)) *err = 2;
+        if (!mbar_wait(&bar[s], (k >> 1) & 1)) atomicOr(err, 2);
         constexpr int UV = ALLV ? V : 1;          // variables held by a thread
         float u[UV][NS];
         const float* us = Ub + (size_t)s * NROW * TE + (size_t)v * TE + el;
@@ -759,8 +776,12 @@ __global__ void __launch_bounds__(32 * NW, FUSE ? 3 : 1) k_flux_rec(KBlock<T> B,
             fence_proxy_async();
             bulk_g2s(part + (size_t)le * B.ers + f * B.frec, REC + src, (uint32_t)(B.frec * sizeof(T)), bar);
         }
-        if (!mbar_wait(bar, parity)) {
-            *E.flag = 2;
+        // The copies' wait, bounded (E.wait_polls > 0: that many non-blocking
+        // polls); when it runs out the timeout bit is set and the kernel waits
+        // again, with the normal bound, for its own copies in flight before it
+        // reads the buffers.
+        if (!(E.wait_polls > 0 ? mbar_test_n(bar, parity, E.wait_polls) : mbar_wait(bar, parity))) {
+            atomicOr(E.flag, 2);
             mbar_wait(bar, parity);
         }
 
@@ -1017,7 +1038,7 @@ __global__ void __launch_bounds__(32 * V, 4) k_flux_rec_dual(KBlock<T> B, const 
                 #pragma unroll
                 for (int r = 0; r < NS; ++r) {
                     const T d = acc[r].d * inv;
-                    if (!isfinite(d)) *E.flag = 1;
+                    if (!isfinite(d)) atomicOr(E.flag, 1);
                     E.out[(size_t)B.u_off + (size_t)(r * V + v) * B.ld + e] = d;
                 }
             }

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128, 1) k_interp_tc(KBlock<float> B, const flo
         for (int v = 0; v < V; ++v) {
             const int b = v & 1;
             if (v >= 2) {                            // buffer b was read by the MMAs of variable v - 2
-                if (!mbar_wait(&bar[b], ph[b])) *err = 2;
+                if (!mbar_wait(&bar[b], ph[b])) atomicOr(err, 2);
                 ph[b] ^= 1u;
             }
             unsigned char* ah = Ah + b * A_BYTES;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(128, 1) k_interp_tc(KBlock<float> B, const flo
         // bulk store to have read the staging buffers.
         #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            if (!mbar_wait(&bar[b], ph[b])) *err = 2;
+            if (!mbar_wait(&bar[b], ph[b])) atomicOr(err, 2);
             ph[b] ^= 1u;
         }
         if (tid == 0) bulk_wait_read0();
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_tc(KBlock<float> B, const float
             b[i] = (epi && need_acc) ? E.uacc[idx] : 0.f;
         }
         if (!mbar_wait(&bar[0], ph_ld)) {
-            *err = 2;
+            atomicOr(err, 2);
             mbar_wait(&bar[0], ph_ld);
         }
         ph_ld ^= 1u;
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_tc(KBlock<float> B, const float
         }
         const float inv = epi ? -met[(size_t)ee * B.nmp] : 0.f;   // -1 / det J of the epilogue's element
         if (!mbar_wait(&bar[1], ph_mma)) {       // phase 1 MMAs have read A
-            *err = 2;
+            atomicOr(err, 2);
             mbar_wait(&bar[1], ph_mma);
         }
         ph_mma ^= 1u;
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_tc(KBlock<float> B, const float
         // the MMAs and the epilogue.
         if (tile + (int)gridDim.x < ntiles) issue_loads(tile + gridDim.x);
         if (!mbar_wait(&bar[1], ph_mma)) {
-            *err = 2;
+            atomicOr(err, 2);
             mbar_wait(&bar[1], ph_mma);
         }
         ph_mma ^= 1u;
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_tc(KBlock<float> B, const float
                         default: E.out[idx] = fmaf(E.cacc, r, b[i]); break;
                     }
                 }
-                if (bad) *err = 1;
+                if (bad) atomicOr(err, 1);
             }
         }
         tc_fence_before();       // this thread's TMEM loads precede the next tile's MMAs

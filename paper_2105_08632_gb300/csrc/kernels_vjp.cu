@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem(KTable<T> tab, const T* __rest
                                 bad |= !isfinite(acc[i]);
                                 out[(size_t)B.u_off + ((size_t)m * V + v) * B.ld + e] = acc[i];
                             }
-                            if (bad) *flag = 1;
+                            if (bad) atomicOr(flag, 1);
                         });
     }
 }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256) k_vjp_cbar(KTable<T> tab, const T* __rest
                                 o = o + acc[i];
                                 bad |= !isfinite(o);
                             }
-                            if (bad) *flag = 1;
+                            if (bad) atomicOr(flag, 1);
                         });
     }
 }

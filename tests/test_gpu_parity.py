@@ -204,3 +204,30 @@ def test_face_map_matches_oracle_on_device_context(ctx):
     part, left = M.face_map()
     assert np.array_equal(part.astype(np.int64), geom.partner)
     assert np.array_equal(left.astype(bool), geom.is_left)
+
+
+def test_wait_timeout_reported_and_results_intact(ctx):
+    """A bounded device wait that runs out is reported as SDRT_ERR_TIMEOUT by
+    sdrt_sync (SDRT_OPT_WAIT_POLLS makes the record flux kernel's first copy
+    wait a single non-blocking check); the kernel then waits for its own
+    copies with the normal bound, so the residual is still the right one, and
+    with the option reset the next call reports nothing."""
+    from paper_2105_08632_gb300 import sdrt
+    M, geom, oph, _ = gu.build_pair(ctx, "tet", (3, 3, 2), 3, "euler", "rusanov", "fp32")
+    assert sdrt.PATHS[sdrt.sdrt_get_mesh_info(ctx.ptr, M.id)["path"]] == "record"
+    U = gu.perturb(gu.oracle_state(geom, gu.smooth_gas, 5), 19, 0.02)
+    Ud = torch.from_numpy(M.pack(U)).to("cuda")
+    R1, R2 = torch.zeros_like(Ud), torch.zeros_like(Ud)
+    sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_WAIT_POLLS, 1)
+    try:
+        M.residual(Ud, R1)
+        with pytest.raises(sdrt.SdrtError) as ei:
+            M.sync()
+        assert ei.value.code == -6
+    finally:
+        sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_WAIT_POLLS, 0)
+    M.residual(Ud, R2)
+    M.sync()
+    assert torch.equal(R1, R2)
+    linf, l2 = gu.rel_errors(M.unpack(R2.cpu().numpy()), ores.residual(geom, oph, U))
+    assert linf < TOL32[0] and l2 < TOL32[1], (linf, l2)
