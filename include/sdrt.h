@@ -308,6 +308,36 @@ int sdrt_residual_noalloc(sdrt_ctx* ctx, int mesh_id, const void* U_dev, void* R
  * kernels and the stage states stay on chip. */
 int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U_dev, double dt, int nsteps);
 
+/* nsteps RK54 steps of size dt, in place on U_dev (device): the five-stage
+ * fourth-order two-register scheme of Carpenter & Kennedy (1994) that the
+ * paper cites for its Taylor-Green runs (Sec. 5.3; its stability polynomial
+ * is Eq. "rk_exponential"), published coefficients.  Each stage is one
+ * residual evaluation and an update of the two registers
+ * dU <- A_i dU + dt R(U), U <- U + B_i dU.  Uses mesh workspaces (allocated
+ * on first use). */
+int sdrt_rk54_step(sdrt_ctx* ctx, int mesh_id, void* U_dev, double dt, int nsteps);
+
+/* One adaptive RK54 step attempt of size dt with the embedded third-order
+ * estimate (U - U^ = sum_j n_j k_j over the stage slopes, n the unit null
+ * vector of the order <= 3 conditions) and a PI step-size controller (the
+ * paper pairs RK54 with one, Sec. 5.3, citing Butcher; it prints neither the
+ * estimator nor the gains):
+ *   err = max |U - U^| / (atol + rtol max(|U_start|, |U|))   (L-infinity, as
+ *         in the paper's runs);
+ *   accepted (err <= 1): U holds the new state, dt_next = dt * clip(0.9
+ *         err^(-0.7/4) err_prev^(0.4/4), 0.2, 5), err_prev <- err (kept per mesh,
+ *         initially 1);
+ *   rejected: U is restored, dt_next = dt * clip(0.9 err^(-0.7/4), 0.2, 5).
+ * Synchronises the stream (the error norm is read on the host). */
+int sdrt_rk54_adaptive_step(sdrt_ctx* ctx, int mesh_id, void* U_dev, double dt, double atol, double rtol,
+                            double* err, double* dt_next, int* accepted);
+
+/* Adaptive RK54 over a time span t_span from the step size *dt_inout (the
+ * last step is shortened to end exactly at t_span); *dt_inout returns the
+ * controller's next step size.  SDRT_ERR_STATE after max_steps attempts. */
+int sdrt_rk54_integrate(sdrt_ctx* ctx, int mesh_id, void* U_dev, double t_span, double* dt_inout, double atol,
+                        double rtol, int max_steps, int* n_accepted, int* n_rejected);
+
 /* Same as sdrt_rk4_step with host buffers: copies U_in_host to the device,
  * steps, copies the result to U_out_host and synchronises the stream.
  * U_in_host / U_out_host: state_len values (may be the same buffer; pinned

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -97,6 +99,8 @@ struct Mesh {
     DevBuf rec2, fiur2;          // second record buffers of the fused RK4 stages
     DevBuf qfe, dqfe, qfiu, dqfiu;    // viscous: flux-point gradients (kargs.hpp layout)
     DevBuf cbar;                      // viscous VJP: adjoint of the common value (UFE layout)
+    DevBuf rk_r, rk_du, rk_err, rk_u0, rk_part;   // RK54: residual, second register, estimate, step start
+    double pi_err_prev = 1.0;         // RK54 PI controller: error norm of the last accepted step
     // Block tables of the generic kernels (one launch per kernel kind walks
     // every block): host copies and the device array, in the mesh precision.
     std::vector<KBlock<float>> kb_f;
@@ -686,6 +690,84 @@ int rk4_stages(sdrt_ctx* ctx, Mesh& m, T* U, double dt) {
     E.cacc = c6;
     E.out = U;
     return run_residual<T>(ctx, m, us, nullptr, E);
+}
+
+// ---------------------------------------------------------------------------
+// RK54: the five-stage fourth-order two-register scheme of Carpenter & Kennedy
+// (1994, NASA TM-109112), published rationals.  Its linear stability
+// polynomial is the one of the paper's Eq. "rk_exponential".
+const double kRK54A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                          -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRK54B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                          1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                          2277821191437.0 / 14882151754819.0};
+
+// The embedded estimate's weights n = b - b^: the unit null vector (last
+// component positive) of the four conditions of order <= 3 on the stages,
+// sum n = 0, n.c = 0, n.c^2 = 0, n.(a c) = 0, so U - U^ = sum_j n_j k_j with
+// U^ third order.  Computed from the Butcher form of the two-register scheme;
+// the null vector from the 4 x 4 minors (cofactor expansion).
+std::array<double, 5> rk54_estimate_weights() {
+    double a[5][5] = {}, D[5] = {}, W[5] = {};
+    for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) a[i][j] = W[j];
+        for (int j = 0; j < 5; ++j) D[j] = kRK54A[i] * D[j] + (j == i ? 1.0 : 0.0);
+        for (int j = 0; j < 5; ++j) W[j] += kRK54B[i] * D[j];
+    }
+    double c[5], ac[5];
+    for (int i = 0; i < 5; ++i) {
+        c[i] = 0;
+        for (int j = 0; j < 5; ++j) c[i] += a[i][j];
+    }
+    for (int i = 0; i < 5; ++i) {
+        ac[i] = 0;
+        for (int j = 0; j < 5; ++j) ac[i] += a[i][j] * c[j];
+    }
+    double M[4][5];
+    for (int j = 0; j < 5; ++j) {
+        M[0][j] = 1.0;
+        M[1][j] = c[j];
+        M[2][j] = c[j] * c[j];
+        M[3][j] = ac[j];
+    }
+    auto det4 = [](double m[4][4]) {
+        double d = 0;
+        for (int c0 = 0; c0 < 4; ++c0) {
+            double s[3][3];
+            for (int r = 1; r < 4; ++r)
+                for (int cc = 0, k = 0; cc < 4; ++cc)
+                    if (cc != c0) s[r - 1][k++] = m[r][cc];
+            const double d3 = s[0][0] * (s[1][1] * s[2][2] - s[1][2] * s[2][1]) -
+                              s[0][1] * (s[1][0] * s[2][2] - s[1][2] * s[2][0]) +
+                              s[0][2] * (s[1][0] * s[2][1] - s[1][1] * s[2][0]);
+            d += (c0 % 2 ? -1.0 : 1.0) * m[0][c0] * d3;
+        }
+        return d;
+    };
+    std::array<double, 5> n{};
+    double nn = 0;
+    for (int j = 0; j < 5; ++j) {
+        double m[4][4];
+        for (int r = 0; r < 4; ++r)
+            for (int cc = 0, k = 0; cc < 5; ++cc)
+                if (cc != j) m[r][k++] = M[r][cc];
+        n[j] = (j % 2 ? -1.0 : 1.0) * det4(m);
+        nn += n[j] * n[j];
+    }
+    const double sgn = n[4] < 0 ? -1.0 : 1.0;
+    for (double& x : n) x *= sgn / std::sqrt(nn);
+    return n;
+}
+
+// PI step-size factor (the reading stated with the oracle): accepted steps
+// 0.9 err^(-0.7/k) err_prev^(0.4/k), rejected ones 0.9 err^(-0.7/k), k = 4
+// (third-order estimate), clipped to [0.2, 5].
+double pi_factor(double err, double err_prev, bool accepted) {
+    const double k = 4.0;
+    err = std::max(err, 1e-16);
+    err_prev = std::max(err_prev, 1e-16);
+    double f = 0.9 * std::pow(err, -0.7 / k) * (accepted ? std::pow(err_prev, 0.4 / k) : 1.0);
+    return std::min(5.0, std::max(0.2, f));
 }
 
 int check_mesh(sdrt_ctx* ctx, int mesh_id) {
@@ -1802,6 +1884,132 @@ int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
     }
     // Events inside the graph hold the timings of its last replay.
     if (ctx->prof) ctx->pending.insert(ctx->pending.end(), m.graph_slots.begin(), m.graph_slots.end());
+    return SDRT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One RK54 step of U (device), five residuals and stage updates; with
+// estimate, the embedded estimate accumulates in m.rk_err.
+template <typename T>
+int rk54_stages(sdrt_ctx* ctx, Mesh& m, T* U, double dt, bool estimate) {
+    static const std::array<double, 5> ne = rk54_estimate_weights();
+    T* R = m.rk_r.as<T>();
+    for (int i = 0; i < 5; ++i) {
+        KEpi<T> E{};
+        E.mode = EPI_STORE;
+        E.out = R;
+        E.flag = ctx->flag.as<int>();
+        int r = run_residual<T>(ctx, m, U, nullptr, E);
+        if (r) return r;
+        launch_rk2n<T>(m.state_len, U, m.rk_du.as<T>(), R, estimate ? m.rk_err.as<T>() : nullptr, kRK54A[i],
+                       kRK54B[i], ne[i], dt, i == 0, ctx->nsm, ctx->stream);
+        ++ctx->launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+int rk54_workspace(sdrt_ctx* ctx, Mesh& m, bool adaptive) {
+    const size_t bytes = (size_t)m.state_len * (m.phys.precision == SDRT_FP32 ? 4 : 8);
+    if (!m.rk_r.p) SDRT_CUDA(m.rk_r.alloc(bytes));
+    if (!m.rk_du.p) SDRT_CUDA(m.rk_du.alloc(bytes));
+    if (adaptive) {
+        if (!m.rk_err.p) SDRT_CUDA(m.rk_err.alloc(bytes));
+        if (!m.rk_u0.p) SDRT_CUDA(m.rk_u0.alloc(bytes));
+        if (!m.rk_part.p) SDRT_CUDA(m.rk_part.alloc(256 * sizeof(double)));
+    }
+    return SDRT_OK;
+}
+
+// One attempted adaptive step: on acceptance U holds the new state, on
+// rejection the old one; *err = the L-infinity error norm.
+template <typename T>
+int rk54_attempt(sdrt_ctx* ctx, Mesh& m, T* U, double dt, double atol, double rtol, double* err) {
+    const size_t bytes = (size_t)m.state_len * sizeof(T);
+    SDRT_CUDA(cudaMemcpyAsync(m.rk_u0.p, U, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    int r = rk54_stages<T>(ctx, m, U, dt, true);
+    if (r) return r;
+    const int nparts = 256;
+    launch_err_linf<T>(m.state_len, m.rk_err.as<T>(), m.rk_u0.as<T>(), U, atol, rtol, m.rk_part.as<double>(), nparts,
+                       ctx->stream);
+    ++ctx->launches;
+    double part[256];
+    SDRT_CUDA(cudaMemcpyAsync(part, m.rk_part.p, nparts * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SDRT_CUDA(cudaStreamSynchronize(ctx->stream));
+    double e = 0;
+    for (int i = 0; i < nparts; ++i) e = (part[i] > e || part[i] != part[i]) ? part[i] : e;
+    *err = e;
+    if (!(e <= 1.0)) SDRT_CUDA(cudaMemcpyAsync(U, m.rk_u0.p, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    return SDRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdrt_rk54_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
+    int r = check_whole(ctx, mesh_id);
+    if (r) return r;
+    if (!U || nsteps < 0 || !(std::isfinite(dt))) return fail(ctx, SDRT_ERR_ARG, "bad argument");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if ((r = rk54_workspace(ctx, m, false))) return r;
+    for (int s = 0; s < nsteps; ++s) {
+        r = m.phys.precision == SDRT_FP32 ? rk54_stages<float>(ctx, m, static_cast<float*>(U), dt, false)
+                                           : rk54_stages<double>(ctx, m, static_cast<double*>(U), dt, false);
+        if (r) return r;
+    }
+    return SDRT_OK;
+}
+
+int sdrt_rk54_adaptive_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, double atol, double rtol, double* err,
+                            double* dt_next, int* accepted) {
+    int r = check_whole(ctx, mesh_id);
+    if (r) return r;
+    if (!U || !err || !dt_next || !accepted || !(dt > 0) || !(atol > 0) || !(rtol >= 0))
+        return fail(ctx, SDRT_ERR_ARG, "bad argument");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if ((r = rk54_workspace(ctx, m, true))) return r;
+    double e = 0;
+    r = m.phys.precision == SDRT_FP32 ? rk54_attempt<float>(ctx, m, static_cast<float*>(U), dt, atol, rtol, &e)
+                                       : rk54_attempt<double>(ctx, m, static_cast<double*>(U), dt, atol, rtol, &e);
+    if (r) return r;
+    *err = e;
+    if (!(e == e)) return fail(ctx, SDRT_ERR_NONFINITE, "non-finite RK54 error estimate");
+    *accepted = e <= 1.0;
+    *dt_next = dt * pi_factor(e, m.pi_err_prev, *accepted != 0);
+    if (*accepted) m.pi_err_prev = e;
+    return SDRT_OK;
+}
+
+int sdrt_rk54_integrate(sdrt_ctx* ctx, int mesh_id, void* U, double t_span, double* dt_inout, double atol,
+                        double rtol, int max_steps, int* n_accepted, int* n_rejected) {
+    if (!dt_inout || !n_accepted || !n_rejected || !(t_span >= 0) || max_steps < 1)
+        return fail(ctx, SDRT_ERR_ARG, "bad argument");
+    *n_accepted = *n_rejected = 0;
+    double t = 0, dt = *dt_inout;
+    while (t < t_span) {
+        if (*n_accepted + *n_rejected >= max_steps)
+            return fail(ctx, SDRT_ERR_STATE, "RK54 integration did not reach the end within max_steps");
+        const double h = std::min(dt, t_span - t);
+        double err = 0, dn = 0;
+        int acc = 0;
+        int r = sdrt_rk54_adaptive_step(ctx, mesh_id, U, h, atol, rtol, &err, &dn, &acc);
+        if (r) return r;
+        if (acc) {
+            t += h;
+            ++*n_accepted;
+        } else {
+            ++*n_rejected;
+        }
+        dt = dn;
+    }
+    *dt_inout = dt;
     return SDRT_OK;
 }
 

@@ -136,6 +136,16 @@ void launch_face_records(const T* src, T* dst, const int* off, int64_t n, int le
 template <typename T>
 void launch_gather_values(const T* src, T* dst, const int* idx, int64_t n, bool scatter, int nsm, cudaStream_t st);
 
+// RK54 stage update (kernels_rk.cu): dU = a dU + dt R (dU = dt R when
+// first), U += b dU, and with E non-null E = (first ? 0 : E) + ne dt R.
+template <typename T>
+void launch_rk2n(int64_t n, T* U, T* dU, const T* R, T* E, double a, double b, double ne, double dt, bool first,
+                 int nsm, cudaStream_t st);
+// Per-CTA maxima of |E| / (atol + rtol max(|U0|, |U|)) over n values, part[nparts].
+template <typename T>
+void launch_err_linf(int64_t n, const T* E, const T* U0, const T* U, double atol, double rtol, double* part, int nparts,
+                     cudaStream_t st);
+
 // Fluxes and divergence from the records (dREC / dFIUR non-null: JVP mode) with epilogue E.
 template <typename T>
 int launch_flux_rec(const KBlock<T>& B, int system, const T* REC, const T* dREC, const T* FIUR, const T* dFIUR,

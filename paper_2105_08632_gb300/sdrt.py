@@ -26,7 +26,8 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_get_block_layout", "sdrt_get_sol_points", "sdrt_get_face_map", "sdrt_residual",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
             "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option",
-            "sdrt_autotune", "sdrt_get_tiles", "sdrt_profile_collect_blocks"]
+            "sdrt_autotune", "sdrt_get_tiles", "sdrt_profile_collect_blocks", "sdrt_rk54_step",
+            "sdrt_rk54_adaptive_step", "sdrt_rk54_integrate"]
 
 
 class SdrtError(RuntimeError):
@@ -104,6 +105,9 @@ def lib():
         "sdrt_residual": (I, [P, I, P, P]),
         "sdrt_rk4_step": (I, [P, I, P, D, I]),
         "sdrt_rk4_step_host": (I, [P, I, P, P, D, I]),
+        "sdrt_rk54_step": (I, [P, I, P, D, I]),
+        "sdrt_rk54_adaptive_step": (I, [P, I, P, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
+        "sdrt_rk54_integrate": (I, [P, I, P, D, ctypes.POINTER(D), D, D, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sdrt_jvp": (I, [P, I, P, P, P]),
         "sdrt_vjp": (I, [P, I, P, P, P]),
         "sdrt_sync": (I, [P]),
@@ -294,6 +298,26 @@ def sdrt_residual_noalloc(ctx, mesh, U, R):
 
 def sdrt_rk4_step(ctx, mesh, U, dt, nsteps=1):
     _check(ctx, lib().sdrt_rk4_step(ctx, int(mesh), _ptr(U), float(dt), int(nsteps)))
+
+
+def sdrt_rk54_step(ctx, mesh, U, dt, nsteps=1):
+    _check(ctx, lib().sdrt_rk54_step(ctx, int(mesh), _ptr(U), float(dt), int(nsteps)))
+
+
+def sdrt_rk54_adaptive_step(ctx, mesh, U, dt, atol, rtol):
+    """(accepted, err, dt_next) of one adaptive RK54 step attempt."""
+    err, dtn, acc = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(ctx, lib().sdrt_rk54_adaptive_step(ctx, int(mesh), _ptr(U), float(dt), float(atol), float(rtol),
+                                              ctypes.byref(err), ctypes.byref(dtn), ctypes.byref(acc)))
+    return bool(acc.value), err.value, dtn.value
+
+
+def sdrt_rk54_integrate(ctx, mesh, U, t_span, dt, atol, rtol, max_steps=100000):
+    """(dt_next, accepted steps, rejected steps) of an adaptive integration over t_span."""
+    d, na, nr = ctypes.c_double(dt), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().sdrt_rk54_integrate(ctx, int(mesh), _ptr(U), float(t_span), ctypes.byref(d), float(atol),
+                                          float(rtol), int(max_steps), ctypes.byref(na), ctypes.byref(nr)))
+    return d.value, na.value, nr.value
 
 
 def sdrt_rk4_step_host(ctx, mesh, U_in, U_out, dt, nsteps=1):
@@ -494,6 +518,18 @@ class Mesh:
     def rk4_step(self, U, dt, nsteps=1):
         self._check(U)
         sdrt_rk4_step(self.ctx.ptr, self.id, U, dt, nsteps)
+
+    def rk54_step(self, U, dt, nsteps=1):
+        self._check(U)
+        sdrt_rk54_step(self.ctx.ptr, self.id, U, dt, nsteps)
+
+    def rk54_adaptive_step(self, U, dt, atol, rtol):
+        self._check(U)
+        return sdrt_rk54_adaptive_step(self.ctx.ptr, self.id, U, dt, atol, rtol)
+
+    def rk54_integrate(self, U, t_span, dt, atol, rtol, max_steps=100000):
+        self._check(U)
+        return sdrt_rk54_integrate(self.ctx.ptr, self.id, U, t_span, dt, atol, rtol, max_steps)
 
     def rk4_step_host(self, U_in, U_out, dt, nsteps=1):
         self._check(U_in, U_out, device=False)

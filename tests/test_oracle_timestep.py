@@ -78,8 +78,24 @@ def test_embedded_estimate_is_third_order():
     assert np.all(r > 3.7), (est, r)
 
 
-@pytest.mark.parametrize("err,prev", [(0.5, 1.0), (2.0, 0.8), (1e-9, 1.0)])
-def test_pi_factor_closed_form(err, prev):
+@pytest.mark.parametrize("err,prev,acc", [(0.5, 1.0, True), (0.8, 0.3, True), (1e-9, 1.0, True), (2.0, 0.8, False)])
+def test_pi_factor_closed_form(err, prev, acc):
     k = 4
-    want = min(5.0, max(0.2, 0.9 * err ** (-0.7 / k) * prev ** (0.4 / k)))
-    assert ts.pi_factor(err, prev, 3) == pytest.approx(want, rel=1e-15)
+    want = 0.9 * err ** (-0.7 / k) * (prev ** (0.4 / k) if acc else 1.0)
+    want = min(5.0, max(0.2, want))
+    assert ts.pi_factor(err, prev, acc) == pytest.approx(want, rel=1e-15)
+
+
+def test_adaptive_integration_meets_its_tolerance():
+    """The controller reaches the end of the span exactly, rejects and shrinks
+    a far too large first step, and the global error of the logistic
+    solution is of the order of the tolerance."""
+    for tol in (1e-6, 1e-9):
+        U, dt, nacc, nrej = ts.integrate(_logistic, [np.array([0.2])], 2.0, 1.5, tol, tol)
+        err = abs(U[0][0] - _logistic_exact(0.2, 2.0))
+        assert nrej >= 1 and nacc >= 3
+        assert err < 100 * tol, (tol, err, nacc, nrej)
+    # tighter tolerance, more steps
+    _, _, n6, _ = ts.integrate(_logistic, [np.array([0.2])], 2.0, 0.1, 1e-6, 1e-6)
+    _, _, n9, _ = ts.integrate(_logistic, [np.array([0.2])], 2.0, 0.1, 1e-9, 1e-9)
+    assert n9 > n6
