@@ -338,6 +338,21 @@ int sdrt_rk54_adaptive_step(sdrt_ctx* ctx, int mesh_id, void* U_dev, double dt, 
 int sdrt_rk54_integrate(sdrt_ctx* ctx, int mesh_id, void* U_dev, double t_span, double* dt_inout, double atol,
                         double rtol, int max_steps, int* n_accepted, int* n_rejected);
 
+/* Taylor-Green vortex diagnostics of the state U_dev (paper Sec. 5.3; 3D
+ * Navier-Stokes meshes), ensemble averages <.> = (1/|Omega|) int_Omega . with
+ * an element quadrature exact for degree 10 (7 Gauss-Legendre points per
+ * direction, collapsed on simplices), velocity gradients from the LDG
+ * gradients of the scheme (Sec. 2.1), t_c = length / v_inf:
+ *   out[0] = <E*>, E* = (1/2) rho v.v / (rho_inf v_inf^2);
+ *   out[1] = eps1 = -d<E*>/dt*, from the residual: -t_c <v . R_m - |v|^2 R_rho / 2>
+ *            / (rho_inf v_inf^2);
+ *   out[2] = eps2 = 2 mu t_c <S^d : S^d> / (rho_inf v_inf^2);
+ *   out[3] = eps3 = -t_c <p div v> / (rho_inf v_inf^2).
+ * eps1 - eps2 - eps3 estimates the numerical dissipation.  Synchronises the
+ * stream. */
+int sdrt_tgv_diagnostics(sdrt_ctx* ctx, int mesh_id, const void* U_dev, double rho_inf, double v_inf, double length,
+                         double* out4);
+
 /* Same as sdrt_rk4_step with host buffers: copies U_in_host to the device,
  * steps, copies the result to U_out_host and synchronises the stream.
  * U_in_host / U_out_host: state_len values (may be the same buffer; pinned

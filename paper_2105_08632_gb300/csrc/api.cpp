@@ -61,6 +61,7 @@ struct EType {
     RefElement R;
     int Mi = 0, Mi_pad = 0, Md_pad = 0, Mg_pad = 0, Mir = 0, Mdt_pad = 0, Agr_pad = 0;
     DevBuf Ai[2], Ad[2], Air[2], Ag[2], Adt[2], Agr[2];  // [0] double, [1] float
+    DevBuf Mq[2], wq[2];              // element quadrature: nodal basis at the points, weights
     DevBuf fe_face, fi_tab;
 };
 
@@ -100,6 +101,7 @@ struct Mesh {
     DevBuf qfe, dqfe, qfiu, dqfiu;    // viscous: flux-point gradients (kargs.hpp layout)
     DevBuf cbar;                      // viscous VJP: adjoint of the common value (UFE layout)
     DevBuf rk_r, rk_du, rk_err, rk_u0, rk_part;   // RK54: residual, second register, estimate, step start
+    DevBuf qsol, diag_sums;           // Taylor-Green diagnostics: solution-point gradients, integrals
     double pi_err_prev = 1.0;         // RK54 PI controller: error norm of the last accepted step
     // Block tables of the generic kernels (one launch per kernel kind walks
     // every block): host copies and the device array, in the mesh precision.
@@ -1157,6 +1159,10 @@ int sdrt_setup_element_type(sdrt_ctx* ctx, const sdrt_etype_desc* d, int* etype_
         SDRT_CUDA(upload(et->Adt[1], Adtf));
         SDRT_CUDA(upload(et->Agr[0], Agr));
         SDRT_CUDA(upload(et->Agr[1], Agrf));
+        SDRT_CUDA(upload(et->Mq[0], R.Mq));
+        SDRT_CUDA(upload(et->Mq[1], std::vector<float>(R.Mq.begin(), R.Mq.end())));
+        SDRT_CUDA(upload(et->wq[0], R.wq));
+        SDRT_CUDA(upload(et->wq[1], std::vector<float>(R.wq.begin(), R.wq.end())));
     }
     ctx->etypes.push_back(std::move(et));
     *etype_id = (int)ctx->etypes.size() - 1;
@@ -2010,6 +2016,71 @@ int sdrt_rk54_integrate(sdrt_ctx* ctx, int mesh_id, void* U, double t_span, doub
         dt = dn;
     }
     *dt_inout = dt;
+    return SDRT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+int tgv_diagnostics(sdrt_ctx* ctx, Mesh& m, const T* U, double* sums) {
+    T* R = m.rk_r.as<T>();
+    KEpi<T> E{};
+    E.mode = EPI_STORE;
+    E.out = R;
+    E.flag = ctx->flag.as<int>();
+    int r = run_residual<T>(ctx, m, U, nullptr, E);
+    if (r) return r;
+    const KPhys<T> P = make_phys<T>(m.phys);
+    const KSet<T> ks = kset<T>(m);
+    launch_interp_ext<T>(ks, m.nvar, U, m.ufe.as<T>(), m.Ftot, ctx->nsm, ctx->stream);
+    ++ctx->launches;
+    r = launch_grad<T>(ks, m.phys.system, m.nd, U, nullptr, m.ufe.as<T>(), nullptr, m.Ftot, P, m.qfe.as<T>(), nullptr,
+                       m.qfiu.as<T>(), nullptr, ctx->nsm, ctx->stream, m.qsol.as<T>());
+    if (r) return fail(ctx, SDRT_ERR_UNSUPPORTED, "gradient kernel not available");
+    ++ctx->launches;
+    SDRT_CUDA(cudaMemsetAsync(m.diag_sums.p, 0, 5 * sizeof(double), ctx->stream));
+    const int pi = std::is_same<T, float>::value ? 1 : 0;
+    for (auto& bp : m.blocks) {
+        const EType& et = *ctx->etypes[bp->etype];
+        launch_tgv_diag<T>(make_kblock<T>(et, *bp), U, m.qsol.as<T>(), R, et.Mq[pi].as<T>(), et.wq[pi].as<T>(),
+                           (int)et.R.wq.size(), (T)m.phys.gamma, m.diag_sums.as<double>(), ctx->nsm, ctx->stream);
+        ++ctx->launches;
+    }
+    SDRT_CUDA(cudaMemcpyAsync(sums, m.diag_sums.p, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SDRT_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, SDRT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return SDRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdrt_tgv_diagnostics(sdrt_ctx* ctx, int mesh_id, const void* U, double rho_inf, double v_inf, double length,
+                         double* out) {
+    int r = check_whole(ctx, mesh_id);
+    if (r) return r;
+    if (!U || !out || !(rho_inf > 0) || !(v_inf > 0) || !(length > 0)) return fail(ctx, SDRT_ERR_ARG, "bad argument");
+    Mesh& m = *ctx->meshes[mesh_id];
+    if (m.phys.system != SDRT_NAVIER_STOKES || m.nd != 3)
+        return fail(ctx, SDRT_ERR_UNSUPPORTED, "the Taylor-Green diagnostics need a 3D Navier-Stokes mesh");
+    if ((r = ensure_workspace(ctx, m, false, false))) return r;
+    if ((r = rk54_workspace(ctx, m, false))) return r;
+    const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;
+    if (!m.qsol.p) SDRT_CUDA(m.qsol.alloc((size_t)m.nd * m.state_len * es));
+    if (!m.diag_sums.p) SDRT_CUDA(m.diag_sums.alloc(5 * sizeof(double)));
+    double s[5];
+    r = m.phys.precision == SDRT_FP32 ? tgv_diagnostics<float>(ctx, m, static_cast<const float*>(U), s)
+                                       : tgv_diagnostics<double>(ctx, m, static_cast<const double*>(U), s);
+    if (r) return r;
+    const double scale = rho_inf * v_inf * v_inf, tc = length / v_inf, vol = s[0];
+    out[0] = s[1] / vol / scale;                                   // <E*>
+    out[1] = -tc * s[2] / vol / scale;                             // eps1 = -d<E*>/dt*
+    out[2] = 2.0 * m.phys.mu * tc * s[3] / vol / scale;            // eps2
+    out[3] = -tc * s[4] / vol / scale;                             // eps3
     return SDRT_OK;
 }
 

@@ -57,9 +57,19 @@ int launch_residual_visc(const KSet<T>& ks, int system, int riemann, int nd, con
 // (UFE must hold u_fe of every block): QFE / QFIU (kargs.hpp layout), and with
 // dU / dUFE non-null also their tangents dQFE / dQFIU.  One launch.  Returns
 // -1 for an unsupported (system, nd) combination, -2 without tile widths.
+// QSOL non-null (value mode): also the solution-point gradients, per block
+// [N_s][ND][V][ld] at ND * u_off.
 template <typename T>
 int launch_grad(const KSet<T>& ks, int system, int nd, const T* U, const T* dU, const T* UFE, const T* dUFE,
-                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int nsm, cudaStream_t st);
+                int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int nsm, cudaStream_t st,
+                T* QSOL = nullptr);
+
+// Taylor-Green diagnostics integrals of one block (kernels_visc.cu), added to
+// sums[5] = {volume, kinetic energy, its time derivative from R, S^d : S^d,
+// p div v}; 3D Navier-Stokes.
+template <typename T>
+void launch_tgv_diag(const KBlock<T>& B, const T* U, const T* Q, const T* R, const T* Mq, const T* wq, int nq, T gamma,
+                     double* sums, int nsm, cudaStream_t st);
 
 // Vector-Jacobian product of the inviscid residual, every block in one launch
 // per pass (kernels_vjp.cu).  pass 0: GS (UFE layout) = s G at the external

@@ -240,6 +240,64 @@ std::vector<double> gauss_legendre(int n) {
     return x;
 }
 
+std::vector<double> gauss_legendre_weights(const std::vector<double>& x) {
+    const int n = (int)x.size();
+    std::vector<double> w(n), P(n + 2), dP(n + 2);
+    for (int i = 0; i < n; ++i) {
+        legendre(n, x[i], P.data(), dP.data());
+        w[i] = 2.0 / ((1.0 - x[i] * x[i]) * dP[n] * dP[n]);
+    }
+    return w;
+}
+
+void element_quadrature(int shape, int n, std::vector<double>& X, std::vector<double>& W) {
+    const std::vector<double> g = gauss_legendre(n), w = gauss_legendre_weights(g);
+    X.clear();
+    W.clear();
+    // Triangle x_i >= -1, x + y <= 0: x = (1 + a)(1 - b)/2 - 1, y = b, factor (1 - b)/2.
+    auto tri = [&](std::vector<double>& Xt, std::vector<double>& Wt) {
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                Xt.push_back((1 + g[i]) * (1 - g[j]) / 2 - 1);
+                Xt.push_back(g[j]);
+                Wt.push_back(w[i] * w[j] * (1 - g[j]) / 2);
+            }
+    };
+    if (shape == QUAD || shape == HEX) {
+        const int nz = shape == HEX ? n : 1;
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    X.push_back(g[i]);
+                    X.push_back(g[j]);
+                    if (shape == HEX) X.push_back(g[k]);
+                    W.push_back(w[i] * w[j] * (shape == HEX ? w[k] : 1.0));
+                }
+    } else if (shape == TRI) {
+        tri(X, W);
+    } else if (shape == PRI) {
+        std::vector<double> Xt, Wt;
+        tri(Xt, Wt);
+        for (int k = 0; k < n; ++k)
+            for (size_t m = 0; m < Wt.size(); ++m) {
+                X.insert(X.end(), {Xt[2 * m], Xt[2 * m + 1], g[k]});
+                W.push_back(Wt[m] * w[k]);
+            }
+    } else {
+        // Tetrahedron x_i >= -1, x + y + z <= -1: z = c, y = (1 + b)(1 - c)/2 - 1,
+        // x = (1 + a)(-y - c)/2 - 1, factor (1 - c)/2 (-y - c)/2.
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) {
+                    const double z = g[k];
+                    const double y = (1 + g[j]) * (1 - z) / 2 - 1;
+                    const double x = (1 + g[i]) * (-y - z) / 2 - 1;
+                    X.insert(X.end(), {x, y, z});
+                    W.push_back(w[i] * w[j] * w[k] * (1 - z) / 2 * (-y - z) / 2);
+                }
+    }
+}
+
 RefElement build_ref_element(int shape, int p) {
     if (shape < 0 || shape > 4) throw std::runtime_error("unknown element shape");
     if (p < 1 || p > 8) throw std::runtime_error("degree out of range");
@@ -405,6 +463,8 @@ RefElement build_ref_element(int shape, int p) {
     };
     interp(R.xfe, R.nfe, R.M0);
     interp(R.xfiu, R.nfiu, R.M12);
+    element_quadrature(shape, 7, R.xq, R.wq);
+    interp(R.xq, (int)R.wq.size(), R.Mq);
 
     // Flux nodal basis: Vf[sigma][m] = psi^f_m(x_sigma) . n_sigma, flux DOFs = ext then internal.
     auto modes = rt_modes(shape, p);

@@ -29,6 +29,12 @@ struct RefElement {
     std::vector<double> M15;       // nd*nsol x nfi   (rows: axis outer)
     std::vector<double> M16;       // nd*nsol x nfe
     double cond_hint = 0;          // max |entry| of the inverse flux Vandermonde
+    // Element quadrature exact for polynomials of degree 10 (ensemble
+    // averages of the Taylor-Green diagnostics): Gauss-Legendre tensor rule
+    // with 7 points per direction, collapsed (Duffy) onto simplices.
+    std::vector<double> xq;        // nq x nd  points
+    std::vector<double> wq;        // nq       weights (sum = reference volume)
+    std::vector<double> Mq;        // nq x nsol solution nodal basis at the points
 };
 
 // Builds the element; throws std::runtime_error on failure.
@@ -43,5 +49,12 @@ const std::vector<std::vector<int>>& face_vertices(int shape);
 
 // Gauss-Legendre nodes on [-1, 1], ascending.
 std::vector<double> gauss_legendre(int n);
+// Gauss-Legendre weights of those nodes.
+std::vector<double> gauss_legendre_weights(const std::vector<double>& x);
+
+// Quadrature rule on the reference element of `shape` with n Gauss-Legendre
+// points per direction (tensor rule; collapsed onto simplices): points (nq x nd)
+// and weights.
+void element_quadrature(int shape, int n, std::vector<double>& X, std::vector<double>& W);
 
 }  // namespace sdrt

@@ -27,7 +27,7 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
             "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option",
             "sdrt_autotune", "sdrt_get_tiles", "sdrt_profile_collect_blocks", "sdrt_rk54_step",
-            "sdrt_rk54_adaptive_step", "sdrt_rk54_integrate"]
+            "sdrt_rk54_adaptive_step", "sdrt_rk54_integrate", "sdrt_tgv_diagnostics"]
 
 
 class SdrtError(RuntimeError):
@@ -106,6 +106,7 @@ def lib():
         "sdrt_rk4_step": (I, [P, I, P, D, I]),
         "sdrt_rk4_step_host": (I, [P, I, P, P, D, I]),
         "sdrt_rk54_step": (I, [P, I, P, D, I]),
+        "sdrt_tgv_diagnostics": (I, [P, I, P, D, D, D, ctypes.POINTER(D)]),
         "sdrt_rk54_adaptive_step": (I, [P, I, P, D, D, D, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)]),
         "sdrt_rk54_integrate": (I, [P, I, P, D, ctypes.POINTER(D), D, D, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "sdrt_jvp": (I, [P, I, P, P, P]),
@@ -320,6 +321,13 @@ def sdrt_rk54_integrate(ctx, mesh, U, t_span, dt, atol, rtol, max_steps=100000):
     return d.value, na.value, nr.value
 
 
+def sdrt_tgv_diagnostics(ctx, mesh, U, rho_inf=1.0, v_inf=1.0, length=1.0):
+    """Dict <E*>, eps1, eps2, eps3 of the Taylor-Green diagnostics."""
+    out = (ctypes.c_double * 4)()
+    _check(ctx, lib().sdrt_tgv_diagnostics(ctx, int(mesh), _ptr(U), float(rho_inf), float(v_inf), float(length), out))
+    return {"E": out[0], "eps1": out[1], "eps2": out[2], "eps3": out[3]}
+
+
 def sdrt_rk4_step_host(ctx, mesh, U_in, U_out, dt, nsteps=1):
     _check(ctx, lib().sdrt_rk4_step_host(ctx, int(mesh), _ptr(U_in), _ptr(U_out), float(dt), int(nsteps)))
 
@@ -530,6 +538,10 @@ class Mesh:
     def rk54_integrate(self, U, t_span, dt, atol, rtol, max_steps=100000):
         self._check(U)
         return sdrt_rk54_integrate(self.ctx.ptr, self.id, U, t_span, dt, atol, rtol, max_steps)
+
+    def tgv_diagnostics(self, U, rho_inf=1.0, v_inf=1.0, length=1.0):
+        self._check(U)
+        return sdrt_tgv_diagnostics(self.ctx.ptr, self.id, U, rho_inf, v_inf, length)
 
     def rk4_step_host(self, U_in, U_out, dt, nsteps=1):
         self._check(U_in, U_out, device=False)
