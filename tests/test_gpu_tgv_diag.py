@@ -42,7 +42,7 @@ def test_diagnostics_match_oracle(ctx, kind, n, p, precision):
                 (step, k, got[k], want[k])
         assert abs(got["eps3"] - want["eps3"]) <= (1e-9 if precision == "fp64" else 1e-2) * abs(want["eps2"]), \
             (step, got["eps3"], want["eps3"])
-        U = ores.rk4_step(geom, oph, U, 0.05)
+        U = ores.rk4_step(geom, oph, U, 5e-4)
 
 
 def test_diagnostics_reject_other_systems(ctx):
