@@ -241,7 +241,19 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
             prefetch_rows<NT>(a.metric, SM::NM, a.ld, en);
             prefetch_rows<NT>(a.pmap, K::NFE, a.ld, en);
         }
+        // The RK inputs of this tile's epilogue into L2 while the groups run.
+        if (E.mode == EPI_RK_FIRST || E.mode == EPI_RK_MID)
+            prefetch_rows<NT>(E.u0 + a.u_off, NS * V, a.ld, e0);
+        if (E.mode == EPI_RK_MID || E.mode == EPI_RK_LAST)
+            prefetch_rows<NT>(E.uacc + a.u_off, NS * V, a.ld, e0);
         cp_async_wait_all();
+        __syncthreads();
+        // The partners' face records of the whole tile into L2 (the map has
+        // arrived), ahead of the groups' copies into shared memory.
+        {
+            const int* PMt = reinterpret_cast<const int*>(smem + SM::PM);
+            for (int i = threadIdx.x; i < K::NFE * TE; i += NT) prefetch_l2(a.FRin + PMt[i]);
+        }
         float acc[NSH];
         #pragma unroll
         for (int r = 0; r < NSH; ++r) acc[r] = 0.f;
