@@ -160,13 +160,22 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     for (auto& c : dcol) nnzD += (long)c.size();
     const int NSH = (NS + SPLIT - 1) / SPLIT;      // divergence rows per part
 
-    // x[j * ldx] = sum_c A[row_j][c] u[c * ldu] for the rows (row_j, j) listed
+    // x[j * ldx] = sum_c A[row_j][c] u[c] for the rows (row_j, j) listed; u is
+    // the thread's solution column, contiguous and 16-byte aligned in shared
+    // memory, read as float4 blocks of the columns used
     auto emit_rows = [&](std::ostringstream& o, const std::vector<std::pair<int, int>>& rows) {
         std::vector<int> used(NS, 0);
         for (auto& rj : rows)
             for (auto& e : SI.rows[rj.first]) used[e.first] = 1;
-        for (int c = 0; c < NS; ++c)
-            if (used[c]) o << "        const float u" << c << " = u[" << c << " * ldu];\n";
+        for (int b = 0; 4 * b < NS; ++b) {
+            bool any = false;
+            for (int c = 4 * b; c < std::min(NS, 4 * b + 4); ++c) any = any || used[c];
+            if (!any) continue;
+            o << "        const float4 b" << b << " = reinterpret_cast<const float4*>(u)[" << b << "];\n";
+            const char* comp[4] = {"x", "y", "z", "w"};
+            for (int c = 4 * b; c < std::min(NS, 4 * b + 4); ++c)
+                if (used[c]) o << "        const float u" << c << " = b" << b << "." << comp[c - 4 * b] << ";\n";
+        }
         for (auto& rj : rows) {
             auto& rr = SI.rows[rj.first];
             std::string e = "0.0f";
@@ -222,7 +231,7 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     // in shared memory; x indexed from the chunk's first row
     const int ECH = std::min(NFE, std::max(1, GR - 1)), NECH = (NFE + ECH - 1) / ECH;
     o << "    static constexpr int ECH = " << ECH << ", NECH = " << NECH << ";\n";
-    o << "    static __device__ __forceinline__ void ext(int c, int h, const float* __restrict__ u, const int ldu, "
+    o << "    static __device__ __forceinline__ void ext(int c, int h, const float* __restrict__ u, "
          "float* __restrict__ x, const int ldx) {\n";
     bool first = true;
     for (int c = 0; c < NECH; ++c) {
@@ -243,7 +252,7 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
         for (int i : g) nf += pts[i].ext ? 1 : (int)pts[i].dofs.size();
         o << "template <> struct " << T << "::Grp<" << gi << "> {\n"
           << "    static constexpr int NP = " << g.size() << ", NDOF = " << nf << ", OFF = " << goff[gi] << ";\n"
-          << "    static __device__ __forceinline__ void interp(int h, const float* __restrict__ u, const int ldu, "
+          << "    static __device__ __forceinline__ void interp(int h, const float* __restrict__ u, "
              "float* __restrict__ x, const int ldx) {\n";
         const int np = (int)g.size();
         for (int h = 0; h < SPLIT; ++h) {

@@ -5,7 +5,7 @@
 //                                group's point + DOF rows
 //   K::SPLIT, NSH               threads per (element, variable) column and the
 //                                divergence rows each of them owns
-//   K::Grp<g>::interp(h, u, ldu, x, ldx)  point states of group g, x = A_g u,
+//   K::Grp<g>::interp(h, u, x, ldx)  point states of group g, x = A_g u,
 //                                        part h of the rows (rows of
 //                                        [M0; M12], structural non-zeros
 //                                        only, FP32 immediates)
@@ -14,7 +14,7 @@
 //   K::desc(i)                  point descriptors: external point sigma and
 //                                its face, or internal point with its DOF axes,
 //                                and the first DOF row of the point
-//   K::ext(c, h, u, ldu, x, ldx)  x = M0 u for chunk c of the external points,
+//   K::ext(c, h, u, x, ldx)     x = M0 u for chunk c of the external points,
 //                                part h
 //
 // A CTA works on a tile of 32 consecutive elements of one block with
@@ -50,9 +50,13 @@ struct Smem {
     static constexpr int NT = K::SPLIT * V * TE;             // threads of a CTA
     static constexpr int LDX = V * TE;                       // row stride (values) of US / group rows
     static constexpr int NM = 1 + 9 + K::NF * 4;             // metric rows (3D, kargs.hpp layout)
-    // [US: NS rows][group rows: GR][metric: NM x TE][partner map: NFE x TE (int)]
+    // The tile's state US is stored column by column, [V][TE][CS]: each
+    // thread's solution column contiguous (float4 reads), CS = 4 k with k odd
+    // so that the 16-byte reads of 8 consecutive lanes hit distinct banks.
+    static constexpr int CS = (K::NS + 3) / 4 % 2 ? (K::NS + 3) / 4 * 4 : (K::NS + 3) / 4 * 4 + 4;
+    // [US: V TE CS][group rows: GR][metric: NM x TE][partner map: NFE x TE (int)]
     static constexpr int US = 0;
-    static constexpr int XS = K::NS * LDX;
+    static constexpr int XS = V * TE * CS;
     static constexpr int MS = XS + K::GR * LDX;
     static constexpr int PM = MS + NM * TE;
     static constexpr int MAIN = PM + K::NFE * TE;
@@ -94,6 +98,18 @@ __device__ __forceinline__ void stage_rows(E* dst, const E* src, int rows, int l
             cp_async4(dst + i, src + (size_t)(i >> 5) * ld + min(e0 + (i & 31), nelem - 1));
     }
 }
+// The tile's state (rows (rho, v) of a block's [N_s][V][ld] array) into the
+// column layout [V][TE][CS] with asynchronous copies; lanes past the end
+// repeat the last element.
+template <int NT, int NS, int V, int CS>
+__device__ __forceinline__ void stage_state(float* dst, const float* src, int ld, int e0, int nelem) {
+    for (int i = threadIdx.x; i < NS * V * TE; i += NT) {
+        const int row = i >> 5, te = i & 31;
+        const int rho = row / V, v = row - rho * V;
+        cp_async4(dst + (v * TE + te) * CS + rho, src + (size_t)row * ld + min(e0 + te, nelem - 1));
+    }
+}
+
 // L2 prefetch of the same rows for a later tile (one 128-byte line per row).
 template <int NT, typename E>
 __device__ __forceinline__ void prefetch_rows(const E* src, int rows, int ld, int e0) {
@@ -112,7 +128,7 @@ __device__ __forceinline__ void write_records(float* sm, float* dst, int nvalid,
         const int c0 = c * K::ECH;
         const int rows = min(K::ECH, K::NFE - c0);
         __syncthreads();                                // staging free, US complete
-        K::ext(c, h, sm + SM::US + v * TE + lane, SM::LDX, S + lane * SM::PADREC + v, V);
+        K::ext(c, h, sm + SM::US + (v * TE + lane) * SM::CS, S + lane * SM::PADREC + v, V);
         __syncthreads();
         const int nv = rows * V;
         for (int i = threadIdx.x; i < nvalid * nv; i += SM::NT) {
@@ -147,7 +163,7 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
             for (int q = 0; q < V; ++q) cp_async4(FS + (d.z * V + q) * TE + te, src + q);
         }
     }
-    Grp::interp(h, US + v * TE + lane, LDX, XS + v * TE + lane, LDX);
+    Grp::interp(h, US + (v * TE + lane) * SM::CS, XS + v * TE + lane, LDX);
     cp_async_wait_all();
     __syncthreads();
     for (int it = threadIdx.x; it < Grp::NP * TE; it += NT) {
@@ -232,7 +248,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
         __syncthreads();                                // previous tile's shared memory free
         // The tile's state, metric rows and partner map, copied asynchronously;
         // the next tile's rows prefetched into L2 meanwhile.
-        stage_rows<NT>(smem + SM::US, Ub, NS * V, a.ld, e0, a.nelem);
+        stage_state<NT, NS, V, SM::CS>(smem + SM::US, Ub, a.ld, e0, a.nelem);
         stage_rows<NT>(smem + SM::MS, a.metric, SM::NM, a.ld, e0, a.nelem);
         stage_rows<NT>(reinterpret_cast<int*>(smem + SM::PM), a.pmap, K::NFE, a.ld, e0, a.nelem);
         const int en = (tile + gridDim.x) * TE;
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
             __syncthreads();
             #pragma unroll
             for (int r = 0; r < NSH; ++r)
-                if (r < nrow) smem[SM::US + ((h * NSH + r) * V + v) * TE + lane] = acc[r];
+                if (r < nrow) smem[SM::US + (v * TE + lane) * SM::CS + h * NSH + r] = acc[r];
             write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h,
                                 lane);
         }
@@ -333,7 +349,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE) k_gen_interp(const GenArgs 
     for (int tile = blockIdx.x; tile * TE < a.nelem; tile += gridDim.x) {
         const int e0 = tile * TE;
         __syncthreads();                                // previous tile's staging read
-        stage_rows<NT>(smem + SM::US, a.U + a.u_off, K::NS * V, a.ld, e0, a.nelem);
+        stage_state<NT, K::NS, V, SM::CS>(smem + SM::US, a.U + a.u_off, a.ld, e0, a.nelem);
         cp_async_wait_all();
         write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h, lane);
     }
