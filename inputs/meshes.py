@@ -168,3 +168,70 @@ def merge_meshes(parts):
         shifts.append(m["shift"])
         nb += len(m["blocks"])
     return {"blocks": blocks, "faces": np.concatenate(faces), "shift": np.concatenate(shifts)}
+
+
+# Reference vertices of each element type (the vertex order above).
+_REF_VERTS = {
+    "tri": [(-1, -1), (1, -1), (-1, 1)],
+    "quad": [(-1, -1), (1, -1), (1, 1), (-1, 1)],
+    "tet": [(-1, -1, -1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1)],
+    "pri": [(-1, -1, -1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1), (1, -1, 1), (-1, 1, 1)],
+    "hex": [(-1, -1, -1), (1, -1, -1), (1, 1, -1), (-1, 1, -1), (-1, -1, 1), (1, -1, 1), (1, 1, 1), (-1, 1, 1)],
+}
+
+
+def map_nodes(shape):
+    """Reference positions of the nodes of a curved element's quadratic map:
+    the points of the reference element with every coordinate in {-1, 0, 1},
+    lexicographic with x fastest (tri 6, quad 9, tet 10, pri 18, hex 27)."""
+    nd = len(_REF_VERTS[shape][0])
+    out = []
+    for c in itertools.product((-1, 0, 1), repeat=nd):
+        x = c[::-1]
+        s = sum(x[:2])
+        if shape == "tet":
+            s = sum(x) + 1
+        if shape in ("quad", "hex") or s <= 0:
+            out.append(x)
+    return np.array(out, float)
+
+
+def curved_mesh(mesh, amp, seed=None):
+    """The mesh with every element curved: each block gains "nodes" (E, NN, ND),
+    the nodes of its straight element moved by the smooth periodic displacement
+      2D  d = amp L (sin(2 pi y~) , sin(2 pi x~)),
+      3D  d = amp L (sin(2 pi y~) sin(2 pi z~), sin(2 pi z~) sin(2 pi x~), sin(2 pi x~) sin(2 pi y~)),
+    x~ = (x - lo) / L per axis (L the box size along each axis; a phase drawn
+    from seed shifts each sine when given).  Vertices move too ("verts" is
+    updated), faces and periodic shifts are unchanged: the displacement is
+    periodic, so glued faces keep coincident points."""
+    lo, hi = (np.asarray(v, float) for v in mesh["box"])
+    L = hi - lo
+    nd = len(L)
+    ph = np.zeros(nd) if seed is None else np.random.default_rng(seed).uniform(0, 2 * np.pi, nd)
+
+    def disp(x):
+        t = 2 * np.pi * (x - lo) / L + ph
+        s = np.sin(t)
+        if nd == 2:
+            return amp * L * np.stack([s[..., 1], s[..., 0]], axis=-1)
+        return amp * L * np.stack([s[..., 1] * s[..., 2], s[..., 2] * s[..., 0], s[..., 0] * s[..., 1]], axis=-1)
+
+    blocks = []
+    for blk in mesh["blocks"]:
+        shape = blk["shape"]
+        ref = np.array(_REF_VERTS[shape], float)
+        A = np.column_stack([ref, np.ones(len(ref))])
+        Xn = map_nodes(shape)
+        An = np.column_stack([Xn, np.ones(len(Xn))])
+        V = np.asarray(blk["verts"], float)
+        nodes = np.empty((len(V), len(Xn), nd))
+        for e in range(len(V)):
+            C = np.linalg.lstsq(A, V[e], rcond=None)[0]
+            nodes[e] = An @ C
+        nodes = nodes + disp(nodes)
+        vidx = [int(np.nonzero((Xn == r).all(axis=1))[0][0]) for r in ref]
+        blocks.append({"shape": shape, "verts": nodes[:, vidx].copy(), "nodes": nodes})
+    out = dict(mesh)
+    out["blocks"] = blocks
+    return out

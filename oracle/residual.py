@@ -9,11 +9,14 @@ SDRT residual, in the paper's order (Sec. 2.1):
                                                    "interpolate_sol_to_fluxint", App. B)
   2. viscous only: common value C at external points (Eq. "common_var_for_grad"),
      transformed gradient q~ = M16 C + M15 u_fi (Eq. for q~ at solution points,
-     App. B), physical q = J^{-T} q~, interpolated with M0 / M12
-  3. internal DOFs: F~_nu = [det J J^{-1} f(u, q)] . n~_nu   (Eq. "normal_transformed_flux")
-  4. external points: F~ = det J |J^{-T} n~| F(uL, uR, qL, qR, n)  (common flux, Sec. 2.1)
+     App. B), physical q = J^{-T} q~ with J at each solution point,
+     interpolated with M0 / M12
+  3. internal DOFs: F~_nu = [det J J^{-1} f(u, q)] . n~_nu, J at the internal
+     point (Eq. "normal_transformed_flux")
+  4. external points: F~ = det J |J^{-T} n~| F(uL, uR, qL, qR, n), J at the
+     external point (common flux, Sec. 2.1)
   5. div = M14 F~_fe + M13 F~_fi                   (Eq. "divergence_sdrt", "residual_sdrt_matrices")
-  6. dU/dt = -div / det J                          (semi-discrete form, Sec. 2.1)
+  6. dU/dt = -div / det J, J at each solution point (semi-discrete form, Sec. 2.1)
 FR-SDRT (Sec. 2.3, Eq. "divergence_fr" with grad.g = grad.l^fe):
   div = sum_d D_d f~_d + M14 (F~_fe - (M0 f~) . n~_fe),  f~ at solution points;
   viscous gradient with the same correction: q~ = D u + M16 (C - M0 u).
@@ -59,9 +62,10 @@ def _face_sign(geom, b):
     return np.where(geom.is_left[s:s + n], 1.0, -1.0).reshape(g.nelem, g.ops.n_fe)
 
 
-def _to_phys_grad(Jinv, qt):
-    """q_i = sum_d Jinv[d, i] q~_d.  qt: (ND, N, V, E) -> (ND, N, V, E)."""
-    return np.einsum("edi,dnve->inve", Jinv, qt)
+def _to_phys_grad(Jinvs, qt):
+    """q_i = sum_d Jinv[d, i] q~_d at every solution point.  Jinvs: (E, N_s, ND, ND),
+    qt: (ND, N_s, V, E) -> (ND, N_s, V, E)."""
+    return np.einsum("endi,dnve->inve", Jinvs, qt)
 
 
 def solution_gradients(geom, phys, U, fr=False):
@@ -89,7 +93,7 @@ def _sol_gradients(geom, phys, U, ufe, ufiu, fr=False):
             Du = np.einsum("dsr,rve->dsve", ops.Dsol, U[b]).reshape(nd * ns, *U[b].shape[1:])
             qt = Du + np.einsum("sr,rve->sve", ops.M16, C - ufe[b])
         qt = qt.reshape(nd, ns, *qt.shape[1:])
-        out.append(_to_phys_grad(g.Jinv, qt))               # (ND, N_s, V, E)
+        out.append(_to_phys_grad(g.Jinvs, qt))               # (ND, N_s, V, E)
     return out
 
 
@@ -133,13 +137,13 @@ def residual(geom, phys, U, fr=False, terms=False):
             u_in = np.moveaxis(ufiu[b], -1, 0)
             q_in = np.moveaxis(qfiu[b], -1, 0) if phys.viscous else None
             f = phx.flux(phys, u_in, q_in)
-            ft = g.detJ[:, None, None, None] * np.einsum("edi,ekiv->ekdv", g.Jinv, f)
+            ft = g.detf[:, :, None, None] * np.einsum("ekdi,ekiv->ekdv", g.Jinvf, f)
             ftp = ft[:, ops.fi_point]                          # (E, N_fi, ND, V)
             Ft_fi = np.einsum("nd,endv->nve", ops.fi_dir, ftp)  # (N_fi, V, E)
             div = np.einsum("sf,fve->sve", ops.M14, Ft_fe) + np.einsum("sn,nve->sve", ops.M13, Ft_fi)
             if terms:
                 scales.append((np.einsum("sf,fve->sve", np.abs(ops.M14), np.abs(Ft_fe)) +
-                               np.einsum("sn,nve->sve", np.abs(ops.M13), np.abs(Ft_fi))) / g.detJ[None, None, :])
+                               np.einsum("sn,nve->sve", np.abs(ops.M13), np.abs(Ft_fi))) / g.dets.T[:, None, :])
         else:
             u_s = np.moveaxis(U[b], -1, 0)                      # (E, N_s, V)
             if phys.viscous:
@@ -148,12 +152,12 @@ def residual(geom, phys, U, fr=False, terms=False):
             else:
                 q_s = None
             f = phx.flux(phys, u_s, q_s)                        # (E, N_s, ND, V)
-            ft = g.detJ[:, None, None, None] * np.einsum("edi,esiv->esdv", g.Jinv, f)
+            ft = g.dets[:, :, None, None] * np.einsum("esdi,esiv->esdv", g.Jinvs, f)
             div = np.einsum("dsr,erdv->sve", ops.Dsol, ft)
             ft_fe = np.einsum("fs,esdv->efdv", ops.M0, ft)
             jump = Ft_fe - np.moveaxis(np.einsum("efdv,fd->efv", ft_fe, ops.nrm_fe), 0, -1)
             div = div + np.einsum("sf,fve->sve", ops.M14, jump)
-        out.append(-div / g.detJ[None, None, :])
+        out.append(-div / g.dets.T[:, None, :])
     return (out, scales) if terms else out
 
 
@@ -163,7 +167,7 @@ def _fr_sol_grad(g, phys, U, ufe, uL, uR):
     C = np.moveaxis(phx.common_value(phys, uL, uR), 0, -1)
     qt = np.einsum("dsr,rve->dsve", ops.Dsol, U) + \
         np.einsum("sr,rve->sve", ops.M16, C - ufe).reshape(nd, ns, *U.shape[1:])
-    q = _to_phys_grad(g.Jinv, qt)                           # (ND, N_s, V, E)
+    q = _to_phys_grad(g.Jinvs, qt)                          # (ND, N_s, V, E)
     return np.transpose(q, (3, 1, 0, 2))                   # (E, N_s, ND, V)
 
 

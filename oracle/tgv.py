@@ -78,6 +78,8 @@ def diagnostics(geom, phys, U, rho_inf=1.0, v_inf=1.0, length=1.0):
     Q = ores.solution_gradients(geom, phys, U)           # (ND, N_s, V, E) per block
     s = np.zeros(5)
     for g, u, r, q in zip(geom.blocks, U, R, Q):
+        if g.curved:
+            raise ValueError("diagnostics take affine elements (one det J per element)")
         Xq, Wq = quadrature(g.shape)
         L = operators.nodal_sol(g.shape, g.p, g.ops.xs, Xq)   # (nq, N_s)
         uq = np.einsum("qs,sve->qve", L, u)
