@@ -104,8 +104,9 @@ typedef struct {
  *   tri (-1,-1),(1,-1),(-1,1); quad (-1,-1),(1,-1),(1,1),(-1,1);
  *   tet (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1);
  *   pri tri x {-1} then tri x {+1}; hex quad x {-1} then quad x {+1}.
- * Elements must be affine images of the reference element (curved elements
- * are not supported: SDRT_ERR_UNSUPPORTED). Copied at setup. */
+ * With sdrt_setup_mesh the elements must be affine images of the reference
+ * element (else SDRT_ERR_UNSUPPORTED); curved elements are set up with
+ * sdrt_setup_mesh_curved.  Copied at setup. */
 typedef struct {
     int32_t etype;
     int32_t nelem;
@@ -132,7 +133,7 @@ typedef struct {
     int64_t ndof;        /* sum over blocks of nsol * nvar * nelem */
     int64_t nfe_total;   /* number of external flux points of the mesh */
     int32_t path;        /* kernels of the residual and RK4 steps: SDRT_PATH_* */
-    int32_t reserved;
+    int32_t curved;      /* 1 if some block has curved elements (sdrt_setup_mesh_curved) */
 } sdrt_mesh_info;
 /* Kernel paths of a mesh (sdrt_mesh_info.path). */
 #define SDRT_PATH_GENERIC 0      /* generic tile kernels, any element type / system */
@@ -182,6 +183,38 @@ int sdrt_get_operator(sdrt_ctx* ctx, int etype_id, int which, double* host_out, 
  * exactly once (periodic / closed meshes).  Host inputs are copied. */
 int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
                     int64_t nfaces, const sdrt_face* faces, int* mesh_id);
+
+/* Build a mesh whose blocks may hold curved elements.  The paper maps every
+ * element by a mapping function and evaluates its Jacobian, determinant and
+ * inverse analytically (Sec. 2, Eqs. "mapping_function", "mapping_jacobian",
+ * "inverse_mapping_jacobian", "transformed_quantities"); a curved element
+ * here is the second-order Lagrange map x(x~) = sum_k X_k N_k(x~) of its
+ * nodes.
+ *   nodes[b] = NULL: block b is affine, as for sdrt_setup_mesh.
+ *   nodes[b] != NULL: host FP64 array nelem x nnode x ndim of node positions.
+ *     The nodes are the reference points whose coordinates all lie in
+ *     {-1, 0, 1}, in lexicographic order with x~ fastest (tri 6, quad 9,
+ *     tet 10, pri 18, hex 27 nodes; the vertices are among them), and N_k
+ *     spans polynomials of total degree <= 2 (tri, tet), of degree <= 2 per
+ *     coordinate (quad, hex), or their product (pri: triangle x z).
+ *     blocks[b].verts is not read (may be NULL).  Glued faces must coincide
+ *     point by point (conforming curved faces; periodic shifts as usual).
+ * The metrics are evaluated in FP64 at every point where the method uses
+ * them (Sec. 2.1): J^{-T} at the solution points (physical gradients),
+ * det J J^{-1} at the internal flux points (Eq. "normal_transformed_flux"),
+ * the unit normal and det J |J^{-T} n~| at the external flux points (the
+ * transformed common flux; the L side's normal on both sides, each side's
+ * own scale), 1 / det J at the solution points (the semi-discrete form), and
+ * stored in the mesh precision.  A uniform state is preserved exactly when
+ * the transformed flux space holds the cofactors det J J^{-1} (quadratic
+ * polynomials; e.g. tetrahedra of degree >= 2, triangles of degree >= 1).
+ * Meshes with curved blocks run on the generic kernels (residual, RK
+ * steps, JVP, VJP, viscous systems); SDRT_ERR_UNSUPPORTED for the FR-SDRT
+ * scheme on curved blocks; sdrt_tgv_diagnostics refuses them.
+ * SDRT_ERR_MESH for a non-positive det J at any of those points.  Host
+ * inputs are copied. */
+int sdrt_setup_mesh_curved(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                           const double* const* nodes, int64_t nfaces, const sdrt_face* faces, int* mesh_id);
 int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out);
 
 /* One partition of a mesh whose residual is distributed over processes or

@@ -20,6 +20,7 @@
 #include "kargs.hpp"
 #include "gen_api.hpp"
 #include "launch.hpp"
+#include "mapping.hpp"
 #include "refel.hpp"
 #include "internal.hpp"
 
@@ -69,6 +70,11 @@ struct MBlock {
     int etype = 0, nelem = 0, ld = 0;
     int64_t u_off = 0, fe_base = 0, canon_base = 0;
     DevBuf metric, map;
+    // Metric rows (kargs.hpp): one value set per element (affine) or per
+    // point (curved: quadratic map, sdrt_setup_mesh_curved).
+    bool curved = false;
+    int nmetric = 0;
+    int mr_inv = 0, mr_ss = 1, mr_ssk = 0, mr_si = 1, mr_sik = 0, mr_f = 0, mr_ff = 0, mr_fp = 0;
     int tile = 32;                // elements per CTA tile
     int tile_dual = 32;
     int gtile = 0, gtile_dual = 0;  // gradient kernel (viscous systems)
@@ -91,6 +97,7 @@ struct Mesh {
     std::vector<std::unique_ptr<MBlock>> blocks;
     int64_t state_len = 0, Ftot = 0, ndof = 0, nfe_total = 0;
     bool fast = false;                // every block on the register-blocked record path
+    bool curved = false;              // some block has curved elements (generic kernels only)
     int64_t rec_total = 0, fiur_total = 0;
     int64_t qfiu_total = 0;           // viscous: length of QFIU
     std::vector<int32_t> partner;     // canonical face map
@@ -324,6 +331,14 @@ KBlock<T> make_kblock(const EType& et, const MBlock& b) {
     K.fe_face = et.fe_face.as<int>();
     K.fi_tab = et.fi_tab.as<int>();
     K.metric = b.metric.as<T>();
+    K.mr_inv = b.mr_inv;
+    K.mr_ss = b.mr_ss;
+    K.mr_ssk = b.mr_ssk;
+    K.mr_si = b.mr_si;
+    K.mr_sik = b.mr_sik;
+    K.mr_f = b.mr_f;
+    K.mr_ff = b.mr_ff;
+    K.mr_fp = b.mr_fp;
     K.map = b.map.as<int>();
     K.Air = et.Air[pi].as<T>();
     K.Mir = et.Mir;
@@ -1199,21 +1214,29 @@ int sdrt_get_operator(sdrt_ctx* ctx, int id, int which, double* out, int64_t n) 
 }
 
 static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
-                           const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id);
+                           const double* const* nodes, const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces,
+                           int* mesh_id);
 
 int sdrt_setup_mesh(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks, int64_t nfaces,
                     const sdrt_face* faces, int* mesh_id) {
-    return setup_mesh_impl(ctx, phys, nblocks, blocks, nullptr, nfaces, faces, mesh_id);
+    return setup_mesh_impl(ctx, phys, nblocks, blocks, nullptr, nullptr, nfaces, faces, mesh_id);
+}
+
+int sdrt_setup_mesh_curved(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
+                           const double* const* nodes, int64_t nfaces, const sdrt_face* faces, int* mesh_id) {
+    if (!nodes) return fail(ctx, SDRT_ERR_ARG, "null node array list");
+    return setup_mesh_impl(ctx, phys, nblocks, blocks, nodes, nullptr, nfaces, faces, mesh_id);
 }
 
 int sdrt_setup_partition(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
                          const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id) {
     if (!ghost) return fail(ctx, SDRT_ERR_ARG, "null ghost flags");
-    return setup_mesh_impl(ctx, phys, nblocks, blocks, ghost, nfaces, faces, mesh_id);
+    return setup_mesh_impl(ctx, phys, nblocks, blocks, nullptr, ghost, nfaces, faces, mesh_id);
 }
 
 static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks, const sdrt_block* blocks,
-                           const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces, int* mesh_id) {
+                           const double* const* nodes, const uint8_t* ghost, int64_t nfaces, const sdrt_face* faces,
+                           int* mesh_id) {
     if (!ctx || !phys || !blocks || !mesh_id || nblocks <= 0 || (nfaces > 0 && !faces))
         return fail(ctx, SDRT_ERR_ARG, "null or empty argument");
     int nown = nblocks;
@@ -1241,11 +1264,33 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
     m->fast = true;
     for (int b = 0; b < nblocks; ++b) {
         const sdrt_block& B = blocks[b];
+        const bool curved = nodes && nodes[b];
         if (B.etype < 0 || B.etype >= (int)ctx->etypes.size()) return fail(ctx, SDRT_ERR_ARG, "bad etype id");
-        if (B.nelem <= 0 || !B.verts) return fail(ctx, SDRT_ERR_ARG, "empty block");
+        if (B.nelem <= 0 || (!B.verts && !curved)) return fail(ctx, SDRT_ERR_ARG, "empty block");
         const RefElement& R = ctx->etypes[B.etype]->R;
         if (R.nd != nd) return fail(ctx, SDRT_ERR_ARG, "element dimension does not match physics");
         auto mb = std::make_unique<MBlock>();
+        if (curved) {
+            if (ctx->etypes[B.etype]->desc.scheme != SDRT_SCHEME_SDRT)
+                return fail(ctx, SDRT_ERR_UNSUPPORTED, "curved elements take the SDRT scheme");
+            // per point: 1/det J and S at the solution points, S at the unique
+            // internal points, normal and scale at the external points
+            mb->curved = true;
+            mb->mr_inv = 1;
+            mb->mr_ss = R.nsol;
+            mb->mr_ssk = nd * nd;
+            mb->mr_si = R.nsol * (1 + nd * nd);
+            mb->mr_sik = nd * nd;
+            mb->mr_f = mb->mr_si + R.nfiu * nd * nd;
+            mb->mr_ff = 0;
+            mb->mr_fp = nd + 1;
+            mb->nmetric = mb->mr_f + R.nfe * (nd + 1);
+            m->curved = true;
+        } else {
+            mb->mr_f = 1 + nd * nd;
+            mb->mr_ff = nd + 1;
+            mb->nmetric = 1 + nd * nd + R.nfaces * (nd + 1);
+        }
         mb->etype = B.etype;
         mb->nelem = B.nelem;
         mb->ld = round_up(B.nelem, 32);
@@ -1256,7 +1301,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         m->Ftot += (int64_t)R.nfe * mb->ld;
         m->ndof += (int64_t)R.nsol * m->nvar * B.nelem;
         canon += (int64_t)R.nfe * B.nelem;
-        if (ctx->etypes[B.etype]->desc.scheme != SDRT_SCHEME_SDRT ||
+        if (ctx->etypes[B.etype]->desc.scheme != SDRT_SCHEME_SDRT || curved ||
             !fast_path_available(R.shape, R.nsol, nd, phys->system, phys->riemann))
             m->fast = false;
         if (phys->system == SDRT_ADVDIFF || phys->system == SDRT_NAVIER_STOKES) {
@@ -1310,9 +1355,17 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         }
     }
 
-    // Metrics, physical points.
+    // Metrics and physical points (paper Sec. 2: mapping, Jacobian and its
+    // inverse, evaluated analytically): affine blocks one value set per
+    // element, curved blocks (quadratic map, mapping.hpp) one per point where
+    // the method uses it (Sec. 2.1): 1/det J and S = det J J^{-1} at the
+    // solution points, S at the unique internal points, the normal and scale at
+    // the external points.
     struct HostBlk {
-        std::vector<double> J, Ji, det, xfe;   // per element
+        std::vector<double> Ji, det;           // affine: per element J^{-1}, det J
+        std::vector<double> h;                 // per element: largest |J_ij| (pairing tolerance)
+        std::vector<double> xfe;               // physical external points
+        std::vector<double> pn, pmag;          // curved: unit J^{-T} n~ and det J |J^{-T} n~| per external point
         std::vector<double> metric;            // [NM][ld]
         std::vector<uint8_t> glued;            // per (e, f)
     };
@@ -1322,38 +1375,106 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         const RefElement& R = ctx->etypes[B.etype]->R;
         MBlock& mb = *m->blocks[b];
         const int nv = shape_nverts(R.shape);
-        const int NM = 1 + nd * nd + R.nfaces * (nd + 1);
         HostBlk& H = hb[b];
-        H.J.resize((size_t)B.nelem * nd * nd);
+        H.h.resize(B.nelem);
+        H.xfe.resize((size_t)B.nelem * R.nfe * nd);
+        H.metric.assign((size_t)mb.nmetric * mb.ld, 0.0);
+        H.glued.assign((size_t)B.nelem * R.nfaces, 0);
+        auto row = [&](int k, int e) -> double& { return H.metric[(size_t)k * mb.ld + e]; };
+        if (mb.curved) {
+            const int NN = map_nnodes(R.shape);
+            // shape functions and gradients at a reference point set
+            auto table = [&](const std::vector<double>& X, std::vector<double>& N, std::vector<double>& dN) {
+                const size_t np = X.size() / nd;
+                N.resize(np * NN);
+                dN.resize(np * NN * nd);
+                for (size_t q = 0; q < np; ++q) map_shape(R.shape, &X[q * nd], &N[q * NN], &dN[q * NN * nd]);
+            };
+            std::vector<double> Ns, dNs, Nk, dNk, Nf, dNf;
+            table(R.xs, Ns, dNs);
+            table(R.xfiu, Nk, dNk);
+            table(R.xfe, Nf, dNf);
+            H.pn.resize((size_t)B.nelem * R.nfe * nd);
+            H.pmag.resize((size_t)B.nelem * R.nfe);
+            for (int e = 0; e < B.nelem; ++e) {
+                const double* Xn = nodes[b] + (size_t)e * NN * nd;
+                // x and J (J[i * nd + d] = dx_i / dx~_d) at point q of a table; det and J^{-1}
+                double x[3], J[9], Ji[9];
+                auto at = [&](const std::vector<double>& N, const std::vector<double>& dN, int q) {
+                    for (int i = 0; i < nd; ++i) {
+                        x[i] = 0;
+                        for (int d = 0; d < nd; ++d) J[i * nd + d] = 0;
+                        for (int k = 0; k < NN; ++k) {
+                            const double X = Xn[(size_t)k * nd + i];
+                            x[i] += X * N[(size_t)q * NN + k];
+                            for (int d = 0; d < nd; ++d) J[i * nd + d] += X * dN[((size_t)q * NN + k) * nd + d];
+                        }
+                    }
+                    for (int k = 0; k < nd * nd; ++k) H.h[e] = std::max(H.h[e], std::fabs(J[k]));
+                    return det_inv(J, nd, Ji);
+                };
+                H.h[e] = 0;
+                for (int sp = 0; sp < R.nsol; ++sp) {
+                    const double det = at(Ns, dNs, sp);
+                    if (!(det > 0)) return fail(ctx, SDRT_ERR_MESH, "inverted or degenerate element");
+                    row(sp * mb.mr_inv, e) = 1.0 / det;
+                    for (int k = 0; k < nd * nd; ++k) row(mb.mr_ss + sp * mb.mr_ssk + k, e) = det * Ji[k];
+                    for (int i = 0; i < nd; ++i) m->sol_xyz.push_back(x[i]);
+                }
+                for (int q = 0; q < R.nfiu; ++q) {
+                    const double det = at(Nk, dNk, q);
+                    if (!(det > 0)) return fail(ctx, SDRT_ERR_MESH, "inverted or degenerate element");
+                    for (int k = 0; k < nd * nd; ++k) row(mb.mr_si + q * mb.mr_sik + k, e) = det * Ji[k];
+                }
+                for (int sg = 0; sg < R.nfe; ++sg) {
+                    const double det = at(Nf, dNf, sg);
+                    if (!(det > 0)) return fail(ctx, SDRT_ERR_MESH, "inverted or degenerate element");
+                    const size_t pt = (size_t)e * R.nfe + sg;
+                    const int f = R.fe_face[sg];
+                    double nrm = 0;
+                    for (int i = 0; i < nd; ++i) {
+                        double c = 0;
+                        for (int d = 0; d < nd; ++d) c += Ji[d * nd + i] * R.face_nrm[f * nd + d];
+                        H.pn[pt * nd + i] = c;
+                        nrm += c * c;
+                        H.xfe[pt * nd + i] = x[i];
+                    }
+                    nrm = std::sqrt(nrm);
+                    for (int i = 0; i < nd; ++i) H.pn[pt * nd + i] /= nrm;
+                    H.pmag[pt] = det * nrm;
+                }
+            }
+            continue;
+        }
         H.Ji.resize((size_t)B.nelem * nd * nd);
         H.det.resize(B.nelem);
-        H.xfe.resize((size_t)B.nelem * R.nfe * nd);
-        H.metric.assign((size_t)NM * mb.ld, 0.0);
-        H.glued.assign((size_t)B.nelem * R.nfaces, 0);
         const auto& ref = ref_vertices(R.shape);
         for (int e = 0; e < B.nelem; ++e) {
             const double* X = B.verts + (size_t)e * nv * nd;
-            double* J = &H.J[(size_t)e * nd * nd];
+            double J[9];
             double* Ji = &H.Ji[(size_t)e * nd * nd];
             if (!element_jacobian(R.shape, X, nd, J))
                 return fail(ctx, SDRT_ERR_UNSUPPORTED, "element " + std::to_string(e) + " of block " +
-                                                           std::to_string(b) + " is not affine");
+                                                           std::to_string(b) +
+                                                           " is not affine (curved elements: sdrt_setup_mesh_curved)");
             double det = det_inv(J, nd, Ji);
             if (!(det > 0)) return fail(ctx, SDRT_ERR_MESH, "inverted or degenerate element");
             H.det[e] = det;
-            H.metric[e] = 1.0 / det;
+            H.h[e] = 0;
+            for (int k = 0; k < nd * nd; ++k) H.h[e] = std::max(H.h[e], std::fabs(J[k]));
+            row(0, e) = 1.0 / det;
             for (int d = 0; d < nd; ++d)
-                for (int i = 0; i < nd; ++i) H.metric[(size_t)(1 + d * nd + i) * mb.ld + e] = det * Ji[d * nd + i];
-            for (int s = 0; s < R.nfe; ++s)
+                for (int i = 0; i < nd; ++i) row(1 + d * nd + i, e) = det * Ji[d * nd + i];
+            for (int sg = 0; sg < R.nfe; ++sg)
                 for (int i = 0; i < nd; ++i) {
                     double x = X[i];
-                    for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (R.xfe[s * nd + d] - ref[d]);
-                    H.xfe[((size_t)e * R.nfe + s) * nd + i] = x;
+                    for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (R.xfe[sg * nd + d] - ref[d]);
+                    H.xfe[((size_t)e * R.nfe + sg) * nd + i] = x;
                 }
-            for (int s = 0; s < R.nsol; ++s)
+            for (int sp = 0; sp < R.nsol; ++sp)
                 for (int i = 0; i < nd; ++i) {
                     double x = X[i];
-                    for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (R.xs[s * nd + d] - ref[d]);
+                    for (int d = 0; d < nd; ++d) x += J[i * nd + d] * (R.xs[sp * nd + d] - ref[d]);
                     m->sol_xyz.push_back(x);
                 }
         }
@@ -1362,9 +1483,19 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
     // Face pairing.
     m->partner.assign(m->nfe_total, -1);
     m->is_left.assign(m->nfe_total, 0);
-    auto face_normal = [&](int b, int e, int f, double* n, double& mag) {
+    // Unit physical normal J^{-T} n~ / |J^{-T} n~| and scale det J |J^{-T} n~|
+    // at external point sg of element e of block b.
+    auto point_normal = [&](int b, int e, int sg, double* n, double& mag) {
         const RefElement& R = ctx->etypes[blocks[b].etype]->R;
-        const double* Ji = &hb[b].Ji[(size_t)e * nd * nd];
+        const HostBlk& H = hb[b];
+        if (m->blocks[b]->curved) {
+            const size_t pt = (size_t)e * R.nfe + sg;
+            for (int i = 0; i < nd; ++i) n[i] = H.pn[pt * nd + i];
+            mag = H.pmag[pt];
+            return;
+        }
+        const int f = R.fe_face[sg];
+        const double* Ji = &H.Ji[(size_t)e * nd * nd];
         double s = 0;
         for (int i = 0; i < nd; ++i) {
             n[i] = 0;
@@ -1373,7 +1504,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         }
         s = std::sqrt(s);
         for (int i = 0; i < nd; ++i) n[i] /= s;
-        mag = hb[b].det[e] * s;
+        mag = H.det[e] * s;
     };
     for (int64_t fi = 0; fi < nfaces; ++fi) {
         const sdrt_face& F = faces[fi];
@@ -1395,10 +1526,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         for (int s = 0; s < RR.nfe; ++s)
             if (RR.fe_face[s] == F.face_r) iR.push_back(s);
         if (iL.size() != iR.size()) return fail(ctx, SDRT_ERR_MESH, "glued faces have different point counts");
-        const double* JL = &hb[F.blk_l].J[(size_t)F.elem_l * nd * nd];
-        double h = 0;
-        for (int k = 0; k < nd * nd; ++k) h = std::max(h, std::fabs(JL[k]));
-        const double tol = 1e-8 * h;
+        const double tol = 1e-8 * hb[F.blk_l].h[F.elem_l];
         std::vector<char> used(iR.size(), 0);
         const MBlock& bl = *m->blocks[F.blk_l];
         const MBlock& br = *m->blocks[F.blk_r];
@@ -1417,23 +1545,26 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
             }
             if (hit < 0) return fail(ctx, SDRT_ERR_MESH, "face flux points do not coincide (face " + std::to_string(fi) + ")");
             used[hit] = 1;
-            int64_t gL = bl.canon_base + (int64_t)F.elem_l * RL.nfe + iL[a];
-            int64_t gR = br.canon_base + (int64_t)F.elem_r * RR.nfe + iR[hit];
+            const int sL = iL[a], sR = iR[hit];
+            int64_t gL = bl.canon_base + (int64_t)F.elem_l * RL.nfe + sL;
+            int64_t gR = br.canon_base + (int64_t)F.elem_r * RR.nfe + sR;
             m->partner[gL] = (int32_t)gR;
             m->partner[gR] = (int32_t)gL;
             m->is_left[gL] = 1;
+            // Face metric: the L side's unit normal on both sides; each side's
+            // own scale, signed (+ on the L side).
+            double nL[3], nR[3], magL, magR;
+            point_normal(F.blk_l, F.elem_l, sL, nL, magL);
+            point_normal(F.blk_r, F.elem_r, sR, nR, magR);
+            const int rl = bl.mr_f + F.face_l * bl.mr_ff + sL * bl.mr_fp;
+            const int rr = br.mr_f + F.face_r * br.mr_ff + sR * br.mr_fp;
+            for (int c = 0; c < nd; ++c) {
+                hb[F.blk_l].metric[(size_t)(rl + c) * bl.ld + F.elem_l] = nL[c];
+                hb[F.blk_r].metric[(size_t)(rr + c) * br.ld + F.elem_r] = nL[c];
+            }
+            hb[F.blk_l].metric[(size_t)(rl + nd) * bl.ld + F.elem_l] = magL;
+            hb[F.blk_r].metric[(size_t)(rr + nd) * br.ld + F.elem_r] = -magR;
         }
-        // Face metric: the L side's unit normal for both sides; signed scales.
-        double nL[3], nR[3], magL, magR;
-        face_normal(F.blk_l, F.elem_l, F.face_l, nL, magL);
-        face_normal(F.blk_r, F.elem_r, F.face_r, nR, magR);
-        const int NDD = 1 + nd * nd;
-        for (int c = 0; c < nd; ++c) {
-            hb[F.blk_l].metric[(size_t)(NDD + F.face_l * (nd + 1) + c) * bl.ld + F.elem_l] = nL[c];
-            hb[F.blk_r].metric[(size_t)(NDD + F.face_r * (nd + 1) + c) * br.ld + F.elem_r] = nL[c];
-        }
-        hb[F.blk_l].metric[(size_t)(NDD + F.face_l * (nd + 1) + nd) * bl.ld + F.elem_l] = magL;
-        hb[F.blk_r].metric[(size_t)(NDD + F.face_r * (nd + 1) + nd) * br.ld + F.elem_r] = -magR;
     }
     for (int b = 0; b < nown; ++b)     // ghost elements keep their other faces unglued
         for (uint8_t g : hb[b].glued)
@@ -1467,7 +1598,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         if (m->fast) {
             // Record-path tables: metric rows per element, partner face-record
             // offsets, partner permutations, point offsets inside a record.
-            const int NM = 1 + nd * nd + R.nfaces * (nd + 1);
+            const int NM = mb.nmetric;
             std::vector<double> maos((size_t)mb.nelem * mb.nmp, 0.0);
             for (int e = 0; e < mb.nelem; ++e)
                 for (int k = 0; k < NM; ++k) maos[(size_t)e * mb.nmp + k] = hb[b].metric[(size_t)k * mb.ld + e];
@@ -1583,8 +1714,8 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
     // Operator-specialised path: FP32 3D Euler / Rusanov on whole meshes of
     // SDRT element types that have generated kernels and are not on the
     // record path.
-    if (!ghost && !m->fast && f32 && phys->system == SDRT_EULER && nd == 3 && phys->riemann == SDRT_RUSANOV &&
-        (int64_t)m->nfe_total * m->nvar < INT32_MAX) {
+    if (!ghost && !m->fast && !m->curved && f32 && phys->system == SDRT_EULER && nd == 3 &&
+        phys->riemann == SDRT_RUSANOV && (int64_t)m->nfe_total * m->nvar < INT32_MAX) {
         bool all = true;
         for (auto& bp : m->blocks) {
             const EType& et = *ctx->etypes[bp->etype];
@@ -1635,7 +1766,7 @@ int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out) {
     out->ndof = m.ndof;
     out->nfe_total = m.nfe_total;
     out->path = m.fast ? SDRT_PATH_RECORD : (m.gen && ctx->use_gen) ? SDRT_PATH_GENERATED : SDRT_PATH_GENERIC;
-    out->reserved = 0;
+    out->curved = m.curved ? 1 : 0;
     return SDRT_OK;
 }
 
@@ -2067,6 +2198,8 @@ int sdrt_tgv_diagnostics(sdrt_ctx* ctx, int mesh_id, const void* U, double rho_i
     Mesh& m = *ctx->meshes[mesh_id];
     if (m.phys.system != SDRT_NAVIER_STOKES || m.nd != 3)
         return fail(ctx, SDRT_ERR_UNSUPPORTED, "the Taylor-Green diagnostics need a 3D Navier-Stokes mesh");
+    if (m.curved)
+        return fail(ctx, SDRT_ERR_UNSUPPORTED, "the Taylor-Green diagnostics take affine elements (one det J each)");
     if ((r = ensure_workspace(ctx, m, false, false))) return r;
     if ((r = rk54_workspace(ctx, m, false))) return r;
     const size_t es = m.phys.precision == SDRT_FP32 ? 4 : 8;

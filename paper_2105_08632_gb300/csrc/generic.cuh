@@ -308,8 +308,10 @@ __device__ __forceinline__ void internal_flux(const S* u, const T* Srow, const K
 // base + (m0 + i) * rstride.  Loads are issued before stores (the state arrays
 // are distinct but the compiler cannot prove it).
 template <typename T>
-__device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const T* acc, T inv, size_t base, size_t rstride,
-                                              int m0, int nrows) {
+__device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const T* acc, const T* minv, size_t istride,
+                                              size_t base, size_t rstride, int m0, int nrows) {
+    // minv: 1/det J of solution point 0; point m at minv[m * istride] (0: one value)
+    const T inv0 = -__ldg(minv);
     T a[kMR], b[kMR];
     const bool need_u0 = E.mode == EPI_RK_FIRST || E.mode == EPI_RK_MID;
     const bool need_acc = E.mode == EPI_RK_MID || E.mode == EPI_RK_LAST;
@@ -325,6 +327,7 @@ __device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const T* acc, T 
     for (int i = 0; i < kMR; ++i) {
         if (m0 + i >= nrows) continue;
         const size_t idx = base + (size_t)(m0 + i) * rstride;
+        const T inv = istride ? -__ldg(minv + (size_t)(m0 + i) * istride) : inv0;
         const T r = acc[i] * inv;
         bad |= !isfinite(r);
         switch (E.mode) {
@@ -343,12 +346,14 @@ __device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const T* acc, T 
     if (bad) atomicOr(E.flag, 1);
 }
 template <typename T>
-__device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const Dual<T>* acc, T inv, size_t base,
-                                              size_t rstride, int m0, int nrows) {
+__device__ __forceinline__ void epilogue_rows(const KEpi<T>& E, const Dual<T>* acc, const T* minv, size_t istride,
+                                              size_t base, size_t rstride, int m0, int nrows) {
+    const T inv0 = -__ldg(minv);
     bool bad = false;
     #pragma unroll
     for (int i = 0; i < kMR; ++i) {
         if (m0 + i >= nrows) continue;
+        const T inv = istride ? -__ldg(minv + (size_t)(m0 + i) * istride) : inv0;
         const T d = acc[i].d * inv;
         bad |= !isfinite(d);
         E.out[base + (size_t)(m0 + i) * rstride] = d;
@@ -404,7 +409,6 @@ __global__ void __launch_bounds__(256, (std::is_same<S, float>::value && (SYS ==
                                                   const T* __restrict__ UFE, const T* __restrict__ dUFE, int64_t Ftot,
                                                   KPhys<T> P, KEpi<T> E, KVisc<T> Q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int ND2 = ND * ND;
     constexpr bool dual = !std::is_same<S, T>::value;
     constexpr int kind = dual ? TK_RES_DUAL : TK_RES;
     for (int gt = blockIdx.x;; gt += gridDim.x) {
@@ -434,7 +438,7 @@ __global__ void __launch_bounds__(256, (std::is_same<S, float>::value && (SYS ==
             const int te = it - sg * TE;
             const int e = min(e0 + te, B.nelem - 1);
             const int f = __ldg(B.fe_face + sg);
-            const int mrow = 1 + ND2 + f * (ND + 1);
+            const int mrow = B.mr_f + f * B.mr_ff + sg * B.mr_fp;
             T n[ND];
             #pragma unroll
             for (int c = 0; c < ND; ++c) n[c] = __ldg(B.metric + (size_t)(mrow + c) * B.ld + e);
@@ -493,7 +497,8 @@ __global__ void __launch_bounds__(256, (std::is_same<S, float>::value && (SYS ==
                 const int ax = dofs[q] >> 16;
                 T Srow[ND];
                 #pragma unroll
-                for (int i = 0; i < ND; ++i) Srow[i] = __ldg(B.metric + (size_t)(1 + ax * ND + i) * B.ld + e);
+                for (int i = 0; i < ND; ++i)
+                    Srow[i] = __ldg(B.metric + (size_t)(B.mr_si + k * B.mr_sik + ax * ND + i) * B.ld + e);
                 S Ft[V];
                 internal_flux<SYS, ND>(u, Srow, P, Ft);
                 if constexpr (is_viscous<SYS>()) {
@@ -512,8 +517,8 @@ __global__ void __launch_bounds__(256, (std::is_same<S, float>::value && (SYS ==
                         [&](int m0, int col, const S* acc) {
                             const int v = col / TE, te = col - v * TE, e = e0 + te;
                             if (e >= B.nelem) return;
-                            const T inv = -__ldg(B.metric + e);
-                            epilogue_rows(E, acc, inv, (size_t)B.u_off + (size_t)v * B.ld + e,
+                            epilogue_rows(E, acc, B.metric + e,
+                                          (size_t)B.mr_inv * B.ld, (size_t)B.u_off + (size_t)v * B.ld + e,
                                           (size_t)V * B.ld, m0, B.nsol);
                         });
     }

@@ -13,11 +13,16 @@ enum Riemann { RIE_UPWIND = 0, RIE_RUSANOV = 1, RIE_ROE = 2 };
 // State arrays: value (rho, v, e) of the block at u_off + (rho * V + v) * ld + e.
 // External-point arrays ("face states", UFE): value (sigma, v, e) at
 //   v * F_tot + fe_base + sigma * ld + e   (F_tot = sum of nfe * ld over blocks).
-// Metric rows (k, e) at metric[k * ld + e]:
-//   k = 0                    1 / det J
-//   k = 1 + d * ND + i       S_di = det J * (J^{-1})_di = det J dx~_d / dx_i
-//   k = 1 + ND^2 + f(ND+1)+c unit normal n_L of face f (the face's L side), c < ND
-//   k = 1 + ND^2 + f(ND+1)+ND  signed scale s = +-det J |J^{-T} n~_f| (+ on the L side)
+// Metric rows (k, e) at metric[k * ld + e] hold, at the points where the
+// method evaluates them (paper Sec. 2.1):
+//   1 / det J at each solution point,
+//   S_di = det J * (J^{-1})_di = det J dx~_d / dx_i at each solution point
+//        (physical gradients) and each unique internal flux point (fluxes),
+//   the unit normal n_L of the face's L side (c < ND) and the signed scale
+//        s = +-det J |J^{-T} n~| (+ on the L side) at each external point.
+// Affine elements have one value of each per element (rows: 1/det J at 0,
+// S_di at 1 + d * ND + i, face f at 1 + ND^2 + f (ND + 1) + c), curved ones
+// one per point; the row of each quantity is given by the mr_* fields.
 template <typename T>
 struct KBlock {
     int nsol, nfe, nfi, nfiu, nfaces;
@@ -38,6 +43,11 @@ struct KBlock {
     const int* fe_face;  // [nfe] local face of each external point
     const int* fi_tab;   // [nfiu][4]: count, then (nu | axis << 16) per internal DOF of the point
     const T* metric;     // [NM][ld]
+    // Metric row addressing (affine: strides 0, curved: one row set per point):
+    int mr_inv;          // 1/det J at solution point s: row s * mr_inv
+    int mr_ss, mr_ssk;   // S_di at solution point s: row mr_ss + s * mr_ssk + d * ND + i
+    int mr_si, mr_sik;   // S_di at unique internal point k: row mr_si + k * mr_sik + d * ND + i
+    int mr_f, mr_ff, mr_fp;  // normal / scale of external point sigma on face f: mr_f + f * mr_ff + sigma * mr_fp + c
     const int* map;      // [nfe][ld] UFE index (without the v * F_tot term) of the paired point
     const T* Air;        // interpolation operator row-major: [Mir][Md_pad], rows [M0; M12], Mir = Mi rounded to 4
     int Mir;

@@ -42,7 +42,6 @@ __global__ void __launch_bounds__(256) k_grad(KTable<T> tab, const T* __restrict
                                               KPhys<T> P, T* __restrict__ QFE, T* __restrict__ dQFE,
                                               T* __restrict__ QFIU, T* __restrict__ dQFIU, T* __restrict__ QSOL) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int ND2 = ND * ND;
     constexpr int kind = std::is_same<S, T>::value ? TK_GRAD : TK_GRAD_DUAL;
     for (int gt = blockIdx.x;; gt += gridDim.x) {
         int bi, tile;
@@ -63,7 +62,7 @@ __global__ void __launch_bounds__(256) k_grad(KTable<T> tab, const T* __restrict
             const int te = it - sg * TE;
             const int e = min(e0 + te, B.nelem - 1);
             const int f = __ldg(B.fe_face + sg);
-            const T s = __ldg(B.metric + (size_t)(1 + ND2 + f * (ND + 1) + ND) * B.ld + e);
+            const T s = __ldg(B.metric + (size_t)(B.mr_f + f * B.mr_ff + sg * B.mr_fp + ND) * B.ld + e);
             const T wo = s > T(0) ? T(0.5) - P.beta : T(0.5) + P.beta;   // own side is L when s > 0
             const T wn = T(1) - wo;
             S own[V], nbr[V];
@@ -91,15 +90,16 @@ __global__ void __launch_bounds__(256) k_grad(KTable<T> tab, const T* __restrict
             const int col = it - sp * NCOL;
             const int te = col % TE;
             const int e = min(e0 + te, B.nelem - 1);
-            const T inv = __ldg(B.metric + e);
+            const T inv = __ldg(B.metric + (size_t)sp * B.mr_inv * B.ld + e);
+            const T* Sp = B.metric + (size_t)(B.mr_ss + sp * B.mr_ssk) * B.ld + e;
             S qt[ND];
             #pragma unroll
             for (int d = 0; d < ND; ++d) qt[d] = RQ[(size_t)sp * QCOL + d * NCOL + col];
             #pragma unroll
             for (int i = 0; i < ND; ++i) {
-                S q = qt[0] * (__ldg(B.metric + (size_t)(1 + i) * B.ld + e) * inv);
+                S q = qt[0] * (__ldg(Sp + (size_t)i * B.ld) * inv);
                 #pragma unroll
-                for (int d = 1; d < ND; ++d) q = q + qt[d] * (__ldg(B.metric + (size_t)(1 + d * ND + i) * B.ld + e) * inv);
+                for (int d = 1; d < ND; ++d) q = q + qt[d] * (__ldg(Sp + (size_t)(d * ND + i) * B.ld) * inv);
                 RQ[(size_t)sp * QCOL + i * NCOL + col] = q;
                 if constexpr (std::is_same<S, T>::value) {
                     // optional copy of the solution-point gradients, [N_s][ND][V][ld] per block

@@ -38,13 +38,24 @@
 
 namespace sdrt {
 
-// GS = s * (-(1/det J) M14^T W) at the external points of a tile.
+// R[s][col] *= 1/det J at solution point s of the column's element: the W
+// tile scaled by the semi-discrete form's factor (one per element on affine
+// blocks, one per point on curved ones).
+template <typename T>
+__device__ __forceinline__ void scale_inv_det(const KBlock<T>& B, T* R, int e0, int TE, int NCOL) {
+    for (int it = threadIdx.x; it < B.nsol * NCOL; it += blockDim.x) {
+        const int sp = it / NCOL;
+        const int e = min(e0 + (it - sp * NCOL) % TE, B.nelem - 1);
+        R[it] *= __ldg(B.metric + (size_t)sp * B.mr_inv * B.ld + e);
+    }
+}
+
+// GS = s * (-M14^T (W / det J)) at the external points of a tile.
 template <typename T, int V, int ND>
 __global__ void __launch_bounds__(256) k_vjp_face(KTable<T> tab, const T* __restrict__ W, T* __restrict__ GS,
                                                   int64_t Ftot) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* RW = reinterpret_cast<T*>(smem_raw);
-    constexpr int ND2 = ND * ND;
     for (int gt = blockIdx.x;; gt += gridDim.x) {
         int bi, tile;
         if (!locate(tab, TK_VJP, gt, bi, tile)) break;
@@ -55,18 +66,19 @@ __global__ void __launch_bounds__(256) k_vjp_face(KTable<T> tab, const T* __rest
         __syncthreads();
         load_tile<T, T, V>(B, W, nullptr, e0, TE, RW);
         __syncthreads();
+        scale_inv_det(B, RW, e0, TE, NCOL);
+        __syncthreads();
         tile_gemm<T, T>(B.Adt, B.Mdt_pad, B.nfe, B.nsol, RW, B.nsol, RW, NCOL,
                         [&](int m0, int col, const T* acc) {
                             const int v = col / TE, te = col - v * TE, e = e0 + te;
                             if (e >= B.nelem) return;
-                            const T inv = __ldg(B.metric + e);
                             #pragma unroll
                             for (int i = 0; i < kMR; ++i) {
                                 const int m = m0 + i;
                                 if (m >= B.nfe) break;
                                 const int f = __ldg(B.fe_face + m);
-                                const T s = __ldg(B.metric + (size_t)(1 + ND2 + f * (ND + 1) + ND) * B.ld + e);
-                                GS[(size_t)v * Ftot + B.fe_base + (size_t)m * B.ld + e] = -(inv * s) * acc[i];
+                                const T s = __ldg(B.metric + (size_t)(B.mr_f + f * B.mr_ff + m * B.mr_fp + ND) * B.ld + e);
+                                GS[(size_t)v * Ftot + B.fe_base + (size_t)m * B.ld + e] = -s * acc[i];
                             }
                         });
     }
@@ -80,7 +92,6 @@ __global__ void __launch_bounds__(256) k_vjp_elem(KTable<T> tab, const T* __rest
                                                   KPhys<T> P, T* __restrict__ out, int* flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using D = Dual<T>;
-    constexpr int ND2 = ND * ND;
     for (int gt = blockIdx.x;; gt += gridDim.x) {
         int bi, tile;
         if (!locate(tab, TK_VJP, gt, bi, tile)) break;
@@ -106,15 +117,14 @@ __global__ void __launch_bounds__(256) k_vjp_elem(KTable<T> tab, const T* __rest
         __syncthreads();
         load_tile<T, T, V>(B, W, nullptr, e0, TE, RA);
         __syncthreads();
-        // Fb = -(1/det J) M13^T W
+        scale_inv_det(B, RA, e0, TE, NCOL);
+        __syncthreads();
+        // Fb = -M13^T (W / det J)
         tile_gemm<T, T>(B.Adt + nfe_pad, B.Mdt_pad, B.nfi, B.nsol, RA, B.nsol, RA, NCOL,
                         [&](int m0, int col, const T* acc) {
-                            const int te = col % TE;
-                            const int e = min(e0 + te, B.nelem - 1);
-                            const T inv = __ldg(B.metric + e);
                             #pragma unroll
                             for (int i = 0; i < kMR; ++i)
-                                if (m0 + i < B.nfi) RC[(size_t)(m0 + i) * NCOL + col] = -inv * acc[i];
+                                if (m0 + i < B.nfi) RC[(size_t)(m0 + i) * NCOL + col] = -acc[i];
                         });
         // External points: ub_fe = (dF / du_own)^T (GS_own + GS_partner).
         for (int it = threadIdx.x; it < B.nfe * TE; it += blockDim.x) {
@@ -122,7 +132,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem(KTable<T> tab, const T* __rest
             const int te = it - sg * TE;
             const int e = min(e0 + te, B.nelem - 1);
             const int f = __ldg(B.fe_face + sg);
-            const int mrow = 1 + ND2 + f * (ND + 1);
+            const int mrow = B.mr_f + f * B.mr_ff + sg * B.mr_fp;
             T n[ND];
             #pragma unroll
             for (int c = 0; c < ND; ++c) n[c] = __ldg(B.metric + (size_t)(mrow + c) * B.ld + e);
@@ -172,7 +182,8 @@ __global__ void __launch_bounds__(256) k_vjp_elem(KTable<T> tab, const T* __rest
                 const int ax = dofs[q] >> 16;
                 T Srow[ND], Fb[V];
                 #pragma unroll
-                for (int i = 0; i < ND; ++i) Srow[i] = __ldg(B.metric + (size_t)(1 + ax * ND + i) * B.ld + e);
+                for (int i = 0; i < ND; ++i)
+                    Srow[i] = __ldg(B.metric + (size_t)(B.mr_si + k * B.mr_sik + ax * ND + i) * B.ld + e);
                 #pragma unroll
                 for (int v = 0; v < V; ++v) Fb[v] = RC[(size_t)nu * NCOL + v * TE + te];
                 #pragma unroll
@@ -243,7 +254,6 @@ __global__ void __launch_bounds__(256) k_vjp_elem_visc(KTable<T> tab, const T* _
                                                        T* __restrict__ CB, T* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using D = Dual<T>;
-    constexpr int ND2 = ND * ND;
     for (int gt = blockIdx.x;; gt += gridDim.x) {
         int bi, tile;
         if (!locate(tab, TK_VJP, gt, bi, tile)) break;
@@ -273,15 +283,14 @@ __global__ void __launch_bounds__(256) k_vjp_elem_visc(KTable<T> tab, const T* _
         __syncthreads();
         load_tile<T, T, V>(B, W, nullptr, e0, TE, RA);
         __syncthreads();
-        // Fb = -(1/det J) M13^T W
+        scale_inv_det(B, RA, e0, TE, NCOL);
+        __syncthreads();
+        // Fb = -M13^T (W / det J)
         tile_gemm<T, T>(B.Adt + nfe_pad, B.Mdt_pad, B.nfi, B.nsol, RA, B.nsol, RA, NCOL,
                         [&](int m0, int col, const T* acc) {
-                            const int te = col % TE;
-                            const int e = min(e0 + te, B.nelem - 1);
-                            const T inv = __ldg(B.metric + e);
                             #pragma unroll
                             for (int i = 0; i < kMR; ++i)
-                                if (m0 + i < B.nfi) RC[(size_t)(m0 + i) * NCOL + col] = -inv * acc[i];
+                                if (m0 + i < B.nfi) RC[(size_t)(m0 + i) * NCOL + col] = -acc[i];
                         });
         // External points: (ub_fe, qb_fe) = (dF / d(u, q)_own)^T (GS_own + GS_partner).
         for (int it = threadIdx.x; it < B.nfe * TE; it += blockDim.x) {
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(256) k_vjp_elem_visc(KTable<T> tab, const T* _
             const int te = it - sg * TE;
             const int e = min(e0 + te, B.nelem - 1);
             const int f = __ldg(B.fe_face + sg);
-            const int mrow = 1 + ND2 + f * (ND + 1);
+            const int mrow = B.mr_f + f * B.mr_ff + sg * B.mr_fp;
             T n[ND];
             #pragma unroll
             for (int c = 0; c < ND; ++c) n[c] = __ldg(B.metric + (size_t)(mrow + c) * B.ld + e);
@@ -355,7 +364,8 @@ __global__ void __launch_bounds__(256) k_vjp_elem_visc(KTable<T> tab, const T* _
                 const int ax = dofs[j] >> 16;
                 T Srow[ND], Fb[V];
                 #pragma unroll
-                for (int i = 0; i < ND; ++i) Srow[i] = __ldg(B.metric + (size_t)(1 + ax * ND + i) * B.ld + e);
+                for (int i = 0; i < ND; ++i)
+                    Srow[i] = __ldg(B.metric + (size_t)(B.mr_si + k * B.mr_sik + ax * ND + i) * B.ld + e);
                 #pragma unroll
                 for (int v = 0; v < V; ++v) Fb[v] = RC[(size_t)nu * NCOL + v * TE + te];
                 #pragma unroll 1
@@ -396,15 +406,16 @@ __global__ void __launch_bounds__(256) k_vjp_elem_visc(KTable<T> tab, const T* _
             const int col = it - sp * NCOL;
             const int te = col % TE;
             const int e = min(e0 + te, B.nelem - 1);
-            const T inv = __ldg(B.metric + e);
+            const T inv = __ldg(B.metric + (size_t)sp * B.mr_inv * B.ld + e);
+            const T* Sp = B.metric + (size_t)(B.mr_ss + sp * B.mr_ssk) * B.ld + e;
             T qb[ND];
             #pragma unroll
             for (int i = 0; i < ND; ++i) qb[i] = QS[(size_t)sp * QCOL + i * NCOL + col];
             #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                T a = qb[0] * (__ldg(B.metric + (size_t)(1 + d * ND) * B.ld + e) * inv);
+                T a = qb[0] * (__ldg(Sp + (size_t)(d * ND) * B.ld) * inv);
                 #pragma unroll
-                for (int i = 1; i < ND; ++i) a = a + qb[i] * (__ldg(B.metric + (size_t)(1 + d * ND + i) * B.ld + e) * inv);
+                for (int i = 1; i < ND; ++i) a = a + qb[i] * (__ldg(Sp + (size_t)(d * ND + i) * B.ld) * inv);
                 QS[(size_t)sp * QCOL + d * NCOL + col] = a;
             }
         }
@@ -448,7 +459,6 @@ __global__ void __launch_bounds__(256) k_vjp_cbar(KTable<T> tab, const T* __rest
                                                   T* __restrict__ out, int* flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* RD = reinterpret_cast<T*>(smem_raw);
-    constexpr int ND2 = ND * ND;
     for (int gt = blockIdx.x;; gt += gridDim.x) {
         int bi, tile;
         if (!locate(tab, TK_VJP, gt, bi, tile)) break;
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(256) k_vjp_cbar(KTable<T> tab, const T* __rest
             const int te = it - sg * TE;
             const int e = min(e0 + te, B.nelem - 1);
             const int f = __ldg(B.fe_face + sg);
-            const bool left = __ldg(B.metric + (size_t)(1 + ND2 + f * (ND + 1) + ND) * B.ld + e) > T(0);
+            const bool left = __ldg(B.metric + (size_t)(B.mr_f + f * B.mr_ff + sg * B.mr_fp + ND) * B.ld + e) > T(0);
             const T wo = left ? T(0.5) - P.beta : T(0.5) + P.beta;
             const size_t oi = (size_t)B.fe_base + (size_t)sg * B.ld + e;
             const size_t pi = (size_t)__ldg(B.map + (size_t)sg * B.ld + e);

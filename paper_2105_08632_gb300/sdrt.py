@@ -27,7 +27,7 @@ EXPORTED = ["sdrt_create", "sdrt_destroy", "sdrt_last_error", "sdrt_set_stream",
             "sdrt_rk4_step", "sdrt_rk4_step_host", "sdrt_jvp", "sdrt_vjp", "sdrt_sync", "sdrt_launch_count",
             "sdrt_profile_enable", "sdrt_profile_collect", "sdrt_residual_noalloc", "sdrt_set_option",
             "sdrt_autotune", "sdrt_get_tiles", "sdrt_profile_collect_blocks", "sdrt_rk54_step",
-            "sdrt_rk54_adaptive_step", "sdrt_rk54_integrate", "sdrt_tgv_diagnostics"]
+            "sdrt_rk54_adaptive_step", "sdrt_rk54_integrate", "sdrt_tgv_diagnostics", "sdrt_setup_mesh_curved"]
 
 
 class SdrtError(RuntimeError):
@@ -67,7 +67,7 @@ class Face(ctypes.Structure):
 class MeshInfo(ctypes.Structure):
     _fields_ = [("nvar", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("ndim", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("state_len", ctypes.c_int64), ("ndof", ctypes.c_int64),
-                ("nfe_total", ctypes.c_int64), ("path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("nfe_total", ctypes.c_int64), ("path", ctypes.c_int32), ("curved", ctypes.c_int32)]
 
 
 class BlockLayout(ctypes.Structure):
@@ -98,6 +98,9 @@ def lib():
         "sdrt_get_operator": (I, [P, I, I, ctypes.POINTER(D), I64]),
         "sdrt_setup_mesh": (I, [P, ctypes.POINTER(Physics), I, ctypes.POINTER(Block), I64, ctypes.POINTER(Face),
                                 ctypes.POINTER(I)]),
+        "sdrt_setup_mesh_curved": (I, [P, ctypes.POINTER(Physics), I, ctypes.POINTER(Block),
+                                       ctypes.POINTER(ctypes.POINTER(D)), I64, ctypes.POINTER(Face),
+                                       ctypes.POINTER(I)]),
         "sdrt_get_mesh_info": (I, [P, I, ctypes.POINTER(MeshInfo)]),
         "sdrt_get_block_layout": (I, [P, I, I, ctypes.POINTER(BlockLayout)]),
         "sdrt_get_sol_points": (I, [P, I, ctypes.POINTER(D), I64]),
@@ -199,10 +202,11 @@ def sdrt_get_operator(ctx, etype, name):
     return out
 
 
-def sdrt_setup_mesh(ctx, physics, blocks, faces, ghost=None):
+def sdrt_setup_mesh(ctx, physics, blocks, faces, ghost=None, nodes=None):
     """physics: Physics struct; blocks: list of (etype_id, verts float64 (E, nv, ND));
     faces: int array (F, 6) and shift array (F, ND) as a tuple.  ghost: per-block
-    flags (uint8) -> sdrt_setup_partition."""
+    flags (uint8) -> sdrt_setup_partition.  nodes: per-block None or the curved
+    elements' quadratic-map nodes float64 (E, NN, ND) -> sdrt_setup_mesh_curved."""
     nb = len(blocks)
     barr = (Block * nb)()
     keep = []
@@ -210,6 +214,20 @@ def sdrt_setup_mesh(ctx, physics, blocks, faces, ghost=None):
         v = np.ascontiguousarray(verts, np.float64)
         keep.append(v)
         barr[i] = Block(int(et), int(v.shape[0]), v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if nodes is not None and any(x is not None for x in nodes):
+        if ghost is not None:
+            raise ValueError("partitions take affine elements")
+        if len(nodes) != nb:
+            raise ValueError("one node array (or None) per block")
+        narr = (ctypes.POINTER(ctypes.c_double) * nb)()
+        for i, x in enumerate(nodes):
+            if x is None:
+                continue
+            x = np.ascontiguousarray(x, np.float64)
+            if x.ndim != 3 or x.shape[0] != blocks[i][1].shape[0]:
+                raise ValueError("nodes of block %d: (nelem, nnode, ndim) expected" % i)
+            keep.append(x)
+            narr[i] = x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     fidx, shift = faces
     nf = len(fidx)
     farr = (Face * max(nf, 1))()
@@ -218,7 +236,10 @@ def sdrt_setup_mesh(ctx, physics, blocks, faces, ghost=None):
         s = list(shift[i]) + [0.0] * (3 - len(shift[i]))
         farr[i] = Face(int(r[0]), int(r[1]), int(r[2]), int(r[3]), int(r[4]), int(r[5]), (ctypes.c_double * 3)(*s))
     out = ctypes.c_int()
-    if ghost is None:
+    if nodes is not None and any(x is not None for x in nodes):
+        _check(ctx, lib().sdrt_setup_mesh_curved(ctx, ctypes.byref(physics), nb, barr, narr, nf, farr,
+                                                 ctypes.byref(out)))
+    elif ghost is None:
         _check(ctx, lib().sdrt_setup_mesh(ctx, ctypes.byref(physics), nb, barr, nf, farr, ctypes.byref(out)))
     else:
         g = np.ascontiguousarray(ghost, np.uint8)
@@ -431,7 +452,8 @@ class Context:
 
 
 class Mesh:
-    """A mesh set up in a Context: mesh dict from inputs.meshes plus physics."""
+    """A mesh set up in a Context: mesh dict from inputs.meshes plus physics.
+    Blocks with a "nodes" array hold curved elements (sdrt_setup_mesh_curved)."""
 
     def __init__(self, ctx, mesh, degree, physics, ghost=None, scheme="sdrt"):
         self.ctx = ctx
@@ -448,7 +470,8 @@ class Mesh:
             et = sdrt_setup_element_type(c, blk["shape"], p, scheme)
             self.etypes.append(et)
             blocks.append((et, blk["verts"]))
-        self.id = sdrt_setup_mesh(c, physics, blocks, (mesh["faces"], mesh["shift"]), ghost=ghost)
+        nodes = [blk.get("nodes") for blk in mesh["blocks"]]
+        self.id = sdrt_setup_mesh(c, physics, blocks, (mesh["faces"], mesh["shift"]), ghost=ghost, nodes=nodes)
         self.info = sdrt_get_mesh_info(c, self.id)
         self.layouts = [sdrt_get_block_layout(c, self.id, b) for b in range(self.info["nblocks"])]
         self.dtype_np = np.float32 if self.info["precision"] == 1 else np.float64

@@ -33,11 +33,14 @@ def perturb(U, seed, amp):
 
 
 def build_pair(ctx, kind, n, degree, system="euler", riemann="rusanov", precision="fp64", lo=0.0, hi=1.0,
-               a=(1.0, 0.5, 0.25), scheme="sdrt", **kw):
-    """Library Mesh and oracle (geom, physics) for the same seeded box mesh."""
+               a=(1.0, 0.5, 0.25), scheme="sdrt", curve=0.0, curve_seed=None, **kw):
+    """Library Mesh and oracle (geom, physics) for the same seeded box mesh;
+    curve > 0: curved elements, the box displaced by meshes.curved_mesh."""
     from paper_2105_08632_gb300 import sdrt
     nd = len(n)
     mesh = meshes.box_mesh(kind, n, [lo] * nd, [hi] * nd)
+    if curve:
+        mesh = meshes.curved_mesh(mesh, curve, curve_seed)
     phys = sdrt.make_physics(system, nd, riemann, precision, a=a, **kw)
     M = sdrt.Mesh(ctx, mesh, degree, phys, scheme=scheme)
     geom = omesh.build(mesh, degree)

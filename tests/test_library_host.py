@@ -180,3 +180,57 @@ def test_viscous_mesh_setup_on_host(hctx):
     with pytest.raises(sdrt.SdrtError) as ei:
         sdrt.sdrt_setup_mesh(hctx, sdrt.make_physics("advdiff", 3, "roe", "fp32", mu=0.01), blocks, faces)
     assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("kind,n,p", [("tet", (2, 2, 2), 2), ("hex", (2, 2, 2), 2), ("pri", (2, 2, 2), 3),
+                                      ("tri", (3, 3), 2), ("quad", (3, 2), 3)])
+def test_curved_mesh_on_host(hctx, kind, n, p):
+    """Curved elements (quadratic map): solution points at the oracle's mapped
+    points, the oracle's face map bit for bit, the curved flag."""
+    mesh = meshes.curved_mesh(meshes.box_mesh(kind, n, [0.0] * len(n), [1.0] * len(n)), 0.04, seed=7)
+    nd = len(n)
+    phys = sdrt.make_physics("euler", nd, "rusanov", "fp64")
+    blocks = [(sdrt.sdrt_setup_element_type(hctx, b["shape"], p), b["verts"]) for b in mesh["blocks"]]
+    mid = sdrt.sdrt_setup_mesh(hctx, phys, blocks, (mesh["faces"], mesh["shift"]),
+                               nodes=[b["nodes"] for b in mesh["blocks"]])
+    info = sdrt.sdrt_get_mesh_info(hctx, mid)
+    assert info["curved"] == 1 and info["path"] == 0
+    geom = omesh.build(mesh, p)
+    part, left = sdrt.sdrt_get_face_map(hctx, mid, info["nfe_total"])
+    assert np.array_equal(part.astype(np.int64), geom.partner)
+    assert np.array_equal(left.astype(bool), geom.is_left)
+    off = 0
+    flat = sdrt.sdrt_get_sol_points(hctx, mid, sum(g.nelem * g.ops.n_sol * nd for g in geom.blocks))
+    for g in geom.blocks:
+        k = g.nelem * g.ops.n_sol * nd
+        np.testing.assert_allclose(flat[off:off + k].reshape(g.xsol.shape), g.xsol, atol=1e-13)
+        off += k
+    # the straight mesh's info says affine
+    m0 = meshes.box_mesh(kind, n, [0.0] * nd, [1.0] * nd)
+    assert sdrt.sdrt_get_mesh_info(hctx, _lib_mesh(hctx, m0, p))["curved"] == 0
+
+
+def test_curved_mesh_errors(hctx):
+    mesh = meshes.curved_mesh(meshes.box_mesh("tet", (2, 2, 2), [0.0] * 3, [1.0] * 3), 0.04)
+    phys = sdrt.make_physics("euler", 3, "rusanov", "fp64")
+    et = sdrt.sdrt_setup_element_type(hctx, "tet", 2)
+    X = mesh["blocks"][0]["nodes"]
+    # an inverted element (two vertices swapped) is rejected
+    bad = X.copy()
+    bad[0, [0, 2]] = bad[0, [2, 0]]
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, phys, [(et, mesh["blocks"][0]["verts"])], (mesh["faces"], mesh["shift"]),
+                             nodes=[bad])
+    assert ei.value.code == -7
+    # displaced hexahedron vertices given to the affine entry: not affine
+    hm = meshes.curved_mesh(meshes.box_mesh("hex", (2, 2, 2), [0.0] * 3, [1.0] * 3), 0.04, seed=3)
+    eh = sdrt.sdrt_setup_element_type(hctx, "hex", 2)
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, phys, [(eh, hm["blocks"][0]["verts"])], (hm["faces"], hm["shift"]))
+    assert ei.value.code == -2
+    # FR-SDRT on curved elements is refused
+    efr = sdrt.sdrt_setup_element_type(hctx, "tet", 2, "fr")
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, phys, [(efr, mesh["blocks"][0]["verts"])], (mesh["faces"], mesh["shift"]),
+                             nodes=[X])
+    assert ei.value.code == -2
