@@ -9,8 +9,13 @@ arrays in the mesh's state layout (padding entries stay zero)."""
 
 
 def gmres(matvec, b, x0=None, tol=1e-10, restart=30, maxiter=300):
-    """Restarted GMRES (modified Gram-Schmidt Arnoldi, Givens rotations).
-    Returns (x, iterations, relative residual)."""
+    """Restarted GMRES.  The Arnoldi basis is a device matrix; each new vector
+    is orthogonalised by classical Gram-Schmidt with one re-orthogonalisation
+    (two pairs of matrix-vector products on the device), and only the new
+    Hessenberg column (k + 2 numbers) comes to the host, once per iteration,
+    for the Givens rotations and the convergence test.  Returns (x, iterations,
+    relative residual)."""
+    import numpy as np
     import torch
     x = torch.zeros_like(b) if x0 is None else x0.clone()
     bnorm = float(torch.linalg.vector_norm(b))
@@ -25,26 +30,29 @@ def gmres(matvec, b, x0=None, tol=1e-10, restart=30, maxiter=300):
         if rel <= tol:
             break
         m = min(restart, maxiter - it)
-        Q = [r / beta]
-        H = torch.zeros(m + 1, m, dtype=torch.float64)
-        cs = torch.zeros(m, dtype=torch.float64)
-        sn = torch.zeros(m, dtype=torch.float64)
-        g = torch.zeros(m + 1, dtype=torch.float64)
+        Q = torch.empty((m + 1, b.numel()), dtype=b.dtype, device=b.device)
+        Q[0] = r.reshape(-1) / beta
+        H = np.zeros((m + 1, m))
+        cs, sn, g = np.zeros(m), np.zeros(m), np.zeros(m + 1)
         g[0] = beta
         k_used = 0
         for k in range(m):
-            w = matvec(Q[k])
-            for i in range(k + 1):
-                H[i, k] = float(torch.dot(Q[i], w))
-                w = w - H[i, k] * Q[i]
-            H[k + 1, k] = float(torch.linalg.vector_norm(w))
-            if H[k + 1, k] > 0:
-                Q.append(w / H[k + 1, k])
+            w = matvec(Q[k].reshape(b.shape)).reshape(-1)
+            Qk = Q[:k + 1]
+            h = Qk @ w
+            w = w - Qk.T @ h
+            h2 = Qk @ w                                          # re-orthogonalisation
+            w = w - Qk.T @ h2
+            nrm = torch.linalg.vector_norm(w)
+            col = torch.cat([h + h2, nrm[None]]).cpu().numpy()   # the one transfer of the iteration
+            H[:k + 2, k] = col
+            if col[k + 1] > 0:
+                Q[k + 1] = w / nrm
             for i in range(k):                                   # previous rotations
                 t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
                 H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
                 H[i, k] = t
-            den = (H[k, k] ** 2 + H[k + 1, k] ** 2).sqrt()
+            den = np.hypot(H[k, k], H[k + 1, k])
             cs[k], sn[k] = H[k, k] / den, H[k + 1, k] / den
             H[k, k] = den
             H[k + 1, k] = 0.0
@@ -52,12 +60,11 @@ def gmres(matvec, b, x0=None, tol=1e-10, restart=30, maxiter=300):
             g[k] = cs[k] * g[k]
             k_used = k + 1
             it += 1
-            if abs(float(g[k + 1])) / bnorm <= tol or len(Q) <= k + 1:
+            if abs(g[k + 1]) / bnorm <= tol or col[k + 1] <= 0:
                 break
-        y = torch.linalg.solve_triangular(H[:k_used, :k_used], g[:k_used, None], upper=True)[:, 0]
-        for i in range(k_used):
-            x = x + float(y[i]) * Q[i]
-        rel = abs(float(g[k_used])) / bnorm
+        y = np.linalg.solve(np.triu(H[:k_used, :k_used]), g[:k_used])
+        x = x + (Q[:k_used].T @ torch.from_numpy(y).to(Q.device, Q.dtype)).reshape(b.shape)
+        rel = abs(g[k_used]) / bnorm
         if rel <= tol:
             break
     return x, it, rel
