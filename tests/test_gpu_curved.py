@@ -87,12 +87,15 @@ def test_curved_free_stream(ctx, p, precision):
     state = np.array([1.2, 0.3, -0.2, 0.1, 3.0])
     U = [np.repeat(state[None, :, None], g.nelem, 2).repeat(g.ops.n_sol, 0) for g in geom.blocks]
     R = _call(M, M.residual, U)
-    # zero up to rounding: within 128 u S of the oracle's zero, S the magnitude
-    # of the divergence's terms (u = 2^-24 in FP32, 2^-53 in FP64)
+    # zero up to rounding, in units of u S, S the magnitude of the divergence's
+    # terms: FP32 arithmetic within 128 u S (u = 2^-24); in FP64 (u = 2^-53) the
+    # operators' own construction error (Vandermonde inverses, condition ~1e3)
+    # dominates: the oracle's FP64 residual of a uniform state reaches 270 u S on
+    # affine degree-3 tetrahedra, so the bound is 4096 u S (~5e-13 S)
     _, S = ores.residual(geom, oph, U, terms=True)
-    u = gu.U32 if precision == "fp32" else 2.0 ** -53
+    u, bound = (gu.U32, 128) if precision == "fp32" else (2.0 ** -53, 4096)
     ratio = max(float(np.max(np.abs(r) / (u * s + 1e-300))) for r, s in zip(R, S))
-    assert ratio < 128, ratio
+    assert ratio < bound, ratio
 
 
 def test_curved_conservation(ctx):
