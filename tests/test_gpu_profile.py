@@ -8,7 +8,11 @@ pytestmark = pytest.mark.gpu
 from tests import gpu_util as gu  # noqa: E402
 
 
-def test_profile_counts_rk4_steps():
+@pytest.mark.parametrize("generated", [0, 1])
+def test_profile_counts_rk4_steps(generated):
+    """Generic kernels: one interpolation and one residual launch per stage.
+    Operator-specialised kernels: one interpolation per step (later stages
+    write the next stage's face records), one stage launch per stage."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2105_08632_gb300 import build, sdrt
@@ -16,14 +20,17 @@ def test_profile_counts_rk4_steps():
     stream = torch.cuda.Stream(0)
     with torch.cuda.stream(stream):
         ctx = sdrt.Context(0, stream.cuda_stream)
+        sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_GENERATED, generated)
         M, geom, oph, _ = gu.build_pair(ctx, "tet", (3, 3, 2), 2, "euler", "rusanov", "fp32")
+        assert sdrt.sdrt_get_mesh_info(ctx.ptr, M.id)["path"] == (2 if generated else 0)
+        n_interp = 1 if generated else 4
         U = torch.from_numpy(M.pack(gu.oracle_state(geom, gu.smooth_gas, 5))).to("cuda")
         M.rk4_step(U, 1e-3, 1)                 # eager warm-up step
         sdrt.sdrt_profile_enable(ctx.ptr, True)
         for _ in range(3):                     # graph captured on the first, replayed after
             M.rk4_step(U, 1e-3, 1)
             prof = sdrt.sdrt_profile_collect(ctx.ptr)
-            assert prof["interp_ext"][1] == 4 and prof["residual"][1] == 4
+            assert prof["interp_ext"][1] == n_interp and prof["residual"][1] == 4
             assert prof["residual"][0] > 0 and prof["interp_ext"][0] > 0
         R = torch.zeros_like(U)
         M.residual(U, R)
