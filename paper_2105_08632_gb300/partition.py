@@ -34,7 +34,8 @@ def bisection_owners(mesh, nparts, weights=None):
     partitions they will hold (weights: work per element, e.g. nsol x nvar per
     block; default 1).  Balanced to one element's weight for equal weights;
     the cuts are planes, so the exchanged faces are those of ~nparts^(1/d)
-    planes across the box."""
+    planes across the box.  With at least nparts elements no partition is
+    empty, however skewed the weights."""
     cents = np.concatenate([np.asarray(b["verts"], float).mean(axis=1) for b in mesh["blocks"]])
     n = len(cents)
     w = np.ones(n) if weights is None else np.asarray(weights, float)
@@ -50,6 +51,9 @@ def bisection_owners(mesh, nparts, weights=None):
         order = idx[np.lexsort((idx, c[:, axis]))]           # ties broken by element id
         cw = np.cumsum(w[order])
         k = int(np.searchsorted(cw, cw[-1] * left / count, side="right"))
+        if len(idx) >= count:
+            # skewed weights: each side keeps at least one element per partition
+            k = min(max(k, left), len(idx) - (count - left))
         cut(order[:k], first, left)
         cut(order[k:], first + left, count - left)
 

@@ -323,6 +323,26 @@ def test_bisection_owners_balance_and_cut(kinds, n, nparts):
     assert np.array_equal(owner, pt.bisection_owners(mesh, nparts))     # deterministic
 
 
+@pytest.mark.parametrize("nparts", [2, 5, 8])
+def test_bisection_owners_skewed_weights_leave_no_partition_empty(nparts):
+    """One element carrying almost all the weight: the weighted quantile alone
+    would put every other element on one side; the cut keeps at least one
+    element per partition on each side, and every element has an owner."""
+    mesh = meshes.box_mesh("tet", (2, 2, 1), [0.0] * 3, [1.0] * 3)       # 24 elements
+    n = sum(len(b["verts"]) for b in mesh["blocks"])
+    for heavy in (0, n // 2, n - 1):
+        w = np.ones(n)
+        w[heavy] = 1e6
+        owner = pt.bisection_owners(mesh, nparts, weights=w)
+        counts = np.bincount(owner, minlength=nparts)
+        assert len(counts) == nparts and counts.min() >= 1, counts
+        plans = pt.split(mesh, owner, nparts)                            # plans build for every partition
+        assert sum(len(ids) for pl in plans for _, ids in pl["owned"]) == n
+    # exactly as many elements as parts: one element each
+    owner = pt.bisection_owners(mesh, n, weights=np.arange(1.0, n + 1) ** 4)
+    assert sorted(owner.tolist()) == list(range(n))
+
+
 class _FakePart:
     """A partition of a 1D periodic upwind operator (du_i/dt = u_{i-1} - u_i)
     with the interface of PartitionMesh used by rk4_step_distributed: each rank
