@@ -413,7 +413,8 @@ int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U_dev, const void* W_dev, v
 /* Tile autotuner of the generic kernels (every element type other than the
  * register-blocked tetrahedra of degree 3 and 4, which have fixed tiles): for
  * each block in turn, times `reps` residual evaluations of the whole mesh at
- * U_dev (device state, not modified) for tile widths of 4..64 elements that
+ * U_dev (device state, not modified) for tile widths of 4, 8, 12, 16, 20, 24,
+ * 28, 32, 40, 48 and 64 elements (multiples of 4: 16-byte tile rows) that
  * fit in shared memory, and keeps the fastest (the residual kernel's tile,
  * and for the viscous systems the gradient kernel's).  Results are bit-for-bit
  * the same for every tile width (tiles only partition the elements).  Drops

@@ -2373,7 +2373,9 @@ int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
             const int keep = tile;
             int best = keep;
             float best_ms = 1e30f;
-            for (int te : {4, 8, 16, 32, 64}) {
+            // multiples of 4 (16-byte tile rows); the non-powers of two balance the
+            // tile GEMMs' 8 x 4 thread blocks over the CTA's threads for some shapes
+            for (int te : {4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 64}) {
                 const size_t smem = which == 0
                                         ? (size_t)(std::max(RE.nsol, RE.nfi) + et.Mi) * m.nvar * te * es
                                         : (size_t)(RE.nsol + RE.nfe + m.nd * RE.nsol) * m.nvar * te * es;
