@@ -98,6 +98,12 @@ def box_mesh(kinds, n, lo, hi):
             whole box, or a list of length n[-1] giving the kind of each slab of
             cells along the last axis (mixed meshes).
     n     : cells per axis (tuple of ND ints).
+
+    Elements: cells in lexicographic order (x fastest), within a cell in the
+    order of its subdivision, grouped into one block per shape (blocks in the
+    order the shapes first appear).  Faces: one row per glued pair, in the
+    order of the first appearance of the face (blocks, elements, local faces
+    in order); the first appearance is the L side.
     """
     n = tuple(int(v) for v in n)
     nd = len(n)
@@ -108,46 +114,71 @@ def box_mesh(kinds, n, lo, hi):
         kinds = [kinds] * n[-1]
     assert len(kinds) == n[-1]
 
-    blocks = {}       # shape -> list of integer corner arrays
-    order = []
-    for cell in itertools.product(*[range(k) for k in n[::-1]]):
-        cell = cell[::-1]                           # x fastest
-        shape, elems = _cell_elements(kinds[cell[-1]])
-        for corners in elems:
+    # cells in order, x fastest
+    grids = np.meshgrid(*[np.arange(k) for k in n], indexing="ij")
+    cells = np.stack([g.transpose(tuple(range(nd))[::-1]).ravel() for g in grids], axis=1)   # (Ncell, ND)
+    slab = cells[:, -1]
+    # (shape -> list of (sort key, integer corners)) over the cells of every kind
+    per_shape = {}
+    for kind in dict.fromkeys(kinds):
+        shape, elems = _cell_elements(kind)
+        sel = np.nonzero(np.array([kinds[z] == kind for z in range(n[-1])])[slab])[0]
+        for j, corners in enumerate(elems):
             assert _orient_ok(shape, corners), (shape, corners)
-            if shape not in blocks:
-                blocks[shape] = []
-                order.append(shape)
-            blocks[shape].append(np.array(corners, int) + np.array(cell, int))
-
-    out_blocks = []
-    int_blocks = []
+            iv = cells[sel][:, None, :] + np.asarray(corners, int)[None, :, :]
+            per_shape.setdefault(shape, []).append((sel * 16 + j, iv))
+    first = {s: min(int(k.min()) for k, _ in lst) for s, lst in per_shape.items()}
+    order = sorted(per_shape, key=lambda s: first[s])
+    int_blocks, out_blocks = [], []
     for shape in order:
-        iv = np.array(blocks[shape])                # (E, nv, ND) integer
+        keys = np.concatenate([k for k, _ in per_shape[shape]])
+        ivs = np.concatenate([v for _, v in per_shape[shape]])
+        iv = ivs[np.argsort(keys, kind="stable")]
         int_blocks.append((shape, iv))
         out_blocks.append({"shape": shape, "verts": lo + iv * h})
 
-    # Face adjacency through periodic integer keys.
-    table = {}
+    # Face adjacency through periodic integer keys: the vertex set modulo the
+    # box plus the centroid sum modulo the box (the vertex set alone aliases
+    # distinct faces when a box is 2 cells wide).
     nn = np.array(n)
+    radix = np.cumprod(np.concatenate([[1], nn[:-1]]))
+    recs = []          # (key rows, b, e, f, centroid)
     for b, (shape, iv) in enumerate(int_blocks):
-        for e in range(len(iv)):
-            for f, fv in enumerate(FACE_VERTS[shape]):
-                pts = iv[e, list(fv)]
-                # vertex set modulo the box, plus the centroid modulo the box (the
-                # vertex set alone aliases distinct faces when a box is 2 cells wide)
-                csum = tuple(int(c) for c in (pts.sum(axis=0) % (len(fv) * nn)))
-                key = (csum, tuple(sorted(tuple(int(c) for c in x) for x in (pts % nn))))
-                table.setdefault(key, []).append((b, e, f, pts.mean(axis=0)))
-    faces, shifts = [], []
-    for key, lst in table.items():
-        if len(lst) != 2:
-            raise ValueError(f"non-manifold or unmatched face {key}: {len(lst)}")
-        (bL, eL, fL, cL), (bR, eR, fR, cR) = lst
-        faces.append((bL, eL, fL, bR, eR, fR))
-        shifts.append(np.round((cL - cR) / nn) * nn * h)
-    return {"blocks": out_blocks, "faces": np.array(faces, np.int64),
-            "shift": np.array(shifts, float).reshape(-1, nd), "box": (lo, hi)}
+        E = len(iv)
+        for f, fv in enumerate(FACE_VERTS[shape]):
+            k = len(fv)
+            pts = iv[:, list(fv)]                                   # (E, k, ND)
+            csum = pts.sum(axis=1) % (k * nn)
+            codes = np.sort(((pts % nn) * radix).sum(axis=2), axis=1)
+            key = np.full((E, 1 + nd + 4), -1, np.int64)
+            key[:, 0] = k
+            key[:, 1:1 + nd] = csum
+            key[:, 1 + nd:1 + nd + k] = codes
+            recs.append((key, np.full(E, b), np.arange(E), np.full(E, f), pts.mean(axis=1)))
+    K = np.concatenate([r[0] for r in recs])
+    B = np.concatenate([r[1] for r in recs])
+    El = np.concatenate([r[2] for r in recs])
+    F = np.concatenate([r[3] for r in recs])
+    C = np.concatenate([r[4] for r in recs])
+    # appearance order: blocks, elements, local faces
+    seq = np.lexsort((F, El, B))
+    rank = np.empty(len(seq), np.int64)
+    rank[seq] = np.arange(len(seq))
+    srt = np.lexsort((rank,) + tuple(K[:, c] for c in range(K.shape[1] - 1, -1, -1)))   # by key, then appearance
+    Ks = K[srt]
+    same_next = np.all(Ks[1:] == Ks[:-1], axis=1)
+    starts = np.nonzero(np.concatenate([[True], ~same_next]))[0]
+    counts = np.diff(np.concatenate([starts, [len(srt)]]))
+    if np.any(counts != 2):
+        bad = starts[counts != 2][0]
+        raise ValueError(f"non-manifold or unmatched face {tuple(Ks[bad])}: {counts[counts != 2][0]}")
+    iL, iR = srt[starts], srt[starts + 1]                       # L: first appearance
+    pair_order = np.argsort(rank[iL], kind="stable")
+    iL, iR = iL[pair_order], iR[pair_order]
+    faces = np.stack([B[iL], El[iL], F[iL], B[iR], El[iR], F[iR]], axis=1).astype(np.int64)
+    shifts = np.round((C[iL] - C[iR]) / nn) * nn * h
+    return {"blocks": out_blocks, "faces": faces, "shift": np.asarray(shifts, float).reshape(-1, nd),
+            "box": (lo, hi)}
 
 
 def n_elements(mesh):
