@@ -25,7 +25,7 @@
  *    ld >= nelem is a multiple of 32 (the paper's state matrix, App. B Eq.
  *    "state_matrices", with the element index fastest).  Padding entries
  *    (nelem <= e < ld) are never read as data and never written.
- *    The element type is double (SDRT_FP64) or float (SDRT_FP32).
+ *    The element type is double (SDRT_FP64) or float (SDRT_FP32, SDRT_TF32X3).
  *  - Ordering of solution / flux points and local faces: see sdrt_point_order
  *    in the package documentation; it is the same convention as the mesh
  *    faces' local numbering documented at sdrt_face.
@@ -55,7 +55,15 @@ typedef enum {
 typedef enum { SDRT_TRI = 0, SDRT_QUAD = 1, SDRT_TET = 2, SDRT_PRI = 3, SDRT_HEX = 4 } sdrt_shape;
 typedef enum { SDRT_ADVECTION = 0, SDRT_ADVDIFF = 1, SDRT_EULER = 2, SDRT_NAVIER_STOKES = 3 } sdrt_system;
 typedef enum { SDRT_UPWIND = 0, SDRT_RUSANOV = 1, SDRT_ROE = 2 } sdrt_riemann;
-typedef enum { SDRT_FP64 = 0, SDRT_FP32 = 1 } sdrt_precision;
+/* Arithmetic of a mesh.  SDRT_TF32X3: FP32 states and the FP32 accuracy
+ * class, with the dense contractions of the record path (FP32 Euler /
+ * Rusanov tetrahedra of degree 3: the interpolation [M0; M12] U and the
+ * divergence [M14 | M13] F~) on the tensor cores, each product split into
+ * three TF32 products (hi hi + hi lo + lo hi) with FP32 accumulation
+ * (tcgen05); everything else runs the FP32 kernels.  It meets the same
+ * bounds as SDRT_FP32.  Plain TF32 (10-bit mantissa, ~5e-4 relative per
+ * product) would not, and is not offered. */
+typedef enum { SDRT_FP64 = 0, SDRT_FP32 = 1, SDRT_TF32X3 = 2 } sdrt_precision;
 
 /* Element type: reference element and degree p (paper App. A). */
 typedef struct {

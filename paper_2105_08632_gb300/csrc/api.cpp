@@ -98,6 +98,7 @@ struct Mesh {
     int64_t state_len = 0, Ftot = 0, ndof = 0, nfe_total = 0;
     bool fast = false;                // every block on the register-blocked record path
     bool curved = false;              // some block has curved elements (generic kernels only)
+    bool tc3 = false;                 // SDRT_TF32X3: tensor-core contractions where instantiated
     int64_t rec_total = 0, fiur_total = 0;
     int64_t qfiu_total = 0;           // viscous: length of QFIU
     std::vector<int32_t> partner;     // canonical face map
@@ -463,7 +464,7 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
             auto interp = [&](const T* X, T* rec_out, T* fiur_out) {
                 int r = -1;
                 if constexpr (std::is_same<T, float>::value) {
-                    if (ctx->use_tc && tc_interp_available(et.R.shape, et.R.nsol, m.nvar))
+                    if ((ctx->use_tc || m.tc3) && tc_interp_available(et.R.shape, et.R.nsol, m.nvar))
                         r = launch_interp_tc(K, m.nvar, X, rec_out, fiur_out, ctx->flag.as<int>(), ctx->nsm,
                                              ctx->stream);
                 }
@@ -492,7 +493,8 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
             const int s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
             int r = -1;
             if constexpr (std::is_same<T, float>::value) {
-                if (!dU && ctx->use_tc_div && tc_flux_available(et.R.shape, et.R.nsol, m.nvar, sys, m.phys.riemann))
+                if (!dU && (ctx->use_tc_div || m.tc3) &&
+                    tc_flux_available(et.R.shape, et.R.nsol, m.nvar, sys, m.phys.riemann))
                     r = launch_flux_tc(K, rec, fiur, P, E, ctx->nsm, ctx->stream);
             }
             if (r != 0)
@@ -593,7 +595,8 @@ int run_vjp(sdrt_ctx* ctx, Mesh& m, const T* U, const T* W, T* out) {
 // Whether stages 1-3 of RK4 can interpolate the next stage's state in their
 // epilogue (record path, FP32 Euler on tetrahedra of degree 3, CUDA-core kernels).
 bool rk_fusable(sdrt_ctx* ctx, const Mesh& m) {
-    if (!m.fast || m.phys.precision != SDRT_FP32 || ctx->use_tc || ctx->use_tc_div || !m.rec2.p || !m.fiur2.p)
+    if (!m.fast || m.phys.precision != SDRT_FP32 || ctx->use_tc || ctx->use_tc_div || m.tc3 || !m.rec2.p ||
+        !m.fiur2.p)
         return false;
     for (auto& bp : m.blocks)
         if (!flux_rec_fusable(make_kblock<float>(*ctx->etypes[bp->etype], *bp), m.nvar, m.phys.system)) return false;
@@ -1248,16 +1251,22 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         if (nown == 0) return fail(ctx, SDRT_ERR_ARG, "a partition needs an owned block");
     }
     if (phys->ndim != 2 && phys->ndim != 3) return fail(ctx, SDRT_ERR_ARG, "ndim must be 2 or 3");
-    if (phys->precision != SDRT_FP32 && phys->precision != SDRT_FP64) return fail(ctx, SDRT_ERR_ARG, "bad precision");
+    if (phys->precision != SDRT_FP32 && phys->precision != SDRT_FP64 && phys->precision != SDRT_TF32X3)
+        return fail(ctx, SDRT_ERR_ARG, "bad precision");
     if (phys->system < SDRT_ADVECTION || phys->system > SDRT_NAVIER_STOKES) return fail(ctx, SDRT_ERR_ARG, "bad system");
     const bool scalar = phys->system == SDRT_ADVECTION || phys->system == SDRT_ADVDIFF;
     if (scalar && phys->riemann == SDRT_ROE) return fail(ctx, SDRT_ERR_ARG, "Roe flux needs the Euler or Navier-Stokes system");
     auto m = std::make_unique<Mesh>();
     m->phys = *phys;
+    if (phys->precision == SDRT_TF32X3) {
+        // FP32 states; the record path's contractions on the tensor cores
+        m->tc3 = true;
+        m->phys.precision = SDRT_FP32;
+    }
     const int nd = phys->ndim;
     m->nd = nd;
     m->nvar = (phys->system == SDRT_ADVECTION || phys->system == SDRT_ADVDIFF) ? 1 : nd + 2;
-    const bool f32 = phys->precision == SDRT_FP32;
+    const bool f32 = m->phys.precision == SDRT_FP32;
 
     // Layout.
     int64_t canon = 0;
@@ -1311,7 +1320,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
         m->blocks.push_back(std::move(mb));
     }
     m->nfe_total = canon;
-    if (m->fast && ctx->use_gen == 2 && !ghost && f32 && phys->system == SDRT_EULER && nd == 3 &&
+    if (m->fast && ctx->use_gen == 2 && !ghost && f32 && !m->tc3 && phys->system == SDRT_EULER && nd == 3 &&
         phys->riemann == SDRT_RUSANOV) {
         // SDRT_OPT_GENERATED = 2: the operator-specialised kernels replace the record path.
         bool all = true;
@@ -1761,7 +1770,7 @@ int sdrt_get_mesh_info(sdrt_ctx* ctx, int mesh_id, sdrt_mesh_info* out) {
     out->nvar = m.nvar;
     out->nblocks = (int)m.blocks.size();
     out->ndim = m.nd;
-    out->precision = m.phys.precision;
+    out->precision = m.tc3 ? SDRT_TF32X3 : m.phys.precision;
     out->state_len = m.state_len;
     out->ndof = m.ndof;
     out->nfe_total = m.nfe_total;

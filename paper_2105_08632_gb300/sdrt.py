@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libsdrt.so")
 SHAPES = {"tri": 0, "quad": 1, "tet": 2, "pri": 3, "hex": 4}
 SYSTEMS = {"advection": 0, "advdiff": 1, "euler": 2, "ns": 3}
 RIEMANN = {"upwind": 0, "rusanov": 1, "roe": 2}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32x3": 2}
 STATUS = {0: "SDRT_OK", -1: "SDRT_ERR_ARG", -2: "SDRT_ERR_UNSUPPORTED", -3: "SDRT_ERR_CUDA",
           -4: "SDRT_ERR_STATE", -5: "SDRT_ERR_NONFINITE", -6: "SDRT_ERR_TIMEOUT", -7: "SDRT_ERR_MESH"}
 
@@ -474,7 +474,7 @@ class Mesh:
         self.id = sdrt_setup_mesh(c, physics, blocks, (mesh["faces"], mesh["shift"]), ghost=ghost, nodes=nodes)
         self.info = sdrt_get_mesh_info(c, self.id)
         self.layouts = [sdrt_get_block_layout(c, self.id, b) for b in range(self.info["nblocks"])]
-        self.dtype_np = np.float32 if self.info["precision"] == 1 else np.float64
+        self.dtype_np = np.float64 if self.info["precision"] == 0 else np.float32   # fp32 / tf32x3: FP32 states
 
     @property
     def state_len(self):

@@ -145,3 +145,31 @@ def test_fused_rk_stages_match_the_unfused_sequence(ctx, ncell):
     assert np.isfinite(out[1]).all()
     assert not np.array_equal(out[1], U0)
     assert np.array_equal(out[1], out[0])
+
+
+def test_tf32x3_precision_routes_to_the_tensor_cores(ctx):
+    """SDRT_TF32X3 through the boundary: FP32 states, the record path's
+    interpolation and divergence on the tensor cores -- the same results, bit
+    for bit, as an FP32 mesh with both tensor-core options on, and within the
+    FP32 parity bounds of the oracle (2e-4 / 2e-5)."""
+    from paper_2105_08632_gb300 import sdrt
+    mesh = meshes.box_mesh("tet", (3, 3, 3), [-5.0] * 3, [5.0] * 3)
+    geom = omesh.build(mesh, 3)
+    g = geom.blocks[0]
+    u = fields.isentropic_vortex(g.xsol.reshape(-1, 3), gamma=1.4, mach=0.5)
+    u = u * (1 + fields.uniform_noise(u.shape, 11, 1e-2))
+    U = [np.ascontiguousarray(u.reshape(g.nelem, g.ops.n_sol, 5).transpose(1, 2, 0))]
+    M3 = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "tf32x3", gamma=1.4))
+    assert M3.info["precision"] == 2 and M3.dtype_np == np.float32 and M3.info["path"] == 1
+    r3 = _residual(M3, U)
+    M1 = sdrt.Mesh(ctx, mesh, 3, sdrt.make_physics("euler", 3, "rusanov", "fp32", gamma=1.4))
+    _options(ctx, 1, 1)
+    try:
+        r_tc = _residual(M1, U)
+    finally:
+        _options(ctx, 0, 0)
+    r_fma = _residual(M1, U)
+    assert all(np.array_equal(a, b) for a, b in zip(r3, r_tc))
+    assert not all(np.array_equal(a, b) for a, b in zip(r3, r_fma))      # a different product split
+    linf, l2 = gu.rel_errors(r3, ores.residual(geom, ophx.Physics("euler", 3, "rusanov", gamma=1.4), U))
+    assert linf < TOL32[0] and l2 < TOL32[1], (linf, l2)

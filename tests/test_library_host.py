@@ -234,3 +234,23 @@ def test_curved_mesh_errors(hctx):
         sdrt.sdrt_setup_mesh(hctx, phys, [(efr, mesh["blocks"][0]["verts"])], (mesh["faces"], mesh["shift"]),
                              nodes=[X])
     assert ei.value.code == -2
+
+
+def test_tf32x3_precision_on_host(hctx):
+    """SDRT_TF32X3 meshes hold FP32 states (state length and layout of an FP32
+    mesh) and report their precision; other precision values are refused."""
+    mesh = meshes.box_mesh("tet", (2, 2, 2), [0.0] * 3, [1.0] * 3)
+    et = sdrt.sdrt_setup_element_type(hctx, "tet", 3)
+    blocks = [(et, mesh["blocks"][0]["verts"])]
+    infos = {}
+    for prec in ("fp32", "tf32x3"):
+        mid = sdrt.sdrt_setup_mesh(hctx, sdrt.make_physics("euler", 3, "rusanov", prec), blocks,
+                                   (mesh["faces"], mesh["shift"]))
+        infos[prec] = sdrt.sdrt_get_mesh_info(hctx, mid)
+    assert infos["tf32x3"]["precision"] == 2 and infos["fp32"]["precision"] == 1
+    assert infos["tf32x3"]["state_len"] == infos["fp32"]["state_len"]
+    bad = sdrt.make_physics("euler", 3, "rusanov", "fp32")
+    bad.precision = 3
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_setup_mesh(hctx, bad, blocks, (mesh["faces"], mesh["shift"]))
+    assert ei.value.code == -1
