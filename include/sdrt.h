@@ -481,6 +481,13 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     hook for the timeout path; 0 = the normal bound (about 2^26 polls).
  *     Changing it drops captured RK4 graphs. */
 #define SDRT_OPT_WAIT_POLLS 4
+/*   SDRT_OPT_NVTX (default 0): 1 = NVTX ranges (host-side markers for
+ *     profilers such as Nsight Compute's --nvtx filters) around the main entry
+ *     points (sdrt_residual, sdrt_rk4_step, sdrt_jvp, sdrt_vjp, the RK54 and
+ *     partitioned-residual calls, ...) and around every kernel launch, named by
+ *     the kernel's kind (interpolation, residual, residual_jvp, gradient).  No
+ *     effect on results; without an attached tool the markers cost a branch. */
+#define SDRT_OPT_NVTX 5
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 
 /* Per-launch device timing with CUDA events recorded on the context's stream

@@ -3,6 +3,7 @@
 #include "sdrt.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <array>
 
@@ -168,6 +169,7 @@ struct sdrt_ctx {
     bool fuse_rk = true;          // next-stage interpolation in the RK4 stage update (SDRT_OPT_FUSED_RK)
     int use_gen = 1;              // operator-specialised kernels where generated (SDRT_OPT_GENERATED)
     int wait_polls = 0;           // first copy wait of the record flux kernel (SDRT_OPT_WAIT_POLLS)
+    bool nvtx = false;            // NVTX ranges around entry points and kernel launches (SDRT_OPT_NVTX)
     void* noalloc_scratch = nullptr;   // device address of sdrt_residual_noalloc's static buffer
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
@@ -205,8 +207,26 @@ int new_slot(sdrt_ctx* ctx, int kind) {
 }
 
 // Start timing one launch: returns the slot (or -1 when profiling is off).
+const char* kind_name(int kind) {
+    static const char* names[KIND_COUNT] = {"interpolation", "residual", "residual_jvp", "gradient"};
+    const int k = kind & 0xff;
+    return k >= 0 && k < KIND_COUNT ? names[k] : "kernel";
+}
+
+// An NVTX range for the lifetime of an entry point's call (SDRT_OPT_NVTX).
+struct NvtxScope {
+    bool on;
+    NvtxScope(const sdrt_ctx* ctx, const char* name) : on(ctx && ctx->nvtx) {
+        if (on) nvtxRangePushA(name);
+    }
+    ~NvtxScope() {
+        if (on) nvtxRangePop();
+    }
+};
+
 int prof_begin(sdrt_ctx* ctx, int kind, cudaStream_t st = nullptr) {
     if (!st) st = ctx->stream;
+    if (ctx->nvtx) nvtxRangePushA(kind_name(kind));
     if (!ctx->prof) return -1;
     int s;
     if (ctx->capture_slots) {
@@ -231,6 +251,7 @@ int prof_begin(sdrt_ctx* ctx, int kind, cudaStream_t st = nullptr) {
 }
 
 void prof_end(sdrt_ctx* ctx, int s, cudaStream_t st = nullptr) {
+    if (ctx->nvtx) nvtxRangePop();
     if (s < 0) return;
     if (!st) st = ctx->stream;
     if (ctx->capture_slots) cudaEventRecordWithFlags(ctx->ev[2 * s + 1], st, cudaEventRecordExternal);
@@ -1810,6 +1831,7 @@ int sdrt_get_face_map(sdrt_ctx* ctx, int mesh_id, int32_t* partner, uint8_t* is_
 }
 
 int sdrt_residual(sdrt_ctx* ctx, int mesh_id, const void* U, void* R) {
+    NvtxScope nvtx_scope(ctx, "sdrt_residual");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !R || U == R) return fail(ctx, SDRT_ERR_ARG, "U and R must be distinct device arrays");
@@ -1942,6 +1964,7 @@ static int check_partition(sdrt_ctx* ctx, int mesh_id) {
 }
 
 int sdrt_residual_gradients(sdrt_ctx* ctx, int mesh_id, const void* recv, void* send_grad) {
+    NvtxScope nvtx_scope(ctx, "sdrt_residual_gradients");
     int r = check_partition(ctx, mesh_id);
     if (r) return r;
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1955,6 +1978,7 @@ int sdrt_residual_gradients(sdrt_ctx* ctx, int mesh_id, const void* recv, void* 
 }
 
 int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U, void* send) {
+    NvtxScope nvtx_scope(ctx, "sdrt_residual_begin");
     int r = check_partition(ctx, mesh_id);
     if (r) return r;
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1966,6 +1990,7 @@ int sdrt_residual_begin(sdrt_ctx* ctx, int mesh_id, const void* U, void* send) {
 }
 
 int sdrt_residual_end(sdrt_ctx* ctx, int mesh_id, const void* recv, void* R) {
+    NvtxScope nvtx_scope(ctx, "sdrt_residual_end");
     int r = check_partition(ctx, mesh_id);
     if (r) return r;
     Mesh& m = *ctx->meshes[mesh_id];
@@ -1982,6 +2007,7 @@ static int rk4_eager(sdrt_ctx* ctx, Mesh& m, void* U, double dt) {
 }
 
 int sdrt_rk4_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
+    NvtxScope nvtx_scope(ctx, "sdrt_rk4_step");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || nsteps < 0 || !(std::isfinite(dt))) return fail(ctx, SDRT_ERR_ARG, "bad argument");
@@ -2098,6 +2124,7 @@ int rk54_attempt(sdrt_ctx* ctx, Mesh& m, T* U, double dt, double atol, double rt
 extern "C" {
 
 int sdrt_rk54_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
+    NvtxScope nvtx_scope(ctx, "sdrt_rk54_step");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || nsteps < 0 || !(std::isfinite(dt))) return fail(ctx, SDRT_ERR_ARG, "bad argument");
@@ -2114,6 +2141,7 @@ int sdrt_rk54_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, int nsteps) {
 
 int sdrt_rk54_adaptive_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, double atol, double rtol, double* err,
                             double* dt_next, int* accepted) {
+    NvtxScope nvtx_scope(ctx, "sdrt_rk54_adaptive_step");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !err || !dt_next || !accepted || !(dt > 0) || !(atol > 0) || !(rtol >= 0))
@@ -2135,6 +2163,7 @@ int sdrt_rk54_adaptive_step(sdrt_ctx* ctx, int mesh_id, void* U, double dt, doub
 
 int sdrt_rk54_integrate(sdrt_ctx* ctx, int mesh_id, void* U, double t_span, double* dt_inout, double atol,
                         double rtol, int max_steps, int* n_accepted, int* n_rejected) {
+    NvtxScope nvtx_scope(ctx, "sdrt_rk54_integrate");
     if (!dt_inout || !n_accepted || !n_rejected || !(t_span >= 0) || max_steps < 1)
         return fail(ctx, SDRT_ERR_ARG, "bad argument");
     *n_accepted = *n_rejected = 0;
@@ -2201,6 +2230,7 @@ extern "C" {
 
 int sdrt_tgv_diagnostics(sdrt_ctx* ctx, int mesh_id, const void* U, double rho_inf, double v_inf, double length,
                          double* out) {
+    NvtxScope nvtx_scope(ctx, "sdrt_tgv_diagnostics");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !out || !(rho_inf > 0) || !(v_inf > 0) || !(length > 0)) return fail(ctx, SDRT_ERR_ARG, "bad argument");
@@ -2233,6 +2263,7 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     else if (option == SDRT_OPT_FUSED_RK) ctx->fuse_rk = value != 0;
     else if (option == SDRT_OPT_GENERATED) ctx->use_gen = value < 0 ? 0 : value > 2 ? 2 : value;
     else if (option == SDRT_OPT_WAIT_POLLS) ctx->wait_polls = value < 0 ? 0 : value;
+    else if (option == SDRT_OPT_NVTX) ctx->nvtx = value != 0;
     else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {
@@ -2290,6 +2321,7 @@ int sdrt_profile_collect(sdrt_ctx* ctx, double* ms_out, int64_t* count_out) {
 }
 
 int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* Uin, void* Uout, double dt, int nsteps) {
+    NvtxScope nvtx_scope(ctx, "sdrt_rk4_step_host");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!Uin || !Uout) return fail(ctx, SDRT_ERR_ARG, "null host buffer");
@@ -2304,6 +2336,7 @@ int sdrt_rk4_step_host(sdrt_ctx* ctx, int mesh_id, const void* Uin, void* Uout, 
 }
 
 int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* V, void* JV) {
+    NvtxScope nvtx_scope(ctx, "sdrt_jvp");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !V || !JV || JV == U || JV == V) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
@@ -2324,6 +2357,7 @@ int sdrt_jvp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* V, void* JV)
 }
 
 int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW) {
+    NvtxScope nvtx_scope(ctx, "sdrt_vjp");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || !W || !JTW || JTW == U || JTW == W) return fail(ctx, SDRT_ERR_ARG, "bad device arrays");
@@ -2339,6 +2373,7 @@ int sdrt_vjp(sdrt_ctx* ctx, int mesh_id, const void* U, const void* W, void* JTW
 }
 
 int sdrt_autotune(sdrt_ctx* ctx, int mesh_id, const void* U, int reps) {
+    NvtxScope nvtx_scope(ctx, "sdrt_autotune");
     int r = check_whole(ctx, mesh_id);
     if (r) return r;
     if (!U || reps < 1) return fail(ctx, SDRT_ERR_ARG, "null state or reps < 1");

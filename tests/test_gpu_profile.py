@@ -39,3 +39,29 @@ def test_profile_counts_rk4_steps(generated):
         sdrt.sdrt_profile_enable(ctx.ptr, False)
         M.sync()
         ctx.close()
+
+
+def test_nvtx_ranges_leave_results_unchanged():
+    """SDRT_OPT_NVTX: host-side markers only; the residual and RK4 steps are
+    bit-identical with and without them."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_08632_gb300 import build, sdrt
+    build.build()
+    ctx = sdrt.Context(0)
+    try:
+        M, geom, oph, _ = gu.build_pair(ctx, "hex", (3, 3, 2), 2, "ns", "rusanov", "fp32", mu=0.02)
+        U0 = torch.from_numpy(M.pack(gu.oracle_state(geom, gu.smooth_gas, 5))).to("cuda")
+        out = []
+        for nvtx in (0, 1):
+            sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_NVTX, nvtx)
+            U = U0.clone()
+            R = torch.zeros_like(U)
+            M.residual(U, R)
+            M.rk4_step(U, 1e-3, 2)
+            M.sync()
+            out.append((R, U))
+        sdrt.sdrt_set_option(ctx.ptr, sdrt.SDRT_OPT_NVTX, 0)
+        assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    finally:
+        ctx.close()

@@ -254,3 +254,12 @@ def test_tf32x3_precision_on_host(hctx):
     with pytest.raises(sdrt.SdrtError) as ei:
         sdrt.sdrt_setup_mesh(hctx, bad, blocks, (mesh["faces"], mesh["shift"]))
     assert ei.value.code == -1
+
+
+def test_options_on_host_context(hctx):
+    for opt, default in ((sdrt.SDRT_OPT_NVTX, 0), (sdrt.SDRT_OPT_WAIT_POLLS, 0), (sdrt.SDRT_OPT_GENERATED, 1)):
+        sdrt.sdrt_set_option(hctx, opt, 1 - default)
+        sdrt.sdrt_set_option(hctx, opt, default)
+    with pytest.raises(sdrt.SdrtError) as ei:
+        sdrt.sdrt_set_option(hctx, 99, 1)
+    assert ei.value.code == -1
