@@ -86,8 +86,8 @@ struct MBlock {
     int64_t rec_base = 0, fiur_base = 0;
     DevBuf maos, pfr, perm, recoff;
     // Operator-specialised path (gen_stage.cuh): launcher of the element
-    // type and the face-record index (canonical partner * nvar) of every
-    // external point, [nfe][ld].
+    // type and the face-record index of every external point's partner,
+    // [nfe][ld] (gen_api.hpp layout).
     GenLauncher gen = nullptr;
     DevBuf pmap;
 };
@@ -141,7 +141,7 @@ struct Mesh {
     bool part_grad = false;           // sdrt_residual_gradients ran since the last begin
     // Operator-specialised path: every block has a generated kernel (FP32
     // 3D Euler / Rusanov, SDRT scheme, whole mesh); two face-record arrays
-    // (canonical points x nvar) alternate between RK stages; the blocks run as
+    // (F_tot points x nvar, point-major) alternate between RK stages; the blocks run as
     // concurrent branches (one stream each, forked from and joined to the
     // context's stream).
     bool gen = false;
@@ -428,7 +428,7 @@ int gen_launch_blocks(sdrt_ctx* ctx, Mesh& m, int kind, const float* U, const fl
         a.nelem = mb.nelem;
         a.ld = mb.ld;
         a.u_off = mb.u_off;
-        a.fr_base = mb.canon_base * m.nvar;
+        a.fr_base = mb.fe_base * m.nvar;
         a.metric = mb.metric.as<float>();
         a.pmap = mb.pmap.as<int>();
         a.U = U;
@@ -873,7 +873,7 @@ int ensure_workspace(sdrt_ctx* ctx, Mesh& m, bool need_dual, bool need_rk) {
         if (!m.fiur2.p) SDRT_CUDA(m.fiur2.alloc((size_t)m.fiur_total * es));
     }
     if (m.gen) {
-        const size_t nfr = (size_t)m.nfe_total * m.nvar * sizeof(float);
+        const size_t nfr = (size_t)m.Ftot * m.nvar * sizeof(float);
         if (!m.fr[0].p) SDRT_CUDA(m.fr[0].alloc(nfr));
         if (need_rk && !m.fr[1].p) SDRT_CUDA(m.fr[1].alloc(nfr));
     }
@@ -1745,7 +1745,7 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
     // SDRT element types that have generated kernels and are not on the
     // record path.
     if (!ghost && !m->fast && !m->curved && f32 && phys->system == SDRT_EULER && nd == 3 &&
-        phys->riemann == SDRT_RUSANOV && (int64_t)m->nfe_total * m->nvar < INT32_MAX) {
+        phys->riemann == SDRT_RUSANOV && (int64_t)m->Ftot * m->nvar < INT32_MAX) {
         bool all = true;
         for (auto& bp : m->blocks) {
             const EType& et = *ctx->etypes[bp->etype];
@@ -1760,8 +1760,16 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
             const int nfe = ctx->etypes[mb.etype]->R.nfe;
             std::vector<int> pm((size_t)nfe * mb.ld, 0);
             for (int e = 0; e < mb.nelem; ++e)
-                for (int sg = 0; sg < nfe; ++sg)
-                    pm[(size_t)sg * mb.ld + e] = m->partner[mb.canon_base + (int64_t)e * nfe + sg] * m->nvar;
+                for (int sg = 0; sg < nfe; ++sg) {
+                    // partner (block q, element pe, point ps) of canonical index g
+                    const int64_t g = m->partner[mb.canon_base + (int64_t)e * nfe + sg];
+                    int pb = (int)m->blocks.size() - 1;
+                    while (m->blocks[pb]->canon_base > g) --pb;
+                    const MBlock& q = *m->blocks[pb];
+                    const int qnfe = ctx->etypes[q.etype]->R.nfe;
+                    const int64_t pe = (g - q.canon_base) / qnfe, ps = (g - q.canon_base) % qnfe;
+                    pm[(size_t)sg * mb.ld + e] = (int)((q.fe_base + ps * q.ld + pe) * m->nvar);
+                }
             SDRT_CUDA(upload(mb.pmap, pm));
         }
         if (m->blocks.size() > 1) {

@@ -12,10 +12,12 @@
 namespace sdrt {
 
 // Face records ("FR"): the states at the external flux points of every
-// element, element by element in canonical point order, variables innermost:
-// value (canonical point g, variable v) at g * V + v, with
-// g = canonical base of the block + e * N_fe + sigma.  The face of a partner
-// is one contiguous run of its points' records.
+// element, point-major like the generic path's face states, variables
+// innermost: value (point sigma of element e of a block, variable v) at
+// (fe_base + sigma * ld + e) * V + v, fe_base the block's first external
+// point.  Elements next to each other have their records of a point next to
+// each other, so the partners of a tile's consecutive elements -- often
+// consecutive themselves -- are read from a few cache lines.
 //
 // One launch works on one block (one element type):
 //   kind 0  interpolation: FRout = M0 U at every external point;
@@ -29,9 +31,9 @@ namespace sdrt {
 struct GenArgs {
     int nelem, ld;
     int64_t u_off;           // element offset of the block in the state arrays
-    int64_t fr_base;         // FR index of the block's element 0, point 0 (canonical base * V)
+    int64_t fr_base;         // FR index of the block's point 0, element 0 (fe_base * V)
     const float* metric;     // [NM][ld] (kargs.hpp KBlock layout)
-    const int* pmap;         // [N_fe][ld] FR index (canonical partner * V) of each external point's partner
+    const int* pmap;         // [N_fe][ld] FR index of each external point's partner
     const float* U;          // stage input state (whole state array)
     const float* FRin;       // face records of the stage input (whole array)
     float* FRout;            // face records of the epilogue's new state (whole array) or null

@@ -118,9 +118,11 @@ __device__ __forceinline__ void prefetch_rows(const E* src, int rows, int ld, in
 
 // The external-point values of the tile's state (in US) into the face-record
 // array, chunk by chunk: each chunk staged per element with an odd stride and
-// written as one run per element (the tile's elements are consecutive).
+// written point by point, the tile's elements' records of one point being
+// one contiguous run (dst: the block's records, point-major).
 template <class K, int V>
-__device__ __forceinline__ void write_records(float* sm, float* dst, int nvalid, int v, int h, int lane) {
+__device__ __forceinline__ void write_records(float* sm, float* dst, int e0, int ld, int nvalid, int v, int h,
+                                              int lane) {
     using SM = Smem<K, V>;
     float* S = sm + SM::XS;
     #pragma unroll 1
@@ -130,11 +132,12 @@ __device__ __forceinline__ void write_records(float* sm, float* dst, int nvalid,
         __syncthreads();                                // staging free, US complete
         K::ext(c, h, sm + SM::US + (v * TE + lane) * SM::CS, S + lane * SM::PADREC + v, V);
         __syncthreads();
-        const int nv = rows * V;
-        for (int i = threadIdx.x; i < nvalid * nv; i += SM::NT) {
-            const int el = i / nv;
-            const int j = i - el * nv;
-            dst[((size_t)el * K::NFE + c0) * V + j] = S[el * SM::PADREC + j];
+        const int run = nvalid * V;                     // one point's values of the tile
+        for (int i = threadIdx.x; i < rows * run; i += SM::NT) {
+            const int pt = i / run;
+            const int j = i - pt * run;
+            const int el = j / V;
+            dst[((size_t)(c0 + pt) * ld + e0) * V + j] = S[el * SM::PADREC + pt * V + (j - el * V)];
         }
     }
 }
@@ -333,8 +336,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
             #pragma unroll
             for (int r = 0; r < NSH; ++r)
                 if (r < nrow) smem[SM::US + (v * TE + lane) * SM::CS + h * NSH + r] = acc[r];
-            write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h,
-                                lane);
+            write_records<K, V>(smem, a.FRout + a.fr_base, e0, a.ld, min(TE, a.nelem - e0), v, h, lane);
         }
     }
 }
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE) k_gen_interp(const GenArgs 
         __syncthreads();                                // previous tile's staging read
         stage_state<NT, K::NS, V, SM::CS>(smem + SM::US, a.U + a.u_off, a.ld, e0, a.nelem);
         cp_async_wait_all();
-        write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h, lane);
+        write_records<K, V>(smem, a.FRout + a.fr_base, e0, a.ld, min(TE, a.nelem - e0), v, h, lane);
     }
 }
 
