@@ -1768,7 +1768,8 @@ static int setup_mesh_impl(sdrt_ctx* ctx, const sdrt_physics* phys, int nblocks,
                     const MBlock& q = *m->blocks[pb];
                     const int qnfe = ctx->etypes[q.etype]->R.nfe;
                     const int64_t pe = (g - q.canon_base) / qnfe, ps = (g - q.canon_base) % qnfe;
-                    pm[(size_t)sg * mb.ld + e] = (int)((q.fe_base + ps * q.ld + pe) * m->nvar);
+                    pm[(size_t)sg * mb.ld + e] =
+                        (int)((q.fe_base + (pe / 32) * 32 * qnfe + ps * 32 + pe % 32) * m->nvar);
                 }
             SDRT_CUDA(upload(mb.pmap, pm));
         }

@@ -12,12 +12,14 @@
 namespace sdrt {
 
 // Face records ("FR"): the states at the external flux points of every
-// element, point-major like the generic path's face states, variables
-// innermost: value (point sigma of element e of a block, variable v) at
-// (fe_base + sigma * ld + e) * V + v, fe_base the block's first external
-// point.  Elements next to each other have their records of a point next to
-// each other, so the partners of a tile's consecutive elements -- often
-// consecutive themselves -- are read from a few cache lines.
+// element, in tiles of 32 consecutive elements, each tile point-major,
+// variables innermost: value (point sigma of element e of a block, variable
+// v) at (fe_base + (e / 32) 32 N_fe + sigma 32 + e % 32) * V + v, fe_base the
+// block's first external point (a multiple of 32).  A tile's records are one
+// contiguous block (written as a stream), and within it the records of one
+// point of consecutive elements are next to each other, so the partners of
+// a tile's consecutive elements -- often consecutive themselves -- are read
+// from a few cache lines.
 //
 // One launch works on one block (one element type):
 //   kind 0  interpolation: FRout = M0 U at every external point;
@@ -31,7 +33,7 @@ namespace sdrt {
 struct GenArgs {
     int nelem, ld;
     int64_t u_off;           // element offset of the block in the state arrays
-    int64_t fr_base;         // FR index of the block's point 0, element 0 (fe_base * V)
+    int64_t fr_base;         // FR index of the block's first record (fe_base * V)
     const float* metric;     // [NM][ld] (kargs.hpp KBlock layout)
     const int* pmap;         // [N_fe][ld] FR index of each external point's partner
     const float* U;          // stage input state (whole state array)

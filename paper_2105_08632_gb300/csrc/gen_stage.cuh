@@ -100,13 +100,21 @@ __device__ __forceinline__ void stage_rows(E* dst, const E* src, int rows, int l
 }
 // The tile's state (rows (rho, v) of a block's [N_s][V][ld] array) into the
 // column layout [V][TE][CS] with asynchronous copies; lanes past the end
-// repeat the last element.
+// repeat the last element.  A warp's copies take 8 consecutive elements of 4
+// consecutive rows rho of one variable: with CS an odd multiple of 4 the 32
+// destinations fall on 32 distinct banks (eight 32-byte row segments read).
 template <int NT, int NS, int V, int CS>
 __device__ __forceinline__ void stage_state(float* dst, const float* src, int ld, int e0, int nelem) {
-    for (int i = threadIdx.x; i < NS * V * TE; i += NT) {
-        const int row = i >> 5, te = i & 31;
-        const int rho = row / V, v = row - rho * V;
-        cp_async4(dst + (v * TE + te) * CS + rho, src + (size_t)row * ld + min(e0 + te, nelem - 1));
+    constexpr int RG = (NS + 3) / 4;                    // groups of 4 rows rho
+    for (int i = threadIdx.x; i < RG * V * TE * 4; i += NT) {
+        const int lane = i & 31, w = i >> 5;
+        const int te = (w & 3) * 8 + (lane & 7);
+        const int q = w >> 2;                           // (rho group, v), v fastest
+        const int rg = q / V, v = q - rg * V;
+        const int rho = rg * 4 + (lane >> 3);
+        if (rho < NS)
+            cp_async4(dst + (v * TE + te) * CS + rho,
+                      src + (size_t)(rho * V + v) * ld + min(e0 + te, nelem - 1));
     }
 }
 
@@ -118,11 +126,10 @@ __device__ __forceinline__ void prefetch_rows(const E* src, int rows, int ld, in
 
 // The external-point values of the tile's state (in US) into the face-record
 // array, chunk by chunk: each chunk staged per element with an odd stride and
-// written point by point, the tile's elements' records of one point being
-// one contiguous run (dst: the block's records, point-major).
+// written point by point, the tile's records being one contiguous block
+// (dst: the tile's records, [point][element of the tile][variable]).
 template <class K, int V>
-__device__ __forceinline__ void write_records(float* sm, float* dst, int e0, int ld, int nvalid, int v, int h,
-                                              int lane) {
+__device__ __forceinline__ void write_records(float* sm, float* dst, int nvalid, int v, int h, int lane) {
     using SM = Smem<K, V>;
     float* S = sm + SM::XS;
     #pragma unroll 1
@@ -132,12 +139,12 @@ __device__ __forceinline__ void write_records(float* sm, float* dst, int e0, int
         __syncthreads();                                // staging free, US complete
         K::ext(c, h, sm + SM::US + (v * TE + lane) * SM::CS, S + lane * SM::PADREC + v, V);
         __syncthreads();
-        const int run = nvalid * V;                     // one point's values of the tile
-        for (int i = threadIdx.x; i < rows * run; i += SM::NT) {
-            const int pt = i / run;
-            const int j = i - pt * run;
+        constexpr int RUN = TE * V;                     // one point's values of the tile
+        for (int i = threadIdx.x; i < rows * RUN; i += SM::NT) {
+            const int pt = i / RUN;
+            const int j = i - pt * RUN;
             const int el = j / V;
-            dst[((size_t)(c0 + pt) * ld + e0) * V + j] = S[el * SM::PADREC + pt * V + (j - el * V)];
+            if (el < nvalid) dst[(size_t)(c0 + pt) * RUN + j] = S[el * SM::PADREC + pt * V + (j - el * V)];
         }
     }
 }
@@ -336,7 +343,8 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen
             #pragma unroll
             for (int r = 0; r < NSH; ++r)
                 if (r < nrow) smem[SM::US + (v * TE + lane) * SM::CS + h * NSH + r] = acc[r];
-            write_records<K, V>(smem, a.FRout + a.fr_base, e0, a.ld, min(TE, a.nelem - e0), v, h, lane);
+            write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h,
+                                lane);
         }
     }
 }
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(K::SPLIT * V * TE) k_gen_interp(const GenArgs 
         __syncthreads();                                // previous tile's staging read
         stage_state<NT, K::NS, V, SM::CS>(smem + SM::US, a.U + a.u_off, a.ld, e0, a.nelem);
         cp_async_wait_all();
-        write_records<K, V>(smem, a.FRout + a.fr_base, e0, a.ld, min(TE, a.nelem - e0), v, h, lane);
+        write_records<K, V>(smem, a.FRout + a.fr_base + (size_t)e0 * K::NFE * V, min(TE, a.nelem - e0), v, h, lane);
     }
 }
 
