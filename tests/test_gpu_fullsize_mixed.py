@@ -12,7 +12,8 @@ operator-specialised path):
   Sec. 2), bounded per block by 128 u S with S the largest over the elements
   of a small box of the same cells, computed by the oracle (in a uniform box
   the elements of a cell differ only by orientation); discrete conservation
-  of every variable over every mesh (Sec. 2.1).
+  of every variable over every mesh (Sec. 2.1) within 4 u times the sum of
+  the flux terms' scale (the FP32-rounded operator entries).
 """
 import numpy as np
 import pytest
@@ -96,10 +97,12 @@ def test_uniform_state_and_conservation_at_full_size(setup):
     const = [np.tile(STATE.astype(np.float32)[None, :, None], (l["nsol"], 1, l["nelem"])) for l in M.layouts]
     R = _residual(M, const)
     checked = 0
+    part_scales = []
     for k, (kind, p, nc, n1, n2) in enumerate(bench.MIXED_PARTS):
         cell = (10.0 / nc, 10.0 / nc, 10.0 / (n1 + n2))          # the part's box [-5, 5]^3 in (nc, nc, slabs) cells
         scales = _uniform_scale(kind, p, cell)
         scales.update(_uniform_scale("pri_x" if kind == "hex" else "pri", p, cell))
+        part_scales.append(scales)
         for b in _part_blocks(spec, k):
             shape = spec.mesh["blocks"][b]["shape"]
             S = scales[shape][:, :, None]
@@ -107,12 +110,17 @@ def test_uniform_state_and_conservation_at_full_size(setup):
             assert ratio < 128, (k, shape, ratio)
             checked += 1
     assert checked == len(spec.mesh["blocks"])
-    # conservation: sum over each independent mesh of w_s det J dU/dt_s = 0
+    # conservation: sum over each independent mesh of w_s det J dU/dt_s = 0.  In
+    # FP32 the operators' entries are rounded (relative u each), so the sum is
+    # off by a few u times the flux terms' magnitudes, not by u |dU/dt| (the
+    # near free-stream state cancels its terms): the bound is 4 u sum |w_s| det J S
+    # with S the terms' scale of the uniform state above (same magnitudes);
+    # a face flux missing on one side would be off by whole flux terms.
     U = spec.state(M.sol_points())
     R = _residual(M, U)
     for k in range(len(bench.MIXED_PARTS)):
         tot = np.zeros(5)
-        mag = np.zeros(5)
+        bound = np.zeros(5)
         for b in _part_blocks(spec, k):
             blk = spec.mesh["blocks"][b]
             shape, p = blk["shape"], spec.degrees[b]
@@ -124,5 +132,6 @@ def test_uniform_state_and_conservation_at_full_size(setup):
                                                         "hex": (1, 3, 4)}[shape]], axis=2)))
             r = R[b].astype(np.float64)
             tot += np.einsum("s,sve,e->v", w, r, det)
-            mag += np.einsum("s,sve,e->v", np.abs(w), np.abs(r), det)
-        assert (np.abs(tot) < 1e-5 * mag).all(), (k, tot, mag)
+            smax = part_scales[k][shape].max(axis=0)                 # (V,)
+            bound += 4 * gu.U32 * np.abs(w).sum() * det.sum() * smax
+        assert (np.abs(tot) < bound).all(), (k, tot, bound)
