@@ -242,8 +242,19 @@ __device__ __forceinline__ void run_groups(const GenArgs& a, float* sm, float (&
     if constexpr (G + 1 < K::NG) run_groups<K, V, SYS, RIE, G + 1>(a, sm, acc, v, h, lane);
 }
 
+// CTAs per SM the stage kernel is compiled for (the register cap follows):
+// as many as its shared memory allows, at most 5 for the element types with
+// one thread per column (5 x 160 threads at <= 72 registers, no spills) and 3
+// for those with two (3 x 320 threads at <= 64 registers).
+template <class K, int V>
+constexpr int stage_min_blocks() {
+    constexpr int fit = (228 * 1024) / (Smem<K, V>::FLOATS * (int)sizeof(float) + 1024);
+    constexpr int want = K::SPLIT > 1 ? 3 : 5;
+    return fit < 1 ? 1 : fit < want ? fit : want;
+}
+
 template <class K, int V, int SYS, int RIE>
-__global__ void __launch_bounds__(K::SPLIT * V * TE, K::SPLIT > 1 ? 2 : 3) k_gen_stage(const GenArgs a) {
+__global__ void __launch_bounds__(K::SPLIT * V * TE, (stage_min_blocks<K, V>())) k_gen_stage(const GenArgs a) {
     extern __shared__ __align__(16) float smem[];
     using SM = Smem<K, V>;
     constexpr int NS = K::NS, NSH = K::NSH, NT = SM::NT;
