@@ -137,7 +137,26 @@ void generate(const Key& key, const std::string& dir, std::ostringstream& table)
     // rows of every operator application over SPLIT threads (more warps per
     // SM at the same shared memory per element).
     const int SPLIT = NS > 20 ? 2 : 1;
-    const int budget = SPLIT > 1 ? kBudget : (NS <= 10 ? kBudget / 2 : kBudget * 3 / 4);
+    int budget = SPLIT > 1 ? kBudget : (NS <= 10 ? kBudget / 2 : kBudget * 3 / 4);
+    if (SPLIT > 1) {
+        // Shared memory of the stage kernel (gen_stage.cuh Smem, 5 variables,
+        // 32 elements) for group rows <= b; shrink the groups (not below 48
+        // rows) where that lets three CTAs share an SM.
+        const int CS = (NS + 3) / 4 % 2 ? (NS + 3) / 4 * 4 : (NS + 3) / 4 * 4 + 4;
+        auto smem = [&](int b) {
+            const int us = 5 * 32 * CS, main = us + b * 160 + (10 + 4 * R.nfaces) * 32 + NFE * 32;
+            int crec = std::min(NFE, std::max(1, b - 1)) * 5;
+            if (crec % 2 == 0) ++crec;
+            return 4 * std::max(main, us + 32 * crec);
+        };
+        const int three = 228 * 1024 / 3 - 1024;
+        if (smem(kBudget) > three)
+            for (int b = kBudget - 1; b >= 48; --b)
+                if (smem(b) <= three) {
+                    budget = b;
+                    break;
+                }
+    }
     std::vector<std::vector<int>> groups(1);
     int units = 0;
     for (int i = 0; i < (int)pts.size(); ++i) {
