@@ -488,6 +488,15 @@ int64_t sdrt_launch_count(const sdrt_ctx* ctx);
  *     the kernel's kind (interpolation, residual, residual_jvp, gradient).  No
  *     effect on results; without an attached tool the markers cost a branch. */
 #define SDRT_OPT_NVTX 5
+/*   SDRT_OPT_TC_GRADIENT (default 1): 1 = residuals and RK steps of FP32 3D
+ *     Navier-Stokes meshes whose blocks are all affine tetrahedra of degree
+ *     3 / 4, hexahedra of degree 2 or prisms of degree 2 compute the LDG
+ *     gradient chain (q~ = [M16 | M15 P M12] [C; U], q = J^-T q~, q at the
+ *     flux points = [M0; M12] q; Sec. 2.1) on the tensor cores (tcgen05,
+ *     products split into three TF32 products, FP32 accumulation in tensor
+ *     memory); 0 = the CUDA-core gradient kernel.  Results agree to FP32
+ *     rounding.  The JVP, VJP and diagnostics keep the CUDA-core kernel. */
+#define SDRT_OPT_TC_GRADIENT 6
 int sdrt_set_option(sdrt_ctx* ctx, int option, int value);
 
 /* Per-launch device timing with CUDA events recorded on the context's stream

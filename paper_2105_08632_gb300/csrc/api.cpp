@@ -170,6 +170,7 @@ struct sdrt_ctx {
     int use_gen = 1;              // operator-specialised kernels where generated (SDRT_OPT_GENERATED)
     int wait_polls = 0;           // first copy wait of the record flux kernel (SDRT_OPT_WAIT_POLLS)
     bool nvtx = false;            // NVTX ranges around entry points and kernel launches (SDRT_OPT_NVTX)
+    bool use_tc_grad = true;      // tensor-core gradient chain where instantiated (SDRT_OPT_TC_GRADIENT)
     void* noalloc_scratch = nullptr;   // device address of sdrt_residual_noalloc's static buffer
     std::string err;
     std::vector<std::unique_ptr<EType>> etypes;
@@ -544,14 +545,32 @@ int run_residual(sdrt_ctx* ctx, Mesh& m, const T* U, const T* dU, const KEpi<T>&
     if (viscous(m)) {
         // Flux-point gradients of every block (they read every block's u_fe).
         Q = {m.qfe.as<T>(), dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr};
-        s = prof_begin(ctx, KIND_GRAD);
-        int r = launch_grad<T>(ks, sys, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, m.qfe.as<T>(),
-                               dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr, ctx->nsm,
-                               ctx->stream);
-        prof_end(ctx, s);
-        if (r == -2) return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
-        if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
-        ++ctx->launches;
+        bool tc_grad = false;
+        if constexpr (std::is_same<T, float>::value) {
+            // Tensor-core gradient chain where every block is of an instantiated kind.
+            tc_grad = !dU && ctx->use_tc_grad;
+            for (auto& bp : m.blocks)
+                tc_grad = tc_grad && grad_tc_available(make_kblock<float>(*ctx->etypes[bp->etype], *bp), m.nvar, m.nd);
+            if (tc_grad)
+                for (auto& bp : m.blocks) {
+                    s = prof_begin(ctx, KIND_GRAD);
+                    launch_grad_tc(make_kblock<float>(*ctx->etypes[bp->etype], *bp), m.nvar, m.nd, U, ufe, m.Ftot, P,
+                                   m.qfe.as<float>(), m.qfiu.as<float>(), ctx->flag.as<int>(), ctx->nsm, ctx->stream);
+                    prof_end(ctx, s);
+                    ++ctx->launches;
+                }
+        }
+        if (!tc_grad) {
+            s = prof_begin(ctx, KIND_GRAD);
+            int r = launch_grad<T>(ks, sys, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, m.qfe.as<T>(),
+                                   dU ? m.dqfe.as<T>() : nullptr, m.qfiu.as<T>(), dU ? m.dqfiu.as<T>() : nullptr,
+                                   ctx->nsm, ctx->stream);
+            prof_end(ctx, s);
+            if (r == -2)
+                return fail(ctx, SDRT_ERR_UNSUPPORTED, "JVP tile does not fit in shared memory for this element type");
+            if (r != 0) return fail(ctx, SDRT_ERR_UNSUPPORTED, "system not supported by the gradient kernel");
+            ++ctx->launches;
+        }
     }
     s = prof_begin(ctx, dU ? KIND_JVP : KIND_RESIDUAL);
     int r = launch_residual<T>(ks, sys, m.phys.riemann, m.nd, U, dU, ufe, dU ? dufe : nullptr, m.Ftot, P, E, Q, ctx->nsm,
@@ -2273,6 +2292,7 @@ int sdrt_set_option(sdrt_ctx* ctx, int option, int value) {
     else if (option == SDRT_OPT_GENERATED) ctx->use_gen = value < 0 ? 0 : value > 2 ? 2 : value;
     else if (option == SDRT_OPT_WAIT_POLLS) ctx->wait_polls = value < 0 ? 0 : value;
     else if (option == SDRT_OPT_NVTX) ctx->nvtx = value != 0;
+    else if (option == SDRT_OPT_TC_GRADIENT) ctx->use_tc_grad = value != 0;
     else return fail(ctx, SDRT_ERR_ARG, "unknown option");
     for (auto& m : ctx->meshes)
         if (m && m->graph) {

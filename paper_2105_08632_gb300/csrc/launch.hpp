@@ -64,6 +64,14 @@ int launch_grad(const KSet<T>& ks, int system, int nd, const T* U, const T* dU, 
                 int64_t Ftot, const KPhys<T>& P, T* QFE, T* dQFE, T* QFIU, T* dQFIU, int nsm, cudaStream_t st,
                 T* QSOL = nullptr);
 
+// Gradient chain of one block on the tensor cores (kernels_tc_grad.cu): the
+// value-mode output of launch_grad (QFE / QFIU) for FP32 3D Navier-Stokes on
+// affine blocks of the instantiated element types (tetrahedra p3 / p4,
+// hexahedra p2, prisms p2).  Returns -1 if the block is not of that kind.
+bool grad_tc_available(const KBlock<float>& B, int V, int nd);
+int launch_grad_tc(const KBlock<float>& B, int V, int nd, const float* U, const float* UFE, int64_t Ftot,
+                   const KPhys<float>& P, float* QFE, float* QFIU, int* err, int nsm, cudaStream_t st);
+
 // Taylor-Green diagnostics integrals of one block (kernels_visc.cu), added to
 // sums[5] = {volume, kinetic energy, its time derivative from R, S^d : S^d,
 // p div v}; 3D Navier-Stokes.

@@ -375,6 +375,7 @@ SDRT_OPT_FUSED_RK = 2
 SDRT_OPT_GENERATED = 3
 SDRT_OPT_WAIT_POLLS = 4
 SDRT_OPT_NVTX = 5
+SDRT_OPT_TC_GRADIENT = 6
 PATHS = {0: "generic", 1: "record", 2: "generated"}
 
 
