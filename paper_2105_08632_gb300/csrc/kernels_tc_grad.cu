@@ -14,8 +14,8 @@
 // of kargs.hpp) that the residual kernel reads.  Each product is split into
 // hi + lo TF32 parts, D = Ah Bh + Ah Bl + Al Bh.  The operators are staged
 // once per CTA (K-major core-matrix layout, no swizzle); the A operands are
-// written row by row by the threads, two threads per element (alternate
-// 4-column chunks).  One CTA of 256 threads per SM.  Every wait for the tensor
+// written row by row by the threads, four threads per element (every fourth
+// 4-column chunk).  One CTA of 512 threads per SM.  Every wait for the tensor
 // core is bounded (2^22 polls, far above an MMA's microseconds); when one runs
 // out the kernel records bit 1 of the error flag, the whole CTA stops and frees
 // its tensor memory, and the caller's sdrt_sync reports SDRT_ERR_TIMEOUT.
@@ -35,8 +35,9 @@ namespace {
 
 template <int NS, int NFE, int NFIU>
 struct GradTC {
-    static constexpr int V = 5, ND = 3, TE = 128, NT = 256;
-    static constexpr int N1 = ND * NS, N1P = (N1 + 15) / 16 * 16;      // GEMM 1 N (M = 128 needs N % 16 == 0)
+    static constexpr int V = 5, ND = 3, TE = 128, NT = 512, NH = NT / TE;   // NH threads per row
+    static constexpr int NSP = (NS + 3) / 4 * 4;                        // D1 columns (d, s) at d * NSP + s
+    static constexpr int N1 = ND * NSP, N1P = (N1 + 15) / 16 * 16;     // GEMM 1 N (M = 128 needs N % 16 == 0)
     static constexpr int K1 = NFE + NS, K1P = (K1 + 7) / 8 * 8;         // GEMM 1 K (K8 steps)
     static constexpr int N2 = NFE + NFIU, N2P = (N2 + 15) / 16 * 16;
     static constexpr int K2P = (NS + 7) / 8 * 8;
@@ -81,13 +82,13 @@ __device__ __forceinline__ void mma3(uint32_t d, const unsigned char* ah, const 
 }  // namespace
 
 template <int NS, int NFE, int NFIU>
-__global__ void __launch_bounds__(256, 1) k_grad_tc(KBlock<float> B, const float* __restrict__ U,
+__global__ void __launch_bounds__(512, 1) k_grad_tc(KBlock<float> B, const float* __restrict__ U,
                                                     const float* __restrict__ UFE, int64_t Ftot, float beta,
                                                     float* __restrict__ QFE, float* __restrict__ QFIU,
                                                     int* __restrict__ err) {
     using G = GradTC<NS, NFE, NFIU>;
     constexpr int V = G::V, ND = G::ND, TE = G::TE;
-    constexpr int N1 = G::N1, N1P = G::N1P, K1 = G::K1, K1P = G::K1P, N2 = G::N2, N2P = G::N2P, K2P = G::K2P;
+    constexpr int N1P = G::N1P, K1 = G::K1, K1P = G::K1P, N2 = G::N2, N2P = G::N2P, K2P = G::K2P;
     constexpr uint32_t ID1 = idesc_tf32(128, N1P), ID2 = idesc_tf32(128, N2P);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* B1h = smem_raw;
@@ -99,13 +100,17 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(KBlock<float> B, const float
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int L = tid & (TE - 1), h = tid >> 7;           // element lane, half of the columns
+    constexpr int NH = G::NH;
+    const int L = tid & (TE - 1), h = tid >> 7;           // element lane, quarter of the columns
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     if (warp == 0) tmem_alloc(tslot, G::COLS);
-    // B1[n][k] = [M16 | M15 P M12][n][k]: Ag holds it transposed, [k][Mg_pad].
+    // B1[n][k] = [M16 | M15 P M12][(d, s)][k] with n = d * NSP + s (16-byte aligned
+    // column groups per d): Ag holds it transposed, [k][Mg_pad], column d * NS + s.
+    constexpr int NSP = G::NSP;
     for (int i = tid; i < N1P * K1P; i += G::NT) {
         const int n = i / K1P, k = i - n * K1P;
-        const float x = (n < N1 && k < K1) ? B.Ag[(size_t)k * B.Mg_pad + n] : 0.f;
+        const int d = n / NSP, sp = n - d * NSP;
+        const float x = (d < ND && sp < NS && k < K1) ? B.Ag[(size_t)k * B.Mg_pad + d * NS + sp] : 0.f;
         const float hx = to_tf32(x);
         *reinterpret_cast<float*>(B1h + core_off(n, k, K1P)) = hx;
         *reinterpret_cast<float*>(B1l + core_off(n, k, K1P)) = to_tf32(x - hx);
@@ -155,8 +160,8 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(KBlock<float> B, const float
         #pragma unroll 1
         for (int v = 0; v < V && !aborted; ++v) {
             // A1 row L: [C_v at the external points; U_v at the solution points]
-            #pragma unroll 4
-            for (int c = h; c < K1P / 4; c += 2) {
+            #pragma unroll 3
+            for (int c = h; c < K1P / 4; c += NH) {
                 float x[4];
                 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -188,10 +193,22 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(KBlock<float> B, const float
                 break;
             }
             tc_fence_after();
-            // q~ of this element: TMEM row L, columns (d, s)
-            float qt[N1P];
+            // q~ of this element at the solution points of this thread's chunks of
+            // A2 (columns d * NSP + s of TMEM row L, groups of 4), loaded once for the 3 components
+            constexpr int NCH = (K2P / 4 + NH - 1) / NH;      // chunks per thread
+            float qt[NCH][ND][4];
             #pragma unroll
-            for (int c = 0; c < N1P / 16; ++c) tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), qt + 16 * c);
+            for (int j = 0; j < NCH; ++j) {
+                const int c = h + j * NH;
+                #pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    uint32_t r[4] = {0u, 0u, 0u, 0u};
+                    if (4 * c < NS) tmem_ld4_nowait(tmem + lane_base + (uint32_t)(d * NSP + 4 * c), r);
+                    #pragma unroll
+                    for (int q = 0; q < 4; ++q) qt[j][d][q] = __uint_as_float(r[q]);
+                }
+            }
+            tmem_ld_wait();
             // GEMM 2 per gradient component i: A2_i = q_i(s) = sum_d J^{-1}_{di} q~(d, s)
             #pragma unroll
             for (int i = 0; i < ND; ++i) {
@@ -203,17 +220,17 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(KBlock<float> B, const float
                 unsigned char* ah = AR + b * 2 * G::A2_BYTES;
                 unsigned char* al = ah + G::A2_BYTES;
                 #pragma unroll
-                for (int c = 0; c < K2P / 4; ++c) {
-                    if ((c & 1) != h) continue;                // compile-time indices into qt
+                for (int j = 0; j < NCH; ++j) {
+                    const int c = h + j * NH;
+                    if (c >= K2P / 4) continue;
                     float x[4];
                     #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int s = 4 * c + q;
                         float val = 0.f;
-                        if (s < NS) {
-                            val = Ji[0 * ND + i] * qt[0 * NS + s];
+                        if (4 * c + q < NS) {
+                            val = Ji[0 * ND + i] * qt[j][0][q];
                             #pragma unroll
-                            for (int d = 1; d < ND; ++d) val = fmaf(Ji[d * ND + i], qt[d * NS + s], val);
+                            for (int d = 1; d < ND; ++d) val = fmaf(Ji[d * ND + i], qt[j][d][q], val);
                         }
                         x[q] = val;
                     }
@@ -241,7 +258,7 @@ __global__ void __launch_bounds__(256, 1) k_grad_tc(KBlock<float> B, const float
             for (int i = 0; i < ND; ++i) {
                 const size_t dv = (size_t)(i * V + v);
                 #pragma unroll 1
-                for (int c = h; c < N2P / 16; c += 2) {
+                for (int c = h; c < N2P / 16; c += NH) {
                     float x[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)(N1P + i * N2P + c * 16), x);
                     if (valid) {

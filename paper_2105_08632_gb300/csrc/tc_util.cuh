@@ -112,6 +112,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* o) {
     for (int i = 0; i < 16; ++i) o[i] = __uint_as_float(r[i]);
 }
 
+// 4 consecutive 32-bit TMEM columns of this thread's lane (no wait: call
+// tmem_ld_wait before using the values).
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Byte offset of element (row r, k) in a K-major core-matrix operand with
 // kp K values per row (kp multiple of 4): [r / 8][k / 4][r % 8][k % 4].
 __device__ __forceinline__ uint32_t core_off(int r, int k, int kp) {
