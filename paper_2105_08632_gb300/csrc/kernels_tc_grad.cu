@@ -15,7 +15,7 @@
 // hi + lo TF32 parts, D = Ah Bh + Ah Bl + Al Bh.  The operators are staged
 // once per CTA (K-major core-matrix layout, no swizzle); the A operands are
 // written row by row by the threads, four threads per element (every fourth
-// 4-column chunk).  One CTA of 512 threads per SM.  Every wait for the tensor
+// 4-column chunk), from values gathered one variable ahead.  One CTA of 512 threads per SM.  Every wait for the tensor
 // core is bounded (2^22 polls, far above an MMA's microseconds); when one runs
 // out the kernel records bit 1 of the error flag, the whole CTA stops and frees
 // its tensor memory, and the caller's sdrt_sync reports SDRT_ERR_TIMEOUT.
@@ -146,10 +146,43 @@ __global__ void __launch_bounds__(512, 1) k_grad_tc(KBlock<float> B, const float
     };
     bool aborted = false;
     const int ntiles = (B.nelem + TE - 1) / TE;
+    // This thread's chunks of A1 row L for variable v of element e: [C_v at the
+    // external points; U_v at the solution points], gathered into registers one
+    // variable ahead (the loads run during the previous variable's stores).
+    constexpr int NCH1 = (K1P / 4 + NH - 1) / NH;
+    auto gather = [&](int v, int e, float (&pre)[NCH1][4]) {
+        #pragma unroll
+        for (int j = 0; j < NCH1; ++j) {
+            const int c = h + j * NH;
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * c + q;
+                float val = 0.f;
+                if (k < NFE) {
+                    const int f = __ldg(B.fe_face + k);
+                    const float s = __ldg(B.metric + (size_t)(B.mr_f + f * B.mr_ff + k * B.mr_fp + ND) * B.ld + e);
+                    const float wo = s > 0.f ? 0.5f - beta : 0.5f + beta;   // own side is L when s > 0
+                    const float own = __ldg(UFE + (size_t)v * Ftot + B.fe_base + (size_t)k * B.ld + e);
+                    const float nbr = __ldg(UFE + (size_t)v * Ftot + __ldg(B.map + (size_t)k * B.ld + e));
+                    val = wo * own + (1.f - wo) * nbr;
+                } else if (k < K1) {
+                    val = __ldg(U + B.u_off + (size_t)((k - NFE) * V + v) * B.ld + e);
+                }
+                pre[j][q] = val;
+            }
+        }
+    };
+    float pre[NCH1][4];
+    if (blockIdx.x < ntiles) {
+        const int e = min((int)blockIdx.x * TE + L, B.nelem - 1);
+        gather(0, e, pre);
+    }
     for (int tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
         const int e0 = tile * TE;
         const bool valid = e0 + L < B.nelem;
         const int e = valid ? e0 + L : B.nelem - 1;       // lanes past the end repeat the last element
+        const int tn = tile + gridDim.x;                  // next tile of this CTA
+        const int en = min(tn * TE + L, B.nelem - 1);
         // J^{-1}_{di} = S_di / det J (affine block: one set per element)
         float Ji[ND * ND];
         {
@@ -159,27 +192,11 @@ __global__ void __launch_bounds__(512, 1) k_grad_tc(KBlock<float> B, const float
         }
         #pragma unroll 1
         for (int v = 0; v < V && !aborted; ++v) {
-            // A1 row L: [C_v at the external points; U_v at the solution points]
-            #pragma unroll 3
-            for (int c = h; c < K1P / 4; c += NH) {
-                float x[4];
-                #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = 4 * c + q;
-                    float val = 0.f;
-                    if (k < NFE) {
-                        const int f = __ldg(B.fe_face + k);
-                        const float s = __ldg(B.metric + (size_t)(B.mr_f + f * B.mr_ff + k * B.mr_fp + ND) * B.ld + e);
-                        const float wo = s > 0.f ? 0.5f - beta : 0.5f + beta;   // own side is L when s > 0
-                        const float own = __ldg(UFE + (size_t)v * Ftot + B.fe_base + (size_t)k * B.ld + e);
-                        const float nbr = __ldg(UFE + (size_t)v * Ftot + __ldg(B.map + (size_t)k * B.ld + e));
-                        val = wo * own + (1.f - wo) * nbr;
-                    } else if (k < K1) {
-                        val = __ldg(U + B.u_off + (size_t)((k - NFE) * V + v) * B.ld + e);
-                    }
-                    x[q] = val;
-                }
-                put4(A1h, A1l, L, 4 * c, K1P, x);
+            // A1 row L from the gathered values
+            #pragma unroll
+            for (int j = 0; j < NCH1; ++j) {
+                const int c = h + j * NH;
+                if (c < K1P / 4) put4(A1h, A1l, L, 4 * c, K1P, pre[j]);
             }
             fence_proxy_async();
             __syncthreads();
@@ -253,6 +270,9 @@ __global__ void __launch_bounds__(512, 1) k_grad_tc(KBlock<float> B, const float
                 }
             }
             tc_fence_after();
+            // the next variable's (or the next tile's first) A1 values, in flight during the stores
+            if (v + 1 < V) gather(v + 1, e, pre);
+            else if (tn < ntiles) gather(0, en, pre);
             // rows of D2 -> QFE / QFIU (component i, variable v)
             #pragma unroll 1
             for (int i = 0; i < ND; ++i) {
